@@ -1,0 +1,626 @@
+/*
+ * odp_oracle.c -- plain FP64 CPU oracle of the time-dependent HJ level-set
+ * method of OptimizedDP (arXiv 2204.05520), Algorithm 1.
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark load this library.  It shares no code, header,
+ * table or constant with the CUDA library; the two meet only through the
+ * seeded inputs both are given.
+ *
+ * It is written to be checked against the paper by eye, not to be fast: every
+ * value is double, every grid point is visited with plain loops over its
+ * multi-index, and the two per-point passes of Algorithm 1 (Hamiltonian and
+ * derivative range, then dissipation) are kept as two passes.  The only
+ * liberty is an OpenMP "parallel for" over grid points, the parallel outer loop
+ * of Section 5.1; it changes no result (per-point work is independent and the
+ * one reduction is a max).
+ *
+ * Readings of the paper taken where it is silent or garbled (each is also
+ * listed in the design notes of the repository):
+ *  R1 time runs as look-back tau = -s from 0 to T:  phi(tau+dt) = phi + dt*L.
+ *  R2 Lax-Friedrichs sign: L = H(pbar) + 1/2 sum_d alpha_d (p+_d - p-_d)
+ *     (positive viscosity in tau).
+ *  R4 mode rule: a "max" input takes +bound when its switching function is
+ *     >= 0, a "min" input takes -bound when it is >= 0.
+ *  R5 alpha: global per-component bound, alpha_d = max over grid points of the
+ *     largest |f_d| over the input extremes that the point's derivative box
+ *     can select (a switching interval strictly above or below 0 selects one
+ *     extreme, otherwise both).
+ *  R7 CFL step dt = cfl / sum_d(alpha_d/dz_d), clipped at the segment end;
+ *     a segment ends when its remaining time is <= 1e-12 * its end time.
+ *  R8 TVD-RK2 (Heun / Shu-Osher): phi1 = phi + dt L(phi);
+ *     phi2 = phi1 + dt L(phi1); phi_new = (phi + phi2)/2; one dt per step from
+ *     the stage-1 alpha, stage 2 uses its own alpha.  BRT min once per step.
+ *  R9 ghost cells on non-periodic axes: k cells outside the boundary point b,
+ *     g_k = phi_b + k*sign(phi_b)*|phi_b - phi_inner|, sign(0) = +1.
+ *  R10 ENO2: p- = D-phi + (h/2) c, p+ = D+phi - (h/2) c', c (c') the second
+ *     difference of smaller magnitude among those at i-1 and i (i and i+1);
+ *     on equal magnitude the centred one (at i).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OG_MAXD 8
+
+/* dynamics ids (this library's own numbering) */
+enum { OG_SINGLE_INT = 0, OG_DUBINS3D = 1, OG_DUBINSCAR4D = 2, OG_REL6D = 3, OG_ADVECTION = 4 };
+enum { OG_MIN = 0, OG_MAX = 1 };
+enum { OG_BRS = 0, OG_BRT = 1 };
+
+/* return codes */
+enum { OG_OK = 0, OG_EINVAL = -1, OG_ENOMEM = -2, OG_ETIMEOUT = -5, OG_ENUMERIC = -6 };
+
+typedef struct {
+    int ndim;
+    int64_t n[OG_MAXD];
+    double lo[OG_MAXD], hi[OG_MAXD], dz[OG_MAXD];
+    int periodic[OG_MAXD];
+    int64_t stride[OG_MAXD];
+    int64_t total;
+} og_grid;
+
+typedef struct {
+    int kind;
+    int ndim;
+    double prm[OG_MAXD];
+    int umode, dmode;
+} og_dyn;
+
+/* ------------------------------------------------------------------------- */
+/* Grid (Section 3.1.1): node counts, bounds, periodic axes.                  */
+/* Node i sits at lo + i*dz; dz = (hi-lo)/(n-1), or (hi-lo)/n when periodic.  */
+/* ------------------------------------------------------------------------- */
+static int og_grid_init(og_grid *g, int ndim, const int64_t *n, const double *lo,
+                        const double *hi, const int *periodic)
+{
+    if (ndim < 1 || ndim > OG_MAXD) return OG_EINVAL;
+    g->ndim = ndim;
+    for (int d = 0; d < ndim; ++d) {
+        if (periodic[d] ? n[d] < 1 : n[d] < 2) return OG_EINVAL;
+        if (!(hi[d] > lo[d])) return OG_EINVAL;
+        g->n[d] = n[d];
+        g->lo[d] = lo[d];
+        g->hi[d] = hi[d];
+        g->periodic[d] = periodic[d] ? 1 : 0;
+        g->dz[d] = periodic[d] ? (hi[d] - lo[d]) / (double)n[d]
+                               : (hi[d] - lo[d]) / (double)(n[d] - 1);
+    }
+    g->total = 1;
+    for (int d = ndim - 1; d >= 0; --d) {   /* C order: last axis fastest */
+        g->stride[d] = g->total;
+        g->total *= n[d];
+    }
+    return OG_OK;
+}
+
+static void og_unflatten(const og_grid *g, int64_t flat, int64_t *idx)
+{
+    for (int d = 0; d < g->ndim; ++d) {
+        idx[d] = flat / g->stride[d];
+        flat -= idx[d] * g->stride[d];
+    }
+}
+
+static void og_state(const og_grid *g, const int64_t *idx, double *z)
+{
+    for (int d = 0; d < g->ndim; ++d) z[d] = g->lo[d] + (double)idx[d] * g->dz[d];
+}
+
+/* phi at the node `off` cells away from idx along axis d, with the periodic
+ * wrap or the sign-keeping ghost extrapolation of Section 3.1.1 (reading R9). */
+static double og_shifted(const og_grid *g, const double *phi, const int64_t *idx,
+                         int64_t flat, int d, int off)
+{
+    int64_t n = g->n[d];
+    int64_t j = idx[d] + off;
+    int64_t row = flat - idx[d] * g->stride[d];
+    if (g->periodic[d]) {
+        j = ((j % n) + n) % n;
+        return phi[row + j * g->stride[d]];
+    }
+    if (j >= 0 && j < n) return phi[row + j * g->stride[d]];
+    int64_t b = (j < 0) ? 0 : n - 1;          /* boundary node            */
+    int64_t in = (j < 0) ? 1 : n - 2;         /* its inner neighbour      */
+    double k = (j < 0) ? (double)(-j) : (double)(j - (n - 1));   /* cells outside */
+    double pb = phi[row + b * g->stride[d]];
+    double pin = phi[row + in * g->stride[d]];
+    double sgn = (pb >= 0.0) ? 1.0 : -1.0;
+    return pb + k * sgn * fabs(pb - pin);
+}
+
+/* One-sided derivatives p-, p+ along axis d at a node (Section 3.1.4 and
+ * Algorithm 1: first-order upwind differences, or second-order ENO R10). */
+static void og_one_sided(const og_grid *g, const double *phi, const int64_t *idx,
+                         int64_t flat, int d, int order, double *pm, double *pp)
+{
+    double h = g->dz[d];
+    double f0 = phi[flat];
+    double fm1 = og_shifted(g, phi, idx, flat, d, -1);
+    double fp1 = og_shifted(g, phi, idx, flat, d, +1);
+    double dm = (f0 - fm1) / h;   /* backward difference D-phi */
+    double dp = (fp1 - f0) / h;   /* forward difference  D+phi */
+    if (order == 1) {
+        *pm = dm;
+        *pp = dp;
+        return;
+    }
+    double fm2 = og_shifted(g, phi, idx, flat, d, -2);
+    double fp2 = og_shifted(g, phi, idx, flat, d, +2);
+    double d2_left = (f0 - 2.0 * fm1 + fm2) / (h * h);     /* at i-1 */
+    double d2_mid = (fp1 - 2.0 * f0 + fm1) / (h * h);      /* at i   */
+    double d2_right = (fp2 - 2.0 * fp1 + f0) / (h * h);    /* at i+1 */
+    double c_minus = (fabs(d2_left) < fabs(d2_mid)) ? d2_left : d2_mid;
+    double c_plus = (fabs(d2_right) < fabs(d2_mid)) ? d2_right : d2_mid;
+    *pm = dm + 0.5 * h * c_minus;
+    *pp = dp - 0.5 * h * c_plus;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Dynamics plug-ins (Section 4.2: opt_ctrl, opt_dstb, dynamics).             */
+/* ------------------------------------------------------------------------- */
+
+static int og_n_ctrl(const og_dyn *dy)
+{
+    switch (dy->kind) {
+    case OG_SINGLE_INT: return dy->ndim;
+    case OG_DUBINS3D: return 1;
+    case OG_DUBINSCAR4D: return 2;
+    case OG_REL6D: return 2;
+    default: return 0;
+    }
+}
+
+static int og_n_dstb(const og_dyn *dy)
+{
+    return dy->kind == OG_REL6D ? 2 : 0;
+}
+
+static double og_ctrl_bound(const og_dyn *dy, int k)
+{
+    switch (dy->kind) {
+    case OG_SINGLE_INT: return dy->prm[0];          /* |u_i| <= u_max            */
+    case OG_DUBINS3D: return dy->prm[1];            /* |w| <= w_max              */
+    case OG_DUBINSCAR4D: return dy->prm[k];         /* |a| <= a_max, |w| <= w_max */
+    case OG_REL6D: return dy->prm[k];               /* |a_p|, |alpha_p|          */
+    default: return 0.0;
+    }
+}
+
+static double og_dstb_bound(const og_dyn *dy, int k)
+{
+    return dy->kind == OG_REL6D ? dy->prm[2 + k] : 0.0;   /* |a_e|, |w_e| */
+}
+
+/* f(z, u, d) of each model (Appendix; Rel6D is the repository's 6-D
+ * relative model built from the 3D pursuit-evasion and 5D Dubins equations). */
+static void og_dynamics(const og_dyn *dy, const double *z, const double *u,
+                        const double *dd, double *f)
+{
+    switch (dy->kind) {
+    case OG_SINGLE_INT:
+        for (int i = 0; i < dy->ndim; ++i) f[i] = u[i];
+        break;
+    case OG_ADVECTION:
+        for (int i = 0; i < dy->ndim; ++i) f[i] = dy->prm[i];
+        break;
+    case OG_DUBINS3D: {           /* (x, y, th): v cos th, v sin th, w */
+        double v = dy->prm[0];
+        f[0] = v * cos(z[2]);
+        f[1] = v * sin(z[2]);
+        f[2] = u[0];
+        break;
+    }
+    case OG_DUBINSCAR4D: {        /* (x, y, v, th): v cos th, v sin th, a, w */
+        f[0] = z[2] * cos(z[3]);
+        f[1] = z[2] * sin(z[3]);
+        f[2] = u[0];
+        f[3] = u[1];
+        break;
+    }
+    case OG_REL6D: {              /* (x, y, th, v_p, w_p, v_e) */
+        double x = z[0], y = z[1], th = z[2], vp = z[3], wp = z[4], ve = z[5];
+        f[0] = -vp + ve * cos(th) + wp * y;
+        f[1] = ve * sin(th) - wp * x;
+        f[2] = dd[1] - wp;        /* evader turn rate w_e minus pursuer w_p */
+        f[3] = u[0];              /* pursuer acceleration a_p               */
+        f[4] = u[1];              /* pursuer angular acceleration alpha_p   */
+        f[5] = dd[0];             /* evader acceleration a_e                */
+        break;
+    }
+    default:
+        for (int i = 0; i < dy->ndim; ++i) f[i] = 0.0;
+    }
+}
+
+/* Switching-function coefficients of input k: g = f(z, e_k, 0) - f(z, 0, 0),
+ * exact for the input-affine models above. */
+static void og_input_column(const og_dyn *dy, const double *z, int is_dstb, int k, double *g)
+{
+    double u0[OG_MAXD] = {0}, d0[OG_MAXD] = {0}, f0[OG_MAXD], f1[OG_MAXD];
+    og_dynamics(dy, z, u0, d0, f0);
+    if (is_dstb) d0[k] = 1.0; else u0[k] = 1.0;
+    og_dynamics(dy, z, u0, d0, f1);
+    for (int i = 0; i < dy->ndim; ++i) g[i] = f1[i] - f0[i];
+}
+
+/* Bang-bang choice for one input from its switching function s (R4). */
+static double og_bang(double s, double bound, int mode)
+{
+    if (mode == OG_MAX) return (s >= 0.0) ? bound : -bound;
+    return (s >= 0.0) ? -bound : bound;
+}
+
+/* Optimal control and disturbance (Algorithm 1, the argmin_d argmax_u step). */
+static void og_opt_inputs(const og_dyn *dy, const double *z, const double *p,
+                          double *u, double *dd)
+{
+    double g[OG_MAXD];
+    for (int k = 0; k < og_n_ctrl(dy); ++k) {
+        og_input_column(dy, z, 0, k, g);
+        double s = 0.0;
+        for (int i = 0; i < dy->ndim; ++i) s += p[i] * g[i];
+        u[k] = og_bang(s, og_ctrl_bound(dy, k), dy->umode);
+    }
+    for (int k = 0; k < og_n_dstb(dy); ++k) {
+        og_input_column(dy, z, 1, k, g);
+        double s = 0.0;
+        for (int i = 0; i < dy->ndim; ++i) s += p[i] * g[i];
+        dd[k] = og_bang(s, og_dstb_bound(dy, k), dy->dmode);
+    }
+}
+
+/* H_i = pbar . f(z_i, u_opt, d_opt)  (Algorithm 1). */
+static double og_hamiltonian(const og_dyn *dy, const double *z, const double *pbar)
+{
+    double u[OG_MAXD] = {0}, dd[OG_MAXD] = {0}, f[OG_MAXD];
+    og_opt_inputs(dy, z, pbar, u, dd);
+    og_dynamics(dy, z, u, dd, f);
+    double h = 0.0;
+    for (int i = 0; i < dy->ndim; ++i) h += pbar[i] * f[i];
+    return h;
+}
+
+/* Local dissipation bound a_d(z) (reading R5): the largest |f_d| over every
+ * combination of input extremes that the derivative box [pmin, pmax] admits. */
+static void og_local_alpha(const og_dyn *dy, const double *z, const double *pmin,
+                           const double *pmax, double *a)
+{
+    int nu = og_n_ctrl(dy), nd = og_n_dstb(dy), ni = nu + nd;
+    double choice[2 * OG_MAXD][2];
+    int count[2 * OG_MAXD];
+    double g[OG_MAXD];
+    for (int k = 0; k < ni; ++k) {
+        int is_d = (k >= nu);
+        int kk = is_d ? k - nu : k;
+        og_input_column(dy, z, is_d, kk, g);
+        /* interval of the switching function s = p . g over the box */
+        double slo = 0.0, shi = 0.0;
+        for (int i = 0; i < dy->ndim; ++i) {
+            if (g[i] >= 0.0) { slo += g[i] * pmin[i]; shi += g[i] * pmax[i]; }
+            else             { slo += g[i] * pmax[i]; shi += g[i] * pmin[i]; }
+        }
+        double bound = is_d ? og_dstb_bound(dy, kk) : og_ctrl_bound(dy, kk);
+        int mode = is_d ? dy->dmode : dy->umode;
+        if (slo > 0.0) { choice[k][0] = og_bang(1.0, bound, mode); count[k] = 1; }
+        else if (shi < 0.0) { choice[k][0] = og_bang(-1.0, bound, mode); count[k] = 1; }
+        else { choice[k][0] = -bound; choice[k][1] = bound; count[k] = 2; }
+    }
+    for (int i = 0; i < dy->ndim; ++i) a[i] = 0.0;
+    int combos = 1;
+    for (int k = 0; k < ni; ++k) combos *= count[k];
+    for (int c = 0; c < combos; ++c) {
+        double u[OG_MAXD] = {0}, dd[OG_MAXD] = {0}, f[OG_MAXD];
+        int rest = c;
+        for (int k = 0; k < ni; ++k) {
+            double val = choice[k][rest % count[k]];
+            rest /= count[k];
+            if (k < nu) u[k] = val; else dd[k - nu] = val;
+        }
+        og_dynamics(dy, z, u, dd, f);
+        for (int i = 0; i < dy->ndim; ++i)
+            if (fabs(f[i]) > a[i]) a[i] = fabs(f[i]);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* The two per-point passes of Algorithm 1.                                   */
+/* ------------------------------------------------------------------------- */
+
+/* First pass: alpha^max over the grid (global-alpha approximation of
+ * Section 2.1, reading R5). */
+static void og_alpha(const og_grid *g, const og_dyn *dy, const double *phi, int order,
+                     double *alpha)
+{
+    int nd = g->ndim;
+    double amax[OG_MAXD];
+    for (int d = 0; d < OG_MAXD; ++d) amax[d] = 0.0;
+#pragma omp parallel
+    {
+        double loc[OG_MAXD];
+        for (int d = 0; d < OG_MAXD; ++d) loc[d] = 0.0;
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < g->total; ++i) {
+            int64_t idx[OG_MAXD];
+            double z[OG_MAXD], pm[OG_MAXD], pp[OG_MAXD], lo[OG_MAXD], hi[OG_MAXD], a[OG_MAXD];
+            og_unflatten(g, i, idx);
+            og_state(g, idx, z);
+            for (int d = 0; d < nd; ++d) {
+                og_one_sided(g, phi, idx, i, d, order, &pm[d], &pp[d]);
+                lo[d] = fmin(pm[d], pp[d]);
+                hi[d] = fmax(pm[d], pp[d]);
+            }
+            og_local_alpha(dy, z, lo, hi, a);
+            for (int d = 0; d < nd; ++d)
+                if (a[d] > loc[d]) loc[d] = a[d];
+        }
+#pragma omp critical
+        for (int d = 0; d < nd; ++d)
+            if (loc[d] > amax[d]) amax[d] = loc[d];
+    }
+    for (int d = 0; d < nd; ++d) alpha[d] = amax[d];
+}
+
+/* Second pass: the Lax-Friedrichs right-hand side at every node,
+ * L = H(pbar) + 1/2 sum_d alpha_d (p+_d - p-_d)  (Algorithm 1, reading R2). */
+static void og_rhs(const og_grid *g, const og_dyn *dy, const double *phi, int order,
+                   const double *alpha, double *L)
+{
+    int nd = g->ndim;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < g->total; ++i) {
+        int64_t idx[OG_MAXD];
+        double z[OG_MAXD], pm[OG_MAXD], pp[OG_MAXD], pbar[OG_MAXD];
+        og_unflatten(g, i, idx);
+        og_state(g, idx, z);
+        for (int d = 0; d < nd; ++d) {
+            og_one_sided(g, phi, idx, i, d, order, &pm[d], &pp[d]);
+            pbar[d] = 0.5 * (pp[d] + pm[d]);
+        }
+        double h = og_hamiltonian(dy, z, pbar);
+        double diss = 0.0;
+        for (int d = 0; d < nd; ++d) diss += 0.5 * alpha[d] * (pp[d] - pm[d]);
+        L[i] = h + diss;
+    }
+}
+
+/* CFL step of Algorithm 1: (sum_d alpha_d / dz_d)^-1 scaled by cfl. */
+static double og_cfl_dt(const og_grid *g, const double *alpha, double cfl)
+{
+    double s = 0.0;
+    for (int d = 0; d < g->ndim; ++d) s += alpha[d] / g->dz[d];
+    if (s <= 0.0) return INFINITY;
+    return cfl / s;
+}
+
+static int og_setup(og_grid *g, og_dyn *dy, int ndim, const int64_t *n, const double *lo,
+                    const double *hi, const int *periodic, int kind, const double *prm,
+                    int n_prm, int umode, int dmode)
+{
+    int rc = og_grid_init(g, ndim, n, lo, hi, periodic);
+    if (rc) return rc;
+    memset(dy, 0, sizeof(*dy));
+    dy->kind = kind;
+    dy->ndim = ndim;
+    dy->umode = umode;
+    dy->dmode = dmode;
+    int need;
+    switch (kind) {
+    case OG_SINGLE_INT: need = 1; break;
+    case OG_DUBINS3D: need = 2; if (ndim != 3) return OG_EINVAL; break;
+    case OG_DUBINSCAR4D: need = 2; if (ndim != 4) return OG_EINVAL; break;
+    case OG_REL6D: need = 4; if (ndim != 6) return OG_EINVAL; break;
+    case OG_ADVECTION: need = ndim; break;
+    default: return OG_EINVAL;
+    }
+    if (n_prm < need || n_prm > OG_MAXD) return OG_EINVAL;
+    for (int k = 0; k < n_prm; ++k) dy->prm[k] = prm[k];
+    return OG_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Exported entry points                                                      */
+/* ------------------------------------------------------------------------- */
+
+int og_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void og_set_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
+/* Node spacing of every axis. */
+int og_spacing(int ndim, const int64_t *n, const double *lo, const double *hi,
+               const int *periodic, double *dz_out)
+{
+    og_grid g;
+    int rc = og_grid_init(&g, ndim, n, lo, hi, periodic);
+    if (rc) return rc;
+    for (int d = 0; d < ndim; ++d) dz_out[d] = g.dz[d];
+    return OG_OK;
+}
+
+/* f(z, u, d) for one state (used by brute-force checks). */
+int og_eval_dynamics(int kind, int ndim, const double *prm, int n_prm, const double *z,
+                     const double *u, const double *dd, double *f)
+{
+    og_dyn dy;
+    memset(&dy, 0, sizeof(dy));
+    dy.kind = kind;
+    dy.ndim = ndim;
+    for (int k = 0; k < n_prm && k < OG_MAXD; ++k) dy.prm[k] = prm[k];
+    og_dynamics(&dy, z, u, dd, f);
+    return OG_OK;
+}
+
+/* f(z_j, u_j, d_j) for `count` independent triples (inputs padded to 8). */
+int og_eval_dynamics_batch(int kind, int ndim, const double *prm, int n_prm, int64_t count,
+                           const double *z, const double *u, const double *dd, double *f)
+{
+    og_dyn dy;
+    memset(&dy, 0, sizeof(dy));
+    dy.kind = kind;
+    dy.ndim = ndim;
+    for (int k = 0; k < n_prm && k < OG_MAXD; ++k) dy.prm[k] = prm[k];
+    for (int64_t j = 0; j < count; ++j)
+        og_dynamics(&dy, z + j * ndim, u + j * OG_MAXD, dd + j * OG_MAXD, f + j * ndim);
+    return OG_OK;
+}
+
+/* Per-node terms of one Algorithm 1 evaluation on a given phi:
+ * p- and p+ (ndim each, node-major), pbar, the optimal inputs, H, the local
+ * dissipation bound a_d(z), and the full right-hand side L with the given
+ * alpha (or the grid alpha when alpha_in is NULL).  Any output may be NULL. */
+int og_terms(int ndim, const int64_t *n, const double *lo, const double *hi,
+             const int *periodic, int kind, const double *prm, int n_prm, int umode,
+             int dmode, int order, const double *phi, const double *alpha_in,
+             double *pm_out, double *pp_out, double *u_out, double *d_out,
+             double *h_out, double *a_out, double *alpha_out, double *rhs_out)
+{
+    og_grid g;
+    og_dyn dy;
+    int rc = og_setup(&g, &dy, ndim, n, lo, hi, periodic, kind, prm, n_prm, umode, dmode);
+    if (rc) return rc;
+    if (order != 1 && order != 2) return OG_EINVAL;
+    int nu = og_n_ctrl(&dy), ndst = og_n_dstb(&dy);
+    double alpha[OG_MAXD];
+    og_alpha(&g, &dy, phi, order, alpha);
+    if (alpha_out)
+        for (int d = 0; d < ndim; ++d) alpha_out[d] = alpha[d];
+    if (alpha_in)
+        for (int d = 0; d < ndim; ++d) alpha[d] = alpha_in[d];
+    for (int64_t i = 0; i < g.total; ++i) {
+        int64_t idx[OG_MAXD];
+        double z[OG_MAXD], pm[OG_MAXD], pp[OG_MAXD], pbar[OG_MAXD];
+        double lo_b[OG_MAXD], hi_b[OG_MAXD], a[OG_MAXD];
+        double u[OG_MAXD] = {0}, dd[OG_MAXD] = {0};
+        og_unflatten(&g, i, idx);
+        og_state(&g, idx, z);
+        for (int d = 0; d < ndim; ++d) {
+            og_one_sided(&g, phi, idx, i, d, order, &pm[d], &pp[d]);
+            pbar[d] = 0.5 * (pp[d] + pm[d]);
+            lo_b[d] = fmin(pm[d], pp[d]);
+            hi_b[d] = fmax(pm[d], pp[d]);
+        }
+        og_opt_inputs(&dy, z, pbar, u, dd);
+        og_local_alpha(&dy, z, lo_b, hi_b, a);
+        double h = og_hamiltonian(&dy, z, pbar);
+        for (int d = 0; d < ndim; ++d) {
+            if (pm_out) pm_out[i * ndim + d] = pm[d];
+            if (pp_out) pp_out[i * ndim + d] = pp[d];
+            if (a_out) a_out[i * ndim + d] = a[d];
+        }
+        for (int k = 0; k < nu; ++k)
+            if (u_out) u_out[i * OG_MAXD + k] = u[k];
+        for (int k = 0; k < ndst; ++k)
+            if (d_out) d_out[i * OG_MAXD + k] = dd[k];
+        if (h_out) h_out[i] = h;
+        if (rhs_out) {
+            double diss = 0.0;
+            for (int d = 0; d < ndim; ++d) diss += 0.5 * alpha[d] * (pp[d] - pm[d]);
+            rhs_out[i] = h + diss;
+        }
+    }
+    return OG_OK;
+}
+
+/* Full solve (Algorithm 1 with the BRS / BRT post-step of Section 4.3).
+ *  l           target l(z), total nodes; phi(z, 0) = l(z)
+ *  tau         n_tau look-back times, tau[0] = 0, strictly increasing
+ *  set_kind    OG_BRS (plain PDE) or OG_BRT (phi <- min(phi, l) after each step,
+ *              the HJ variational inequality)
+ *  snapshots   NULL, or n_tau * total doubles: phi at every tau
+ *  final_out   total doubles: phi at tau[n_tau-1]
+ *  steps_out   NULL or n_tau-1 step counts, one per segment
+ *  alpha_out   NULL or ndim doubles: alpha of the last stage
+ *  last_dt     NULL or the last step's dt
+ */
+int og_solve(int ndim, const int64_t *n, const double *lo, const double *hi,
+             const int *periodic, int kind, const double *prm, int n_prm, int umode,
+             int dmode, const double *l, const double *tau, int n_tau, int set_kind,
+             int space_order, int time_order, double cfl, int64_t max_steps,
+             double *snapshots, double *final_out, int64_t *steps_out,
+             double *alpha_out, double *last_dt)
+{
+    og_grid g;
+    og_dyn dy;
+    int rc = og_setup(&g, &dy, ndim, n, lo, hi, periodic, kind, prm, n_prm, umode, dmode);
+    if (rc) return rc;
+    if (n_tau < 2 || tau[0] != 0.0) return OG_EINVAL;
+    for (int k = 1; k < n_tau; ++k)
+        if (!(tau[k] > tau[k - 1])) return OG_EINVAL;
+    if (space_order != 1 && space_order != 2) return OG_EINVAL;
+    if (time_order != 1 && time_order != 2) return OG_EINVAL;
+    if (!(cfl > 0.0)) return OG_EINVAL;
+    if (set_kind != OG_BRS && set_kind != OG_BRT) return OG_EINVAL;
+
+    int64_t N = g.total;
+    double *phi = malloc(sizeof(double) * N);
+    double *phi1 = malloc(sizeof(double) * N);
+    double *L = malloc(sizeof(double) * N);
+    if (!phi || !phi1 || !L) { free(phi); free(phi1); free(L); return OG_ENOMEM; }
+    memcpy(phi, l, sizeof(double) * N);
+    if (snapshots) memcpy(snapshots, phi, sizeof(double) * N);
+
+    double alpha[OG_MAXD] = {0}, alpha2[OG_MAXD] = {0};
+    double dt = 0.0;
+    int64_t total_steps = 0;
+    rc = OG_OK;
+    for (int k = 0; k + 1 < n_tau && rc == OG_OK; ++k) {
+        double t = tau[k], t_end = tau[k + 1];
+        int64_t seg_steps = 0;
+        while (t_end - t > 1e-12 * t_end) {
+            if (total_steps >= max_steps) { rc = OG_ETIMEOUT; break; }
+            /* stage 1: alpha, dt, phi1 = phi + dt L(phi) */
+            og_alpha(&g, &dy, phi, space_order, alpha);
+            double dt_cfl = og_cfl_dt(&g, alpha, cfl);
+            int last = !(dt_cfl < t_end - t);
+            dt = last ? (t_end - t) : dt_cfl;
+            og_rhs(&g, &dy, phi, space_order, alpha, L);
+            for (int64_t i = 0; i < N; ++i) phi1[i] = phi[i] + dt * L[i];
+            if (time_order == 2) {
+                /* stage 2 with its own alpha; Heun average */
+                og_alpha(&g, &dy, phi1, space_order, alpha2);
+                og_rhs(&g, &dy, phi1, space_order, alpha2, L);
+                for (int64_t i = 0; i < N; ++i)
+                    phi1[i] = 0.5 * (phi[i] + (phi1[i] + dt * L[i]));
+            }
+            int bad = 0;
+            for (int64_t i = 0; i < N; ++i) {
+                double v = phi1[i];
+                if (set_kind == OG_BRT && l[i] < v) v = l[i];
+                if (!isfinite(v)) bad = 1;
+                phi[i] = v;
+            }
+            if (bad) { rc = OG_ENUMERIC; break; }
+            t = last ? t_end : t + dt;
+            ++seg_steps;
+            ++total_steps;
+        }
+        if (steps_out) steps_out[k] = seg_steps;
+        if (snapshots) memcpy(snapshots + (int64_t)(k + 1) * N, phi, sizeof(double) * N);
+    }
+    if (final_out) memcpy(final_out, phi, sizeof(double) * N);
+    if (alpha_out)
+        for (int d = 0; d < ndim; ++d) alpha_out[d] = (time_order == 2) ? alpha2[d] : alpha[d];
+    if (last_dt) *last_dt = dt;
+    free(phi);
+    free(phi1);
+    free(L);
+    return rc;
+}
