@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Throughput of the HJ level-set solve (Algorithm 1 of arXiv 2204.05520) on GB300.
+
+One benchmark step = one complete solve of the workload (all time steps of
+the tau schedule) with the value arrays resident in HBM.  The default workload
+is the 4D Dubins car BRT on an 80x80x40x64 grid (16.4M nodes), ENO2 + TVD-RK2,
+CFL 0.8, t in [0, 3] (265 time steps).  The metric is grid-point updates per
+second (nodes x time steps / device time), reported with the fraction of the
+measured HBM copy bandwidth reached by the fused stage kernel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Under torchrun every rank solves its own copy of the workload (independent
+solves, weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "grid-point updates/s"
+UNIT = "updates/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=("dubinscar4d", "dubins3d", "rel6d"), default="dubinscar4d")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def rank_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_sources_sha() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2204_05520_gb300", "csrc")
+    for p in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
+        with open(p, "rb") as fh:
+            h.update(os.path.basename(p).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def dram_traffic(workload: str):
+    """ncu DRAM bytes per stage launch recorded for this workload, if the
+    kernel sources are unchanged since the capture; else None."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            rec = json.load(fh).get(workload)
+        if rec and rec.get("sources_sha") == kernel_sources_sha():
+            return float(rec["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(world: int, use_cuda: bool):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+
+    dist.init_process_group(backend="nccl" if use_cuda else "gloo")
+    return dist
+
+
+def max_over_ranks(dist, value: float, device) -> float:
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle: baseline sample and the reference arm
+# ---------------------------------------------------------------------------
+
+def oracle_sample(problem, n_steps: int):
+    """Time the FP64 oracle on the full workload, stopped by its step limit
+    after `n_steps` time steps; returns (updates/s, seconds, threads, steps)."""
+    import oracle
+
+    oracle.build()
+    l = problem.target_values()
+    t0 = time.perf_counter()
+    r = oracle.solve(problem, l=l, max_steps=n_steps, raise_on_error=False)
+    secs = time.perf_counter() - t0
+    steps = int(r["steps"].sum())
+    return problem.points * steps / secs, secs, oracle.num_threads(), steps
+
+
+def run_reference(args):
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return 0
+    from paper_2204_05520_gb300 import inputs
+
+    problem = inputs.workload(args.workload)
+    for _ in range(args.warmup):
+        oracle_sample(problem, 1)
+    total_updates, total_s, threads = 0.0, 0.0, 1
+    for _ in range(args.steps):
+        ups, secs, threads, steps = oracle_sample(problem, 1)
+        total_updates += ups * secs
+        total_s += secs
+    value = total_updates / total_s
+    sample = "one time step of the full %s grid (%d nodes) per benchmark step" % (
+        problem.name, problem.points)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": problem.name},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2204_05520_gb300 import _build, inputs, odp
+
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    dist = dist_setup(world, True)
+    _build.build()
+    odp.load()
+    device = torch.device("cuda", local)
+    problem = inputs.workload(args.workload)
+    N = problem.points
+    l_host = problem.target_values()
+    stream = torch.cuda.Stream()
+    l_dev = torch.from_numpy(l_host).to(device)
+    grid = odp.Grid.for_problem(problem, stream=stream)
+    grid.set_target(l_dev)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            grid.solve_problem(problem)
+    st = odp.solve_status(grid.handle)
+    steps_per_solve = int(st["steps"])
+    launches_per_solve = int(st["launches"]) + 1   # + the once-per-solve alpha reduction
+    bytes_per_solve = float(st["bytes"])
+
+    sampler = ClockSampler(local)
+    torch.cuda.synchronize()
+    barrier(dist)
+    sampler.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        grid.solve_problem(problem)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    clocks = sampler.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    odp.solve_status(grid.handle)   # raises if the device flagged an error
+    ms_total = max_over_ranks(dist, ms_total, device)
+    ms_per_step = ms_total / args.steps
+    value = world * N * steps_per_solve / (ms_per_step / 1000.0)
+
+    # dominant kernel: the fused stage pass, timed alone on its stream
+    stages = (1, 2) if problem.time_order == 2 else (0,)
+    stage_ms = [odp.time_stage(grid.handle, s, reps=20) for s in stages]
+    brt = problem.set_kind == "brt"
+    if problem.time_order == 2:
+        alg_bytes = [8.0 * N, (12.0 + (4.0 if brt else 0.0)) * N]
+    else:
+        alg_bytes = [(8.0 + (4.0 if brt else 0.0)) * N]
+    launch_ms = sum(stage_ms) / len(stage_ms)
+    bytes_per_launch = sum(alg_bytes) / len(alg_bytes)
+    peak, peak_kind = hbm_peak()
+    achieved = bytes_per_launch / (launch_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": dram_traffic(problem.name),
+                "kernel": "k_stage", "peak_source": peak_kind,
+                "stage_ms": stage_ms, "alg_bytes_per_launch": bytes_per_launch}
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        l_pin = torch.from_numpy(l_host).pin_memory()
+        out_pin = torch.empty_like(l_pin).pin_memory()
+        grid.solve_problem(problem)
+        grid.readback(out_pin)
+        torch.cuda.synchronize()
+        barrier(dist)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            grid.set_target(l_pin)
+            grid.solve_problem(problem)
+            grid.readback(out_pin)
+        t_e2e = time.perf_counter() - t0
+        t_e2e = max_over_ranks(dist, t_e2e, device)
+        e2e = {"value": world * N * steps_per_solve * args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N,
+               "ms_per_step": 1000.0 * t_e2e / args.steps}
+        grid.set_target(l_dev)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ups, secs, threads, nst = oracle_sample(problem, 5)
+        cpu = {"value": ups, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "%d time steps of the full %s grid (%d nodes), %.1f s" % (
+                   nst, problem.name, N, secs)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": problem.name, "nodes": N, "time_steps_per_solve": steps_per_solve,
+                       "scheme": "ENO%d + %s" % (problem.space_order,
+                                                  "TVD-RK2" if problem.time_order == 2 else "Euler"),
+                       "set": problem.set_kind, "cfl": problem.cfl, "horizon": problem.tau[-1],
+                       "l2": "working set (%.0f MB) larger than L2 (129 MB)" % (12.0 * N / 1e6),
+                       "parallelism": "independent solve per GPU"},
+            "gpu_launches": launches_per_solve * args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+            "alg_bytes_per_solve": bytes_per_solve,
+        }
+        print(json.dumps(line), flush=True)
+    grid.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

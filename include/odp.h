@@ -1,0 +1,191 @@
+/*
+ * odp.h -- C ABI of libodp, the GB300 (sm_103a) solver for the time-dependent
+ * Hamilton-Jacobi level-set update of OptimizedDP (arXiv 2204.05520).
+ *
+ * What it computes (paper, Section 2.1, Algorithm 1): starting from a target
+ * function l(z) sampled on a dense N-D grid, phi(z, 0) = l(z), the value
+ * function is advanced in look-back time tau.  Each time step computes, at
+ * every grid node, one-sided spatial derivatives p-, p+ (first-order upwind or
+ * second-order ENO, Section 3.1.4), their mean pbar, the optimal control and
+ * disturbance of the Hamiltonian and H = pbar . f(z, u*, d*), a
+ * Lax-Friedrichs dissipation with per-dimension coefficients alpha taken as a
+ * grid-wide maximum (Section 2.1, global-alpha approximation), a CFL-limited
+ * step dt (Algorithm 1), a forward-Euler or TVD-RK2 update (Section 3.1.3) and,
+ * for a backward reachable tube, the min with l (the HJ variational
+ * inequality of Section 2.1, method "minVWithV0" of Section 4.3).
+ *
+ * Conventions for every function:
+ *  - Return value: an odp_status, ODP_OK (0) on success, a negative code
+ *    otherwise.  No C++ exception crosses the ABI.  odp_last_error() returns a
+ *    message for the calling thread's last failure.
+ *  - Grids are dense C-order arrays (last dimension fastest, as NumPy lays
+ *    them out; paper Section 5.2), float32 values, at most ODP_MAX_DIMS
+ *    dimensions and fewer than 2^31 nodes.
+ *  - Node i of an axis sits at lo + i*h, h = (hi - lo)/(n - 1) on a
+ *    non-periodic axis and (hi - lo)/n on a periodic one (Section 3.1.1).
+ *    Ghost nodes outside a non-periodic axis are extrapolated so that they
+ *    keep the sign of the boundary node:  g_k = phi_b + k*sign(phi_b)*
+ *    |phi_b - phi_inner| for the k-th ghost, sign(0) = +1.
+ *  - Work is asynchronous on the CUDA stream given to odp_grid_create
+ *    (a cudaStream_t passed as void*, NULL = the legacy default stream).
+ *    Functions that return data to the host or report device-side errors
+ *    synchronise that stream; each says so.
+ *  - Pointers marked "device" are CUDA device pointers (for example a torch
+ *    tensor's data_ptr()); "host" pointers may be pageable or pinned.  The
+ *    library copies what it is given and never keeps a caller pointer.
+ *  - A grid object is not thread-safe: calls on one grid must not overlap.
+ */
+#ifndef ODP_H
+#define ODP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ODP_MAX_DIMS 6
+
+typedef int odp_status;
+#define ODP_OK 0
+#define ODP_EINVAL (-1)   /* invalid argument (sizes, ranges, NULL pointers)        */
+#define ODP_ENOMEM (-2)   /* device allocation failed or a memory budget is exceeded */
+#define ODP_ECUDA (-3)    /* a CUDA runtime call failed (message in odp_last_error)  */
+#define ODP_ESTATE (-4)   /* call out of order: dynamics or target missing, no solve */
+#define ODP_ETIMEOUT (-5) /* the solve reached its step limit before the horizon     */
+#define ODP_ENUMERIC (-6) /* a non-finite value appeared in the value function       */
+#define ODP_EBUSY (-7)    /* the object is in use                                   */
+
+typedef struct odp_grid odp_grid;
+
+/* Closed set of hand-coded dynamics (paper Section 4.2 plug-ins, Appendix).
+ * params per model, all bounds >= 0:
+ *  ODP_DYN_SINGLE_INT  any ndim: z' = u, |u_i| <= params[0]
+ *  ODP_DYN_DUBINS3D    z = (x, y, th): x' = v cos th, y' = v sin th, th' = w,
+ *                      |w| <= w_max; params (v, w_max)            (Appendix, 3D Dubins)
+ *  ODP_DYN_DUBINSCAR4D z = (x, y, v, th): x' = v cos th, y' = v sin th, v' = a,
+ *                      th' = w; params (a_max, w_max)             (Appendix, 4D Dubins)
+ *  ODP_DYN_REL6D       z = (x, y, th, v_p, w_p, v_e): relative pursuit-evasion
+ *                      x' = -v_p + v_e cos th + w_p y, y' = v_e sin th - w_p x,
+ *                      th' = w_e - w_p, v_p' = a_p, w_p' = alpha_p, v_e' = a_e;
+ *                      control (a_p, alpha_p), disturbance (a_e, w_e);
+ *                      params (a_p max, alpha_p max, a_e max, w_e max)
+ *                      (the 3D pursuit-evasion model of Section 4.2 extended
+ *                      with speed and turn-rate states as in the 5D Dubins car)
+ *  ODP_DYN_ADVECTION   any ndim: z' = c, params c_0 .. c_{ndim-1} (no inputs)
+ * Angles (th) must lie on a periodic axis. */
+typedef enum {
+    ODP_DYN_SINGLE_INT = 0,
+    ODP_DYN_DUBINS3D = 1,
+    ODP_DYN_DUBINSCAR4D = 2,
+    ODP_DYN_REL6D = 3,
+    ODP_DYN_ADVECTION = 4
+} odp_dyn;
+
+/* Role of an input in the Hamiltonian (Algorithm 1, optimal control and
+ * disturbance step; Section 4.2 uMode/dMode).  ODP_MAX takes +bound when its
+ * switching function is >= 0, ODP_MIN takes -bound when it is >= 0. */
+typedef enum { ODP_MIN = 0, ODP_MAX = 1 } odp_mode;
+
+/* Backward reachable set (plain PDE, method "None") or tube (phi <- min(phi,
+ * l) after every full step, method "minVWithV0"); Section 4.3. */
+typedef enum { ODP_BRS = 0, ODP_BRT = 1 } odp_set;
+
+typedef struct {
+    int64_t steps;     /* full time steps over all tau segments                 */
+    double last_dt;    /* dt of the last step                                   */
+    double t_final;    /* look-back time reached (tau[n_tau-1] on success)      */
+    float alpha[8];    /* dissipation coefficients alpha_d of the last stage    */
+    double device_ms;  /* device time of the time loop (CUDA events)            */
+    double bytes;      /* algorithmic HBM bytes of the time loop                */
+    int64_t launches;  /* kernels launched by the time loop                     */
+} odp_solve_stats;
+
+/* Message describing the calling thread's last failure ("" if none). */
+const char *odp_last_error(void);
+
+/* Library version string. */
+const char *odp_version(void);
+
+/* Create a grid (Section 3.1.1).  n, lo, hi, periodic: ndim entries each
+ * (host).  n[d] >= 2 on a non-periodic axis, >= 1 on a periodic one;
+ * hi[d] > lo[d].  cuda_stream: the stream all work on this grid is issued on.
+ * Allocates the value buffers on the current device.  *out receives the
+ * grid; release it with odp_grid_destroy.
+ * Errors: ODP_EINVAL, ODP_ENOMEM, ODP_ECUDA. */
+odp_status odp_grid_create(int ndim, const int32_t *n, const double *lo, const double *hi,
+                           const uint8_t *periodic, void *cuda_stream, odp_grid **out);
+
+/* Free a grid and all device memory it owns (synchronises its stream).
+ * NULL is accepted. */
+odp_status odp_grid_destroy(odp_grid *g);
+
+/* Number of nodes of a grid (product of n). */
+int64_t odp_grid_points(const odp_grid *g);
+
+/* Choose the dynamics (Section 4.2 plug-ins, Appendix models; see odp_dyn).
+ * params: n_params doubles (host), copied.  u_mode / d_mode: roles of the
+ * control and the disturbance.  Errors: ODP_EINVAL (unknown model, wrong
+ * dimension count, missing parameters, negative bound, angle axis not
+ * periodic). */
+odp_status odp_set_dynamics(odp_grid *g, odp_dyn kind, const double *params, int n_params,
+                            odp_mode u_mode, odp_mode d_mode);
+
+/* Set the target function l(z) (initial value phi(z, 0) = l(z); Section 2.1),
+ * n_elems = odp_grid_points(g) float32 values in C order.  on_device: 1 if l
+ * is a device pointer, 0 for host memory.  The values are copied
+ * (asynchronously for device and pinned host memory).  Errors: ODP_EINVAL. */
+odp_status odp_set_target(odp_grid *g, const float *l, int64_t n_elems, int on_device);
+
+/* Limit the number of full time steps of one solve (default 10,000,000).  A
+ * solve that reaches the limit stops and reports ODP_ETIMEOUT. */
+odp_status odp_set_step_limit(odp_grid *g, int64_t max_steps);
+
+/* Solve the HJ PDE (Algorithm 1) from tau[0] = 0 to tau[n_tau-1].
+ *  tau          n_tau >= 2 strictly increasing look-back times (host), tau[0] = 0;
+ *               each segment is integrated separately, the last CFL step of a
+ *               segment clipped to its end (HJSolver's tau schedule, Section 4.3)
+ *  set          ODP_BRS or ODP_BRT
+ *  space_order  1 (upwind) or 2 (ENO2)
+ *  time_order   1 (forward Euler) or 2 (TVD-RK2)
+ *  cfl          (0, 1]: dt = cfl / sum_d(alpha_d / h_d)
+ *  keep_snapshots  1 keeps phi at every tau (readable with odp_value_readback)
+ *  stats        NULL: the solve is only enqueued and returns at once; device-side
+ *               errors then surface in odp_value_readback or odp_solve_status.
+ *               Non-NULL: the call synchronises the stream and fills *stats.
+ * The whole time loop runs as one CUDA graph with a device-side while loop;
+ * dt and t are kept in float64 on the device.
+ * Errors: ODP_ESTATE (no dynamics or target), ODP_EINVAL, ODP_ENOMEM,
+ * ODP_ECUDA, and with stats != NULL also ODP_ETIMEOUT, ODP_ENUMERIC. */
+odp_status odp_solve_hjb(odp_grid *g, const double *tau, int n_tau, odp_set set,
+                         int space_order, int time_order, double cfl, int keep_snapshots,
+                         odp_solve_stats *stats);
+
+/* Wait for the grid's last solve and return its device-side status
+ * (ODP_OK, ODP_ETIMEOUT or ODP_ENUMERIC); synchronises the stream.  Fills
+ * *stats when non-NULL (device_ms and bytes only if the solve was timed). */
+odp_status odp_solve_status(odp_grid *g, odp_solve_stats *stats);
+
+/* Copy the value function out: tau_index -1 (or n_tau-1) = the final value,
+ * 0..n_tau-2 need keep_snapshots.  dst: n_elems = odp_grid_points(g) floats,
+ * device memory if on_device else host memory.  Synchronises the stream and
+ * reports the solve's device-side status (ODP_ETIMEOUT, ODP_ENUMERIC).
+ * Errors: ODP_ESTATE (no solve yet), ODP_EINVAL, ODP_ECUDA. */
+odp_status odp_value_readback(odp_grid *g, int tau_index, float *dst, int64_t n_elems,
+                              int on_device);
+
+/* Measurement helper (no paper counterpart): launch the fused stage kernel of
+ * the grid's last solve `reps` times on its stream, outside the graph, and
+ * return the mean device time of one launch in *ms_out (CUDA events; the call
+ * synchronises).  stage: 0 = Euler, 1 = RK2 stage 1, 2 = RK2 stage 2 (must
+ * match the last solve's time order).  The launches overwrite the value
+ * buffers: solve again before reading values back.
+ * Errors: ODP_ESTATE (no solve yet), ODP_EINVAL, ODP_ECUDA. */
+odp_status odp_time_stage(odp_grid *g, int stage, int reps, double *ms_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ODP_H */

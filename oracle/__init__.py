@@ -70,7 +70,10 @@ def _load():
                                      P, P, P, P, P, P, P, P]
             lib.og_solve.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, P, i32, i32,
                                      i32, i32, f64, i64, P, P, P, P, P]
-            for f in (lib.og_spacing, lib.og_eval_dynamics, lib.og_terms, lib.og_solve):
+            lib.og_step.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, P, f64, i32, i32,
+                                    i32, P, P]
+            for f in (lib.og_spacing, lib.og_eval_dynamics, lib.og_terms, lib.og_solve,
+                      lib.og_step):
                 f.restype = i32
             _lib = lib
     return _lib
@@ -178,6 +181,28 @@ def terms(problem_or_grid, phi, order=None, alpha=None, dynamics=None, params=No
     for k in ("H", "rhs"):
         out[k] = out[k].reshape(shape)
     return out
+
+
+def step(problem, phi, dt, l=None) -> dict:
+    """One full time step of size ``dt`` from ``phi`` (float64 copy taken),
+    as ``solve`` takes it.  Returns dict(out, alpha) with alpha of stage 1."""
+    lib = _load()
+    p = problem
+    n_a, lo_a, hi_a, per_a = _grid_args(p.n, p.lo, p.hi, p.periodic)
+    if l is None:
+        l = p.target_values()
+    l64 = np.ascontiguousarray(l, dtype=np.float64).reshape(-1)
+    phi64 = np.ascontiguousarray(phi, dtype=np.float64).reshape(-1)
+    prm = np.ascontiguousarray(p.params, dtype=np.float64)
+    out = np.zeros_like(phi64)
+    alpha = np.zeros(len(n_a))
+    rc = lib.og_step(len(n_a), _ptr(n_a), _ptr(lo_a), _ptr(hi_a), _ptr(per_a),
+                     DYN_IDS[p.dynamics], _ptr(prm), len(prm), MODE_IDS[p.u_mode],
+                     MODE_IDS[p.d_mode], _ptr(l64), _ptr(phi64), float(dt), SET_IDS[p.set_kind],
+                     p.space_order, p.time_order, _ptr(out), _ptr(alpha))
+    if rc:
+        raise OracleError(rc, "step")
+    return {"out": out.reshape(tuple(p.n)), "alpha": alpha}
 
 
 def solve(problem, l=None, snapshots: bool = False, max_steps: int = 10_000_000,

@@ -539,6 +539,46 @@ int og_terms(int ndim, const int64_t *n, const double *lo, const double *hi,
     return OG_OK;
 }
 
+/* One full time step of size dt from phi (Algorithm 1 update with the
+ * Euler or TVD-RK2 integrator of Section 3.1.3 and the BRS / BRT post-step),
+ * as taken inside og_solve.  out may not alias phi.  alpha_out (ndim) gets the
+ * stage-1 alpha (the one the CFL step is computed from). */
+int og_step(int ndim, const int64_t *n, const double *lo, const double *hi, const int *periodic,
+            int kind, const double *prm, int n_prm, int umode, int dmode, const double *l,
+            const double *phi, double dt, int set_kind, int space_order, int time_order,
+            double *out, double *alpha_out)
+{
+    og_grid g;
+    og_dyn dy;
+    int rc = og_setup(&g, &dy, ndim, n, lo, hi, periodic, kind, prm, n_prm, umode, dmode);
+    if (rc) return rc;
+    if (space_order != 1 && space_order != 2) return OG_EINVAL;
+    if (time_order != 1 && time_order != 2) return OG_EINVAL;
+    int64_t N = g.total;
+    double *L = malloc(sizeof(double) * N);
+    double *phi1 = (time_order == 2) ? malloc(sizeof(double) * N) : NULL;
+    if (!L || (time_order == 2 && !phi1)) { free(L); free(phi1); return OG_ENOMEM; }
+    double alpha[OG_MAXD] = {0};
+    og_alpha(&g, &dy, phi, space_order, alpha);
+    if (alpha_out)
+        for (int d = 0; d < ndim; ++d) alpha_out[d] = alpha[d];
+    og_rhs(&g, &dy, phi, space_order, alpha, L);
+    if (time_order == 1) {
+        for (int64_t i = 0; i < N; ++i) out[i] = phi[i] + dt * L[i];
+    } else {
+        for (int64_t i = 0; i < N; ++i) phi1[i] = phi[i] + dt * L[i];
+        og_alpha(&g, &dy, phi1, space_order, alpha);
+        og_rhs(&g, &dy, phi1, space_order, alpha, L);
+        for (int64_t i = 0; i < N; ++i) out[i] = 0.5 * (phi[i] + (phi1[i] + dt * L[i]));
+    }
+    if (set_kind == OG_BRT)
+        for (int64_t i = 0; i < N; ++i)
+            if (l[i] < out[i]) out[i] = l[i];
+    free(L);
+    free(phi1);
+    return OG_OK;
+}
+
 /* Full solve (Algorithm 1 with the BRS / BRT post-step of Section 4.3).
  *  l           target l(z), total nodes; phi(z, 0) = l(z)
  *  tau         n_tau look-back times, tau[0] = 0, strictly increasing

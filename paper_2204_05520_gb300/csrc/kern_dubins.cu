@@ -1,0 +1,21 @@
+// kern_dubins.cu -- kernel instantiations for the 3D Dubins car and the 4D
+// Dubins car (Appendix models).
+#include "hj_kernels.cuh"
+
+namespace odp {
+
+cudaError_t launch_stage_dubins(int nd, const GridDesc &g, const DynDesc &dy, SolveState *st,
+                                const float *l, int order, int stage, int brt, cudaStream_t s)
+{
+    if (nd == 3) return launch_stage_t<3, DYN_DUBINS3D>(g, dy, st, l, order, stage, brt, s);
+    return launch_stage_t<4, DYN_DUBINSCAR4D>(g, dy, st, l, order, stage, brt, s);
+}
+
+cudaError_t launch_alpha_static_dubins(int nd, const GridDesc &g, const DynDesc &dy,
+                                       SolveState *st, cudaStream_t s)
+{
+    if (nd == 3) return launch_alpha_static_t<3, DYN_DUBINS3D>(g, dy, st, s);
+    return launch_alpha_static_t<4, DYN_DUBINSCAR4D>(g, dy, st, s);
+}
+
+}  // namespace odp

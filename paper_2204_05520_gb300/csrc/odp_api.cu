@@ -1,0 +1,663 @@
+// odp_api.cu -- the C ABI of libodp (include/odp.h): grid objects, the host
+// scheduler of one solve and the CUDA graph that runs its time loop.
+//
+// One solve (Algorithm 1 with the tau schedule of HJSolver, Section 4.3):
+//   host, once per solve:  phi <- l, state upload, static alpha reduction
+//   one CUDA graph:        WHILE (device flag) {
+//                            [Rel6D: heading alpha of phi]    K1
+//                            dt from alpha (float64)          K3
+//                            stage pass(es)                   K2
+//                            [Rel6D: heading alpha of phi1]   K1
+//                            advance t, segment, flags        K3
+//                            IF (segment ended) snapshot copy
+//                          }
+// t, dt and the tau schedule stay in float64 on the device; the loop never
+// returns to the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/odp.h"
+#include "odp_common.cuh"
+#include "odp_launch.h"
+
+using namespace odp;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static odp_status fail(odp_status code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define ODP_CUDA(call)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(e_ == cudaErrorMemoryAllocation ? ODP_ENOMEM : ODP_ECUDA,         \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                        \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// graph-control kernels (single thread)
+// ---------------------------------------------------------------------------
+
+// CFL step of Algorithm 1 from the stage-1 alpha, clipped to the segment end.
+__global__ void k_dt(SolveState *st, GridDesc g)
+{
+    double s = 0.0;
+    for (int d = 0; d < g.ndim; ++d)
+        s = __dadd_rn(s, __ddiv_rn(double(__uint_as_float(st->alpha_bits[0][d])), g.dz[d]));
+    const double rem = __dsub_rn(st->t_end, st->t);
+    const double dt_cfl = (s > 0.0) ? __ddiv_rn(st->cfl, s) : INFINITY;
+    const int last = !(dt_cfl < rem);
+    st->dt = last ? rem : dt_cfl;
+    st->last = last;
+}
+
+// Close a full step: advance t, count it, swap the Euler ping-pong buffers,
+// clear the phi-dependent alpha components, move to the next tau segment
+// when this one is done, and set the loop and snapshot conditions.
+__global__ void k_advance(SolveState *st, int swap, unsigned dyn_mask, cudaGraphConditionalHandle h_loop,
+                          cudaGraphConditionalHandle h_snap, int keep)
+{
+    st->t = st->last ? st->t_end : __dadd_rn(st->t, st->dt);
+    st->steps += 1;
+    if (swap) {
+        float *tmp = st->cur;
+        st->cur = st->nxt;
+        st->nxt = tmp;
+    }
+    for (int d = 0; d < 8; ++d)
+        if (dyn_mask & (1u << d)) {
+            st->alpha_bits[0][d] = 0u;
+            st->alpha_bits[1][d] = 0u;
+        }
+    int go = 1, snap = 0;
+    if (!(__dsub_rn(st->t_end, st->t) > __dmul_rn(1e-12, st->t_end))) {
+        snap = keep;
+        st->snap_index = st->seg + 1;
+        st->seg += 1;
+        if (st->seg >= st->n_seg)
+            go = 0;
+        else
+            st->t_end = st->tau[st->seg + 1];
+    }
+    if (st->flags) go = 0;
+    if (go && st->steps >= st->max_steps) {
+        st->flags |= FLAG_TIMEOUT;
+        go = 0;
+    }
+    cudaGraphSetConditional(h_loop, go);
+    if (keep) cudaGraphSetConditional(h_snap, snap);
+}
+
+__global__ void k_snapshot(SolveState *st, int total)
+{
+    const float *src = st->cur;
+    float *dst = st->snapshots + (long long)st->snap_index * total;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+// ---------------------------------------------------------------------------
+// grid object
+// ---------------------------------------------------------------------------
+// Kernel arguments (grid and dynamics descriptors) are frozen into the graph
+// when it is captured, so any change of scheme or dynamics rebuilds it.
+struct GraphKey {
+    int order = 0, time_order = 0, brt = 0, keep = 0;
+    long long dyn_version = -1;
+    bool operator==(const GraphKey &o) const
+    {
+        return order == o.order && time_order == o.time_order && brt == o.brt && keep == o.keep &&
+               dyn_version == o.dyn_version;
+    }
+};
+
+struct odp_grid {
+    int ndim = 0;
+    int n[ODP_MAXD] = {0};
+    double lo[ODP_MAXD] = {0}, hi[ODP_MAXD] = {0};
+    int periodic[ODP_MAXD] = {0};
+    int64_t total = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+
+    float *phi_a = nullptr, *phi_b = nullptr, *l = nullptr;
+    float *tables = nullptr;          // all node-coordinate and trig tables
+    SolveState *state = nullptr;
+    double *tau = nullptr;
+    int tau_cap = 0;
+    float *snapshots = nullptr;
+    int snap_cap = 0;
+
+    GridDesc desc{};
+    DynDesc dyn{};
+    bool has_dyn = false, has_target = false, solved = false;
+    long long dyn_version = 0;
+    int64_t max_steps = 10000000;
+    int n_tau = 0, keep = 0, time_order = 1, order = 1, brt = 0;
+    bool timed = false;
+
+    cudaStream_t capture_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    GraphKey key;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int64_t launches_per_step = 0;
+};
+
+static void release(odp_grid *g)
+{
+    if (!g) return;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->capture_stream) cudaStreamDestroy(g->capture_stream);
+    if (g->ev0) cudaEventDestroy(g->ev0);
+    if (g->ev1) cudaEventDestroy(g->ev1);
+    cudaFree(g->phi_a);
+    cudaFree(g->phi_b);
+    cudaFree(g->l);
+    cudaFree(g->tables);
+    cudaFree(g->state);
+    cudaFree(g->tau);
+    cudaFree(g->snapshots);
+    delete g;
+}
+
+extern "C" const char *odp_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char *odp_version(void) { return "libodp 0.1 (sm_103a)"; }
+
+extern "C" int64_t odp_grid_points(const odp_grid *g) { return g ? g->total : 0; }
+
+extern "C" odp_status odp_grid_create(int ndim, const int32_t *n, const double *lo, const double *hi,
+                                      const uint8_t *periodic, void *cuda_stream, odp_grid **out)
+{
+    if (!out) return fail(ODP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (ndim < 1 || ndim > ODP_MAXD) return fail(ODP_EINVAL, "ndim %d outside [1, %d]", ndim, ODP_MAXD);
+    if (!n || !lo || !hi || !periodic) return fail(ODP_EINVAL, "NULL grid description");
+    int64_t total = 1;
+    for (int d = 0; d < ndim; ++d) {
+        const int need = periodic[d] ? 1 : 2;
+        if (n[d] < need) return fail(ODP_EINVAL, "axis %d: n = %d < %d", d, n[d], need);
+        if (!(hi[d] > lo[d]) || !std::isfinite(lo[d]) || !std::isfinite(hi[d]))
+            return fail(ODP_EINVAL, "axis %d: need finite lo < hi", d);
+        total *= n[d];
+        if (total >= (int64_t(1) << 31)) return fail(ODP_EINVAL, "grid has 2^31 nodes or more");
+    }
+    odp_grid *g = new (std::nothrow) odp_grid();
+    if (!g) return fail(ODP_ENOMEM, "host allocation failed");
+    g->ndim = ndim;
+    g->total = total;
+    g->stream = static_cast<cudaStream_t>(cuda_stream);
+    for (int d = 0; d < ndim; ++d) {
+        g->n[d] = n[d];
+        g->lo[d] = lo[d];
+        g->hi[d] = hi[d];
+        g->periodic[d] = periodic[d] ? 1 : 0;
+    }
+    auto bail = [&](odp_status rc) {
+        release(g);
+        return rc;
+    };
+    odp_status rc;
+#define ODP_TRY(call)                    \
+    do {                                 \
+        cudaError_t e_ = (call);         \
+        if (e_ != cudaSuccess) {         \
+            rc = fail(e_ == cudaErrorMemoryAllocation ? ODP_ENOMEM : ODP_ECUDA, "%s: %s", #call, \
+                      cudaGetErrorString(e_)); \
+            return bail(rc);             \
+        }                                \
+    } while (0)
+    ODP_TRY(cudaGetDevice(&g->device));
+    const size_t bytes = size_t(total) * sizeof(float);
+    ODP_TRY(cudaMalloc(&g->phi_a, bytes));
+    ODP_TRY(cudaMalloc(&g->phi_b, bytes));
+    ODP_TRY(cudaMalloc(&g->l, bytes));
+    ODP_TRY(cudaMalloc(&g->state, sizeof(SolveState)));
+    ODP_TRY(cudaStreamCreateWithFlags(&g->capture_stream, cudaStreamNonBlocking));
+    ODP_TRY(cudaEventCreate(&g->ev0));
+    ODP_TRY(cudaEventCreate(&g->ev1));
+
+    // node tables: coordinates of every axis, then cos / sin of every axis
+    // (only the angle axis is used); float64 on the host, rounded once.
+    int64_t tab_len = 0;
+    for (int d = 0; d < ndim; ++d) tab_len += 3 * int64_t(n[d]);
+    std::vector<float> tab(static_cast<size_t>(tab_len));
+    GridDesc &D = g->desc;
+    D.ndim = ndim;
+    D.total = int(total);
+    int64_t off = 0;
+    std::vector<int64_t> coord_off(ndim), trig_off(ndim);
+    for (int d = 0; d < ndim; ++d) {
+        const double h = periodic[d] ? (hi[d] - lo[d]) / double(n[d]) : (hi[d] - lo[d]) / double(n[d] - 1);
+        D.n[d] = n[d];
+        D.periodic[d] = periodic[d] ? 1 : 0;
+        D.dz[d] = h;
+        D.inv_dz[d] = float(1.0 / h);
+        D.div[d] = make_fastdiv(uint32_t(n[d]));
+        coord_off[d] = off;
+        for (int i = 0; i < n[d]; ++i) tab[size_t(off + i)] = float(lo[d] + double(i) * h);
+        off += n[d];
+        trig_off[d] = off;
+        for (int i = 0; i < n[d]; ++i) {
+            const double z = lo[d] + double(i) * h;
+            tab[size_t(off + i)] = float(std::cos(z));
+            tab[size_t(off + n[d] + i)] = float(std::sin(z));
+        }
+        off += 2 * int64_t(n[d]);
+    }
+    int64_t s = 1;
+    for (int d = ndim - 1; d >= 0; --d) {
+        D.stride[d] = int(s);
+        s *= n[d];
+    }
+    ODP_TRY(cudaMalloc(&g->tables, size_t(tab_len) * sizeof(float)));
+    ODP_TRY(cudaMemcpy(g->tables, tab.data(), size_t(tab_len) * sizeof(float), cudaMemcpyHostToDevice));
+    for (int d = 0; d < ndim; ++d) D.coord[d] = g->tables + coord_off[d];
+    // the trig tables of the angle axis are bound by odp_set_dynamics
+    D.cos_tab = nullptr;
+    D.sin_tab = nullptr;
+    g->dyn.angle_axis = -1;
+#undef ODP_TRY
+    *out = g;
+    return ODP_OK;
+}
+
+extern "C" odp_status odp_grid_destroy(odp_grid *g)
+{
+    release(g);
+    return ODP_OK;
+}
+
+static int64_t trig_offset(const odp_grid *g, int axis)
+{
+    int64_t off = 0;
+    for (int d = 0; d < axis; ++d) off += 3 * int64_t(g->n[d]);
+    return off + g->n[axis];
+}
+
+extern "C" odp_status odp_set_dynamics(odp_grid *g, odp_dyn kind, const double *params, int n_params,
+                                       odp_mode u_mode, odp_mode d_mode)
+{
+    if (!g) return fail(ODP_EINVAL, "grid is NULL");
+    if ((u_mode != ODP_MIN && u_mode != ODP_MAX) || (d_mode != ODP_MIN && d_mode != ODP_MAX))
+        return fail(ODP_EINVAL, "input modes must be ODP_MIN or ODP_MAX");
+    int need = 0, angle = -1, nd_req = -1;
+    switch (kind) {
+    case ODP_DYN_SINGLE_INT: need = 1; break;
+    case ODP_DYN_ADVECTION: need = g->ndim; break;
+    case ODP_DYN_DUBINS3D: need = 2; angle = 2; nd_req = 3; break;
+    case ODP_DYN_DUBINSCAR4D: need = 2; angle = 3; nd_req = 4; break;
+    case ODP_DYN_REL6D: need = 4; angle = 2; nd_req = 6; break;
+    default: return fail(ODP_EINVAL, "unknown dynamics %d", int(kind));
+    }
+    if (nd_req > 0 && g->ndim != nd_req)
+        return fail(ODP_EINVAL, "dynamics %d needs %d dimensions, grid has %d", int(kind), nd_req, g->ndim);
+    if (n_params < need || n_params > 8 || (need > 0 && !params))
+        return fail(ODP_EINVAL, "dynamics %d needs %d parameters, got %d", int(kind), need, n_params);
+    for (int k = 0; k < n_params; ++k) {
+        if (!std::isfinite(params[k])) return fail(ODP_EINVAL, "parameter %d is not finite", k);
+        if (kind != ODP_DYN_ADVECTION && params[k] < 0.0)
+            return fail(ODP_EINVAL, "parameter %d (a bound or speed) is negative", k);
+    }
+    if (angle >= 0 && !g->periodic[angle])
+        return fail(ODP_EINVAL, "axis %d holds an angle and must be periodic", angle);
+    DynDesc dy{};
+    dy.kind = int(kind);
+    dy.umode = int(u_mode);
+    dy.dmode = int(d_mode);
+    dy.angle_axis = angle;
+    for (int k = 0; k < n_params; ++k) dy.prm[k] = float(params[k]);
+    g->dyn = dy;
+    g->dyn_version += 1;
+    if (angle >= 0) {
+        const int64_t off = trig_offset(g, angle);
+        g->desc.cos_tab = g->tables + off;
+        g->desc.sin_tab = g->tables + off + g->n[angle];
+    }
+    g->has_dyn = true;
+    return ODP_OK;
+}
+
+extern "C" odp_status odp_set_target(odp_grid *g, const float *l, int64_t n_elems, int on_device)
+{
+    if (!g || !l) return fail(ODP_EINVAL, "NULL argument");
+    if (n_elems != g->total) return fail(ODP_EINVAL, "target has %lld values, grid has %lld",
+                                         (long long)n_elems, (long long)g->total);
+    ODP_CUDA(cudaMemcpyAsync(g->l, l, size_t(n_elems) * sizeof(float),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));
+    g->has_target = true;
+    return ODP_OK;
+}
+
+extern "C" odp_status odp_set_step_limit(odp_grid *g, int64_t max_steps)
+{
+    if (!g || max_steps < 1) return fail(ODP_EINVAL, "need a grid and max_steps >= 1");
+    g->max_steps = max_steps;
+    return ODP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the time-loop graph
+// ---------------------------------------------------------------------------
+static cudaError_t launch_stage_any(odp_grid *g, int stage)
+{
+    const GridDesc &D = g->desc;
+    switch (g->dyn.kind) {
+    case DYN_SINGLE_INT:
+    case DYN_ADVECTION:
+        return launch_stage_si(g->ndim, D, g->dyn, g->state, g->l, g->order, stage, g->brt, g->capture_stream);
+    case DYN_DUBINS3D:
+    case DYN_DUBINSCAR4D:
+        return launch_stage_dubins(g->ndim, D, g->dyn, g->state, g->l, g->order, stage, g->brt,
+                                   g->capture_stream);
+    default:
+        return launch_stage_rel6d(D, g->dyn, g->state, g->l, g->order, stage, g->brt, g->capture_stream);
+    }
+}
+
+static cudaError_t launch_alpha_static_any(odp_grid *g, cudaStream_t s)
+{
+    switch (g->dyn.kind) {
+    case DYN_SINGLE_INT:
+    case DYN_ADVECTION: return launch_alpha_static_si(g->ndim, g->desc, g->dyn, g->state, s);
+    case DYN_DUBINS3D:
+    case DYN_DUBINSCAR4D: return launch_alpha_static_dubins(g->ndim, g->desc, g->dyn, g->state, s);
+    default: return launch_alpha_static_rel6d(g->desc, g->dyn, g->state, s);
+    }
+}
+
+static unsigned dynamic_alpha_mask(const odp_grid *g) { return g->dyn.kind == DYN_REL6D ? (1u << 2) : 0u; }
+
+// Capture the body of the time loop into `body` and add the snapshot IF node.
+static odp_status build_graph(odp_grid *g)
+{
+    if (g->exec) {
+        ODP_CUDA(cudaStreamSynchronize(g->stream));
+        cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
+    }
+    if (g->graph) {
+        cudaGraphDestroy(g->graph);
+        g->graph = nullptr;
+    }
+    ODP_CUDA(cudaGraphCreate(&g->graph, 0));
+    cudaGraphConditionalHandle h_loop;
+    ODP_CUDA(cudaGraphConditionalHandleCreate(&h_loop, g->graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams wp{};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = h_loop;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t loop_node;
+    ODP_CUDA(cudaGraphAddNode(&loop_node, g->graph, nullptr, nullptr, 0, &wp));
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+
+    cudaGraphConditionalHandle h_snap = 0;
+    if (g->keep) ODP_CUDA(cudaGraphConditionalHandleCreate(&h_snap, body, 0, 0));
+
+    const bool dyn_alpha = g->dyn.kind == DYN_REL6D;
+    cudaStream_t s = g->capture_stream;
+    ODP_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    int64_t launches = 0;
+    cudaError_t e = cudaSuccess;
+    if (dyn_alpha) {
+        e = launch_alpha_dynamic_rel6d(g->desc, g->dyn, g->state, g->order, 0, s);
+        ++launches;
+    }
+    if (e == cudaSuccess) {
+        k_dt<<<1, 1, 0, s>>>(g->state, g->desc);
+        ++launches;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        if (g->time_order == 1) {
+            e = launch_stage_any(g, 0);
+            ++launches;
+        } else {
+            e = launch_stage_any(g, 1);
+            ++launches;
+            if (e == cudaSuccess && dyn_alpha) {
+                e = launch_alpha_dynamic_rel6d(g->desc, g->dyn, g->state, g->order, 1, s);
+                ++launches;
+            }
+            if (e == cudaSuccess) {
+                e = launch_stage_any(g, 2);
+                ++launches;
+            }
+        }
+    }
+    if (e == cudaSuccess) {
+        k_advance<<<1, 1, 0, s>>>(g->state, g->time_order == 1 ? 1 : 0, dynamic_alpha_mask(g), h_loop,
+                                  h_snap, g->keep);
+        ++launches;
+        e = cudaGetLastError();
+    }
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    std::vector<cudaGraphNode_t> leaf;
+    if (e == cudaSuccess) {
+        e = cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
+        if (e == cudaSuccess) leaf.assign(deps, deps + ndeps);
+    }
+    cudaGraph_t captured = body;
+    cudaError_t e2 = cudaStreamEndCapture(s, &captured);
+    if (e != cudaSuccess) return fail(ODP_ECUDA, "capturing the time loop: %s", cudaGetErrorString(e));
+    if (e2 != cudaSuccess) return fail(ODP_ECUDA, "ending the capture: %s", cudaGetErrorString(e2));
+
+    if (g->keep) {
+        cudaGraphNodeParams ip{};
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = h_snap;
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        cudaGraphNode_t if_node;
+        ODP_CUDA(cudaGraphAddNode(&if_node, body, leaf.data(), nullptr, leaf.size(), &ip));
+        cudaGraph_t snap_body = ip.conditional.phGraph_out[0];
+        ODP_CUDA(cudaStreamBeginCaptureToGraph(s, snap_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        const int blocks = int(std::min<int64_t>((g->total + 255) / 256, 152 * 8));
+        k_snapshot<<<blocks, 256, 0, s>>>(g->state, int(g->total));
+        e = cudaGetLastError();
+        cudaGraph_t cap2 = snap_body;
+        e2 = cudaStreamEndCapture(s, &cap2);
+        if (e != cudaSuccess || e2 != cudaSuccess)
+            return fail(ODP_ECUDA, "capturing the snapshot copy: %s / %s", cudaGetErrorString(e),
+                        cudaGetErrorString(e2));
+    }
+    ODP_CUDA(cudaGraphInstantiate(&g->exec, g->graph, 0));
+    g->launches_per_step = launches;
+    return ODP_OK;
+}
+
+extern "C" odp_status odp_solve_hjb(odp_grid *g, const double *tau, int n_tau, odp_set set,
+                                    int space_order, int time_order, double cfl, int keep_snapshots,
+                                    odp_solve_stats *stats)
+{
+    if (!g) return fail(ODP_EINVAL, "grid is NULL");
+    if (!g->has_dyn) return fail(ODP_ESTATE, "odp_set_dynamics was not called");
+    if (!g->has_target) return fail(ODP_ESTATE, "odp_set_target was not called");
+    if (!tau || n_tau < 2) return fail(ODP_EINVAL, "need n_tau >= 2");
+    if (tau[0] != 0.0) return fail(ODP_EINVAL, "tau[0] must be 0");
+    for (int k = 1; k < n_tau; ++k)
+        if (!(tau[k] > tau[k - 1]) || !std::isfinite(tau[k]))
+            return fail(ODP_EINVAL, "tau must be finite and strictly increasing");
+    if (set != ODP_BRS && set != ODP_BRT) return fail(ODP_EINVAL, "set must be ODP_BRS or ODP_BRT");
+    if (space_order != 1 && space_order != 2) return fail(ODP_EINVAL, "space_order must be 1 or 2");
+    if (time_order != 1 && time_order != 2) return fail(ODP_EINVAL, "time_order must be 1 or 2");
+    if (!(cfl > 0.0 && cfl <= 1.0)) return fail(ODP_EINVAL, "cfl must lie in (0, 1]");
+
+    cudaStream_t st = g->stream;
+    if (n_tau > g->tau_cap) {
+        cudaFree(g->tau);
+        g->tau = nullptr;
+        ODP_CUDA(cudaMalloc(&g->tau, sizeof(double) * size_t(n_tau)));
+        g->tau_cap = n_tau;
+    }
+    if (keep_snapshots && n_tau > g->snap_cap) {
+        cudaStreamSynchronize(st);
+        cudaFree(g->snapshots);
+        g->snapshots = nullptr;
+        g->snap_cap = 0;
+        ODP_CUDA(cudaMalloc(&g->snapshots, sizeof(float) * size_t(n_tau) * size_t(g->total)));
+        g->snap_cap = n_tau;
+    }
+    g->order = space_order;
+    g->time_order = time_order;
+    g->brt = (set == ODP_BRT) ? 1 : 0;
+    g->keep = keep_snapshots ? 1 : 0;
+    g->n_tau = n_tau;
+    GraphKey key;
+    key.order = space_order;
+    key.time_order = time_order;
+    key.brt = g->brt;
+    key.keep = g->keep;
+    key.dyn_version = g->dyn_version;
+    if (!g->exec || !(key == g->key)) {
+        odp_status rc = build_graph(g);
+        if (rc != ODP_OK) return rc;
+        g->key = key;
+    }
+
+    // state of the solve; pageable source, so the copy is staged at once
+    SolveState h{};
+    h.t = 0.0;
+    h.t_end = tau[1];
+    h.dt = 0.0;
+    h.cfl = cfl;
+    h.steps = 0;
+    h.max_steps = g->max_steps;
+    h.seg = 0;
+    h.n_seg = n_tau - 1;
+    h.flags = 0;
+    h.cur = g->phi_a;
+    h.nxt = g->phi_b;
+    h.tau = g->tau;
+    h.snapshots = g->keep ? g->snapshots : nullptr;
+    const size_t bytes = size_t(g->total) * sizeof(float);
+    ODP_CUDA(cudaMemcpyAsync(g->tau, tau, sizeof(double) * size_t(n_tau), cudaMemcpyHostToDevice, st));
+    ODP_CUDA(cudaMemcpyAsync(g->state, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+    ODP_CUDA(cudaMemcpyAsync(g->phi_a, g->l, bytes, cudaMemcpyDeviceToDevice, st));
+    if (g->keep) ODP_CUDA(cudaMemcpyAsync(g->snapshots, g->l, bytes, cudaMemcpyDeviceToDevice, st));
+    ODP_CUDA(launch_alpha_static_any(g, st));
+    g->timed = stats != nullptr;
+    if (g->timed) ODP_CUDA(cudaEventRecord(g->ev0, st));
+    ODP_CUDA(cudaGraphLaunch(g->exec, st));
+    if (g->timed) ODP_CUDA(cudaEventRecord(g->ev1, st));
+    g->solved = true;
+    if (stats) return odp_solve_status(g, stats);
+    return ODP_OK;
+}
+
+static odp_status read_state(odp_grid *g, SolveState *h)
+{
+    ODP_CUDA(cudaMemcpyAsync(h, g->state, sizeof(*h), cudaMemcpyDeviceToHost, g->stream));
+    ODP_CUDA(cudaStreamSynchronize(g->stream));
+    return ODP_OK;
+}
+
+static odp_status status_of(const SolveState &h)
+{
+    if (h.flags & FLAG_NONFINITE) return fail(ODP_ENUMERIC, "a non-finite value appeared in the solve");
+    if (h.flags & FLAG_TIMEOUT)
+        return fail(ODP_ETIMEOUT, "step limit %lld reached at t = %g", (long long)h.max_steps, h.t);
+    return ODP_OK;
+}
+
+extern "C" odp_status odp_solve_status(odp_grid *g, odp_solve_stats *stats)
+{
+    if (!g) return fail(ODP_EINVAL, "grid is NULL");
+    if (!g->solved) return fail(ODP_ESTATE, "no solve was issued on this grid");
+    SolveState h{};
+    odp_status rs = read_state(g, &h);
+    if (rs != ODP_OK) return rs;
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->steps = h.steps;
+        stats->last_dt = h.dt;
+        stats->t_final = h.t;
+        const int slot = g->time_order == 2 ? 1 : 0;
+        for (int d = 0; d < g->ndim; ++d) memcpy(&stats->alpha[d], &h.alpha_bits[slot][d], sizeof(float));
+        if (g->timed) {
+            float ms = 0.0f;
+            ODP_CUDA(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+            stats->device_ms = ms;
+        }
+        // algorithmic HBM bytes per node per step: every stage reads phi once
+        // and writes its result; stage 2 also reads phi^n; the last stage of a
+        // tube reads l; Rel6D adds one read of phi per stage for its alpha.
+        const double per_stage_rw = 8.0;
+        double b = (g->time_order == 1) ? per_stage_rw : (2 * per_stage_rw + 4.0);
+        if (g->brt) b += 4.0;
+        if (g->dyn.kind == DYN_REL6D) b += 4.0 * g->time_order;
+        stats->bytes = b * double(g->total) * double(h.steps);
+        stats->launches = g->launches_per_step * h.steps;
+    }
+    return status_of(h);
+}
+
+extern "C" odp_status odp_value_readback(odp_grid *g, int tau_index, float *dst, int64_t n_elems,
+                                         int on_device)
+{
+    if (!g || !dst) return fail(ODP_EINVAL, "NULL argument");
+    if (!g->solved) return fail(ODP_ESTATE, "no solve was issued on this grid");
+    if (n_elems != g->total) return fail(ODP_EINVAL, "destination holds %lld values, grid has %lld",
+                                         (long long)n_elems, (long long)g->total);
+    if (tau_index < -1 || tau_index >= g->n_tau) return fail(ODP_EINVAL, "tau_index %d out of range", tau_index);
+    if (tau_index == g->n_tau - 1) tau_index = -1;
+    if (tau_index >= 0 && !g->keep) return fail(ODP_EINVAL, "snapshots were not kept");
+    SolveState h{};
+    odp_status rs = read_state(g, &h);
+    if (rs != ODP_OK) return rs;
+    const float *src = (tau_index >= 0) ? g->snapshots + size_t(tau_index) * size_t(g->total) : h.cur;
+    ODP_CUDA(cudaMemcpyAsync(dst, src, size_t(n_elems) * sizeof(float),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
+    ODP_CUDA(cudaStreamSynchronize(g->stream));
+    return status_of(h);
+}
+
+extern "C" odp_status odp_time_stage(odp_grid *g, int stage, int reps, double *ms_out)
+{
+    if (!g || !ms_out) return fail(ODP_EINVAL, "NULL argument");
+    if (!g->solved || !g->exec) return fail(ODP_ESTATE, "no solve was issued on this grid");
+    if (reps < 1) return fail(ODP_EINVAL, "reps must be >= 1");
+    if ((g->time_order == 1) != (stage == 0) || stage < 0 || stage > 2)
+        return fail(ODP_EINVAL, "stage %d does not belong to a time order %d solve", stage, g->time_order);
+    cudaStream_t s = g->capture_stream;
+    ODP_CUDA(cudaStreamSynchronize(g->stream));
+    ODP_CUDA(cudaEventRecord(g->ev0, s));
+    for (int r = 0; r < reps; ++r) {
+        cudaError_t e = launch_stage_any(g, stage);
+        if (e != cudaSuccess) return fail(ODP_ECUDA, "stage launch: %s", cudaGetErrorString(e));
+    }
+    ODP_CUDA(cudaEventRecord(g->ev1, s));
+    ODP_CUDA(cudaEventSynchronize(g->ev1));
+    float ms = 0.0f;
+    ODP_CUDA(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+    *ms_out = double(ms) / reps;
+    g->timed = false;
+    return ODP_OK;
+}

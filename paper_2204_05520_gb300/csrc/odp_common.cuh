@@ -1,0 +1,92 @@
+// odp_common.cuh -- device-side data layout shared by the libodp kernels.
+//
+// A grid is a dense C-order float32 array (last axis fastest).  Kernels get a
+// GridDesc by value (sizes, strides, reciprocal spacings, per-axis node
+// tables) and a DynDesc (model id, input modes, parameters).  The mutable
+// state of a solve (t, dt, step counters, alpha, ping-pong pointers, error
+// flags) lives in one SolveState in device memory so that a captured CUDA
+// graph can run the whole time loop without the host.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define ODP_MAXD 6
+
+namespace odp {
+
+enum DynKind { DYN_SINGLE_INT = 0, DYN_DUBINS3D = 1, DYN_DUBINSCAR4D = 2, DYN_REL6D = 3, DYN_ADVECTION = 4 };
+enum Mode { MODE_MIN = 0, MODE_MAX = 1 };
+
+// Error flags raised on the device.
+enum : int { FLAG_NONFINITE = 1, FLAG_TIMEOUT = 2 };
+
+// Unsigned division by an invariant divisor through a multiply-high
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (umulhi(m, n) + n) >> l for
+// every n < 2^31.
+struct FastDiv {
+    uint32_t d, m, l;
+};
+
+inline FastDiv make_fastdiv(uint32_t d)
+{
+    FastDiv f;
+    f.d = d;
+    uint32_t l = 0;
+    while ((uint64_t(1) << l) < d) ++l;
+    f.l = l;
+    f.m = uint32_t(((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1);
+    return f;
+}
+
+__device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv &f)
+{
+    return (__umulhi(f.m, n) + n) >> f.l;
+}
+
+struct GridDesc {
+    int ndim;
+    int total;                   // number of nodes (< 2^31)
+    int n[ODP_MAXD];
+    int stride[ODP_MAXD];        // C order: stride[ndim-1] == 1
+    int periodic[ODP_MAXD];
+    float inv_dz[ODP_MAXD];      // 1 / node spacing
+    double dz[ODP_MAXD];         // node spacing (float64, for the CFL step)
+    FastDiv div[ODP_MAXD];       // divisors n[d] for unflattening
+    const float *coord[ODP_MAXD];  // node coordinates of each axis (device)
+    const float *cos_tab;        // cos / sin of the angle axis nodes (device)
+    const float *sin_tab;
+};
+
+struct DynDesc {
+    int kind;
+    int umode, dmode;
+    int angle_axis;              // axis holding the heading angle, -1 if none
+    float prm[8];
+};
+
+// alpha is kept as the bit pattern of a non-negative float so that the
+// grid-wide max is an atomicMax on unsigned integers.
+struct SolveState {
+    double t;                    // look-back time reached
+    double t_end;                // end of the current tau segment
+    double dt;                   // step of the current time step
+    double cfl;
+    long long steps;             // full steps taken over all segments
+    long long max_steps;
+    int seg;                     // current tau segment
+    int n_seg;
+    int last;                    // current step is the clipped last step of a segment
+    int flags;                   // FLAG_* bits
+    int snap_index;              // snapshot to write when the IF body runs
+    int pad;
+    float *cur;                  // phi^n
+    float *nxt;                  // phi^{n+1} (Euler) or phi^1 (RK2)
+    const double *tau;           // device copy of the tau schedule
+    float *snapshots;            // n_tau * total floats, or nullptr
+    unsigned alpha_bits[2][8];   // per stage slot (0: stage 1, 1: stage 2)
+};
+
+}  // namespace odp

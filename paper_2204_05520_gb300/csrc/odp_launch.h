@@ -1,0 +1,30 @@
+// odp_launch.h -- host-side launchers of the per-model kernel instantiations.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "odp_common.cuh"
+
+namespace odp {
+
+// One fused stage pass (K2) over the whole grid.
+cudaError_t launch_stage_si(int nd, const GridDesc &g, const DynDesc &dy, SolveState *st,
+                            const float *l, int order, int stage, int brt, cudaStream_t s);
+cudaError_t launch_stage_dubins(int nd, const GridDesc &g, const DynDesc &dy, SolveState *st,
+                                const float *l, int order, int stage, int brt, cudaStream_t s);
+cudaError_t launch_stage_rel6d(const GridDesc &g, const DynDesc &dy, SolveState *st,
+                               const float *l, int order, int stage, int brt, cudaStream_t s);
+
+// Grid-wide max of the phi-independent alpha components (K1, once per solve).
+cudaError_t launch_alpha_static_si(int nd, const GridDesc &g, const DynDesc &dy, SolveState *st,
+                                   cudaStream_t s);
+cudaError_t launch_alpha_static_dubins(int nd, const GridDesc &g, const DynDesc &dy,
+                                       SolveState *st, cudaStream_t s);
+cudaError_t launch_alpha_static_rel6d(const GridDesc &g, const DynDesc &dy, SolveState *st,
+                                      cudaStream_t s);
+
+// Grid-wide max of the Rel6D heading-rate alpha of cur (slot 0) or nxt (slot 1).
+cudaError_t launch_alpha_dynamic_rel6d(const GridDesc &g, const DynDesc &dy, SolveState *st,
+                                       int order, int slot, cudaStream_t s);
+
+}  // namespace odp

@@ -1,0 +1,237 @@
+"""ctypes binding of libodp (include/odp.h).
+
+Each function has the name of the C entry point without the ``odp_`` prefix
+and only marshals arguments: shapes and dtypes are checked, torch tensors are
+passed by ``data_ptr()`` (device) or as host buffers, numpy arrays as host
+buffers, and a negative status raises :class:`OdpError`.  All arithmetic of
+the solve runs in the library's CUDA kernels; there is no other code path.
+If the library has not been built, :func:`load` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, ENUMERIC, EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
+DYN = {"single_integrator": 0, "dubins3d": 1, "dubinscar4d": 2, "rel6d": 3, "advection": 4}
+MODE = {"min": 0, "max": 1}
+SET = {"brs": 0, "brt": 1}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class OdpError(RuntimeError):
+    def __init__(self, code: int, where: str, message: str):
+        super().__init__("%s failed (%d): %s" % (where, code, message))
+        self.code = code
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("last_dt", ctypes.c_double),
+                ("t_final", ctypes.c_double), ("alpha", ctypes.c_float * 8),
+                ("device_ms", ctypes.c_double), ("bytes", ctypes.c_double),
+                ("launches", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {"steps": self.steps, "last_dt": self.last_dt, "t_final": self.t_final,
+                "alpha": list(self.alpha), "device_ms": self.device_ms, "bytes": self.bytes,
+                "launches": self.launches}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libodp.so (built by ``__graft_entry__.build()`` or ``_build.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError("libodp.so is not built (%s); run __graft_entry__.build()" % path)
+        lib = ctypes.CDLL(path)
+        P, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "odp_last_error": ([], ctypes.c_char_p),
+            "odp_version": ([], ctypes.c_char_p),
+            "odp_grid_create": ([i32, P, P, P, P, P, P], i32),
+            "odp_grid_destroy": ([P], i32),
+            "odp_grid_points": ([P], i64),
+            "odp_set_dynamics": ([P, i32, P, i32, i32, i32], i32),
+            "odp_set_target": ([P, P, i64, i32], i32),
+            "odp_set_step_limit": ([P, i64], i32),
+            "odp_solve_hjb": ([P, P, i32, i32, i32, i32, f64, i32, P], i32),
+            "odp_solve_status": ([P, P], i32),
+            "odp_value_readback": ([P, i32, P, i64, i32], i32),
+            "odp_time_stage": ([P, i32, i32, P], i32),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise OdpError(rc, where, load().odp_last_error().decode())
+    return rc
+
+
+def last_error() -> str:
+    return load().odp_last_error().decode()
+
+
+def version() -> str:
+    return load().odp_version().decode()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _buffer(x, n_elems: int, writable: bool):
+    """(pointer, on_device) of a float32 C-contiguous tensor or array."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float32 or not x.flags["C_CONTIGUOUS"] or x.size != n_elems:
+            raise ValueError("need a C-contiguous float32 array of %d values" % n_elems)
+        if writable and not x.flags["WRITEABLE"]:
+            raise ValueError("array is read-only")
+        return ctypes.c_void_p(x.ctypes.data), 0
+    import torch
+
+    if not isinstance(x, torch.Tensor):
+        raise TypeError("need a numpy array or a torch tensor")
+    if x.dtype != torch.float32 or not x.is_contiguous() or x.numel() != n_elems:
+        raise ValueError("need a contiguous float32 tensor of %d values" % n_elems)
+    return ctypes.c_void_p(x.data_ptr()), 1 if x.is_cuda else 0
+
+
+def grid_create(n, lo, hi, periodic, stream=None):
+    lib = load()
+    nd = len(n)
+    n_a = (ctypes.c_int32 * nd)(*[int(v) for v in n])
+    lo_a = (ctypes.c_double * nd)(*[float(v) for v in lo])
+    hi_a = (ctypes.c_double * nd)(*[float(v) for v in hi])
+    per_a = (ctypes.c_uint8 * nd)(*[1 if p else 0 for p in periodic])
+    out = ctypes.c_void_p()
+    _check(lib.odp_grid_create(nd, n_a, lo_a, hi_a, per_a, _stream_ptr(stream), ctypes.byref(out)),
+           "odp_grid_create")
+    return out
+
+
+def grid_destroy(g):
+    _check(load().odp_grid_destroy(g), "odp_grid_destroy")
+
+
+def grid_points(g) -> int:
+    return int(load().odp_grid_points(g))
+
+
+def set_dynamics(g, kind, params, u_mode="min", d_mode="max"):
+    k = DYN[kind] if isinstance(kind, str) else int(kind)
+    prm = (ctypes.c_double * max(1, len(params)))(*[float(v) for v in params])
+    _check(load().odp_set_dynamics(g, k, prm, len(params), MODE[u_mode], MODE[d_mode]),
+           "odp_set_dynamics")
+
+
+def set_target(g, l):
+    n = grid_points(g)
+    ptr, dev = _buffer(l, n, writable=False)
+    _check(load().odp_set_target(g, ptr, n, dev), "odp_set_target")
+
+
+def set_step_limit(g, max_steps: int):
+    _check(load().odp_set_step_limit(g, int(max_steps)), "odp_set_step_limit")
+
+
+def solve_hjb(g, tau, set_kind="brt", space_order=1, time_order=1, cfl=0.8, keep_snapshots=False,
+              stats=False):
+    """Enqueue a solve; with ``stats`` wait for it and return its statistics."""
+    t = (ctypes.c_double * len(tau))(*[float(v) for v in tau])
+    st = SolveStats() if stats else None
+    _check(load().odp_solve_hjb(g, t, len(tau), SET[set_kind], int(space_order), int(time_order),
+                                float(cfl), 1 if keep_snapshots else 0,
+                                ctypes.byref(st) if st is not None else None), "odp_solve_hjb")
+    return st.as_dict() if st is not None else None
+
+
+def solve_status(g) -> dict:
+    st = SolveStats()
+    _check(load().odp_solve_status(g, ctypes.byref(st)), "odp_solve_status")
+    return st.as_dict()
+
+
+def value_readback(g, out, tau_index: int = -1):
+    n = grid_points(g)
+    ptr, dev = _buffer(out, n, writable=True)
+    _check(load().odp_value_readback(g, int(tau_index), ptr, n, dev), "odp_value_readback")
+    return out
+
+
+def time_stage(g, stage: int, reps: int = 20) -> float:
+    """Mean device milliseconds of one launch of the fused stage kernel."""
+    ms = ctypes.c_double(0.0)
+    _check(load().odp_time_stage(g, int(stage), int(reps), ctypes.byref(ms)), "odp_time_stage")
+    return ms.value
+
+
+class Grid:
+    """Owning wrapper of an odp_grid handle (one problem on one stream)."""
+
+    def __init__(self, n, lo, hi, periodic, stream=None):
+        self.shape = tuple(int(v) for v in n)
+        self.handle = grid_create(n, lo, hi, periodic, stream)
+
+    @classmethod
+    def for_problem(cls, problem, stream=None) -> "Grid":
+        g = cls(problem.n, problem.lo, problem.hi, problem.periodic, stream)
+        set_dynamics(g.handle, problem.dynamics, problem.params, problem.u_mode, problem.d_mode)
+        return g
+
+    def close(self):
+        if self.handle is not None:
+            grid_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_target(self, l):
+        set_target(self.handle, l)
+
+    def solve(self, tau, set_kind="brt", space_order=1, time_order=1, cfl=0.8,
+              keep_snapshots=False, stats=False):
+        return solve_hjb(self.handle, tau, set_kind, space_order, time_order, cfl, keep_snapshots,
+                         stats)
+
+    def solve_problem(self, problem, keep_snapshots=False, stats=False):
+        return self.solve(problem.tau, problem.set_kind, problem.space_order, problem.time_order,
+                          problem.cfl, keep_snapshots, stats)
+
+    def readback(self, out, tau_index: int = -1):
+        return value_readback(self.handle, out, tau_index)

@@ -1,0 +1,58 @@
+"""The C-ABI library builds for sm_103a, loads on the host and exports every
+entry point that include/*.h declares (no compute call: no GPU needed)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2204_05520_gb300 import _build, odp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_entry_points():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b(odp_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return odp.load()
+
+
+def test_header_declares_the_solver_boundary():
+    names = declared_entry_points()
+    for required in ("odp_grid_create", "odp_set_dynamics", "odp_set_target", "odp_solve_hjb",
+                     "odp_value_readback"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_entry_points() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_library_reports_version_and_no_error(lib):
+    assert "sm_103a" in odp.version()
+    assert odp.last_error() == ""
+
+
+def test_argument_errors_need_no_gpu(lib):
+    # validation happens before any CUDA call
+    with pytest.raises(odp.OdpError) as e:
+        odp.grid_create((1, 4), (0.0, 0.0), (1.0, 1.0), (False, False), stream=0)
+    assert e.value.code == odp.EINVAL
+    with pytest.raises(odp.OdpError) as e:
+        odp.grid_create((4,) * 7, (0.0,) * 7, (1.0,) * 7, (False,) * 7, stream=0)
+    assert e.value.code == odp.EINVAL
+    with pytest.raises(odp.OdpError) as e:
+        odp.grid_create((4, 4), (1.0, 0.0), (0.0, 1.0), (False, False), stream=0)
+    assert e.value.code == odp.EINVAL

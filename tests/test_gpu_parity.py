@@ -1,0 +1,222 @@
+"""GPU (FP32, CUDA kernels through the C ABI) against the FP64 oracle.
+
+Criterion (the same everywhere): max |V_gpu - V_oracle| <= 1e-4 * (max l - min l)
+on the same seeded inputs, at every kept tau, with equal step counts.
+Small grids span many 256-thread blocks with a ragged tail; full-size
+workloads are checked step by step (one step from the GPU's own state,
+recomputed by the oracle over the whole grid) and by the properties that hold
+at any size.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2204_05520_gb300 import inputs, odp
+
+pytestmark = pytest.mark.gpu
+REL_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_05520_gb300 import _build
+
+    _build.build()
+    odp.load()
+    oracle.build()
+    return torch
+
+
+def gpu_solve(problem, keep=False, l=None, step_limit=None):
+    import torch
+
+    l_host = problem.target_values() if l is None else l
+    l_dev = torch.from_numpy(l_host).cuda()
+    with odp.Grid.for_problem(problem) as g:
+        if step_limit:
+            odp.set_step_limit(g.handle, step_limit)
+        g.set_target(l_dev)
+        stats = g.solve_problem(problem, keep_snapshots=keep, stats=True)
+        out = torch.empty_like(l_dev)
+        g.readback(out)
+        snaps = None
+        if keep:
+            snaps = np.stack([g.readback(torch.empty_like(l_dev), k).cpu().numpy()
+                              for k in range(len(problem.tau))])
+    return out.cpu().numpy(), stats, snaps
+
+
+def check_parity(problem, keep=False):
+    v, stats, snaps = gpu_solve(problem, keep=keep)
+    ref = oracle.solve(problem, snapshots=keep)
+    l = problem.target_values().astype(np.float64)
+    tol = REL_TOL * (l.max() - l.min())
+    assert stats["steps"] == int(ref["steps"].sum())
+    err = np.abs(v - ref["final"]).max()
+    assert err <= tol, "max err %.3g > tol %.3g" % (err, tol)
+    if keep:
+        for k in range(len(problem.tau)):
+            e = np.abs(snaps[k] - ref["snapshots"][k]).max()
+            assert e <= tol, "tau[%d]: max err %.3g > tol %.3g" % (k, e, tol)
+    np.testing.assert_allclose(stats["alpha"][: problem.ndim], ref["alpha"], rtol=1e-6)
+    return err / (l.max() - l.min())
+
+
+# ---------------------------------------------------------------------------
+# every model and scheme on small grids
+# ---------------------------------------------------------------------------
+
+CASES = [
+    inputs.dubins3d(),                                                   # 41x41x36, Euler, upwind
+    inputs.dubins3d(n=(23, 19, 13), space_order=2, time_order=2),
+    inputs.dubins3d(n=(17, 21, 12), u_mode="max", set_kind="brs"),
+    inputs.dubins3d(n=(31, 31, 24), set_kind="brs", tau=(0.0, 0.3, 0.7, 1.0)),
+    inputs.dubinscar4d(n=(21, 19, 11, 16)),                              # ENO2 + RK2
+    inputs.dubinscar4d(n=(17, 15, 9, 12), space_order=1, time_order=1),
+    inputs.dubinscar4d(n=(13, 13, 7, 10), u_mode="max", set_kind="brs"),
+    inputs.rel6d(n=(9, 8, 10, 5, 4, 3), horizon=0.3),                    # upwind + RK2
+    inputs.rel6d(n=(7, 7, 8, 3, 4, 3), space_order=2, horizon=0.2),
+    inputs.rel6d(n=(8, 9, 8, 3, 3, 4), time_order=1, set_kind="brs", horizon=0.2),
+]
+
+
+@pytest.mark.parametrize("problem", CASES, ids=lambda p: "%s_o%d%d_%s_%s" % (
+    p.name, p.space_order, p.time_order, p.set_kind, p.u_mode))
+def test_models_match_oracle(problem):
+    check_parity(problem, keep=len(problem.tau) > 2)
+
+
+SI = [((37,), "min", "brt"), ((13, 11), "max", "brs"), ((9, 7, 6), "min", "brs"),
+      ((6, 5, 7, 4), "max", "brt"), ((5, 4, 3, 6, 3), "min", "brt"),
+      ((3, 4, 3, 3, 2, 4), "min", "brs")]
+
+
+@pytest.mark.parametrize("n,mode,kind", SI, ids=lambda v: str(v))
+@pytest.mark.parametrize("order", [(1, 1), (2, 2)])
+def test_single_integrator_every_dimension(n, mode, kind, order):
+    p = inputs.single_integrator(n, u_mode=mode, set_kind=kind, space_order=order[0],
+                                 time_order=order[1], horizon=0.4)
+    check_parity(p)
+
+
+def test_advection_exact_shift_on_gpu():
+    n, k = 64, 7
+    h = 2 * math.pi / n
+    p = inputs.advection((n,), (1.0,), horizon=k * h, cfl=1.0)
+    v, stats, _ = gpu_solve(p)
+    assert stats["steps"] == k
+    l = p.target_values()
+    np.testing.assert_allclose(v, np.roll(l, -k), atol=1e-5)
+
+
+def test_degenerate_axes():
+    # periodic axes of 1 and 2 nodes, non-periodic axes of 2 nodes
+    for n, per in (((1, 9), (True, True)), ((2, 7), (True, False)), ((2, 2, 5), (False, False, True))):
+        p = inputs.Problem(
+            name="deg", n=n, lo=(0.0,) * len(n), hi=(1.0,) * len(n), periodic=per,
+            dynamics="advection", params=tuple(0.5 + 0.25 * d for d in range(len(n))),
+            u_mode="max", d_mode="max", target=inputs.sine_bump((1,) * len(n)), tau=(0.0, 0.3),
+            set_kind="brs", space_order=2, time_order=2)
+        check_parity(p)
+
+
+# ---------------------------------------------------------------------------
+# error paths reported by the device
+# ---------------------------------------------------------------------------
+
+def test_step_limit_reports_timeout():
+    p = inputs.dubins3d(n=(9, 9, 8))
+    with pytest.raises(odp.OdpError) as e:
+        gpu_solve(p, step_limit=3)
+    assert e.value.code == odp.ETIMEOUT
+
+
+def test_non_finite_target_reports_numeric_error():
+    p = inputs.dubins3d(n=(9, 9, 8))
+    l = p.target_values()
+    l[4, 4, 3] = np.nan
+    with pytest.raises(odp.OdpError) as e:
+        gpu_solve(p, l=l)
+    assert e.value.code == odp.ENUMERIC
+
+
+def test_missing_target_is_a_state_error():
+    p = inputs.dubins3d(n=(9, 9, 8))
+    with odp.Grid.for_problem(p) as g:
+        with pytest.raises(odp.OdpError) as e:
+            g.solve_problem(p)
+        assert e.value.code == odp.ESTATE
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads
+# ---------------------------------------------------------------------------
+
+def one_step_at_full_size(problem, t_a):
+    """GPU state at t_a, then one clipped step of size delta on the GPU, and
+    the same step recomputed by the oracle from the GPU's state."""
+    import torch
+
+    l = problem.target_values()
+    with odp.Grid.for_problem(problem) as g:
+        g.set_target(torch.from_numpy(l).cuda())
+        st0 = g.solve((0.0, t_a), problem.set_kind, problem.space_order, problem.time_order,
+                      problem.cfl, stats=True)
+        delta = 0.5 * st0["last_dt"] if st0["steps"] > 1 else 0.25 * t_a
+        tau = (0.0, t_a, t_a + delta)
+        st = g.solve(tau, problem.set_kind, problem.space_order, problem.time_order,
+                     problem.cfl, keep_snapshots=True, stats=True)
+        phi_a = g.readback(torch.empty(l.shape, device="cuda"), 1).cpu().numpy()
+        phi_b = g.readback(torch.empty(l.shape, device="cuda")).cpu().numpy()
+    assert st["steps"] == st0["steps"] + 1
+    ref = oracle.step(problem, phi_a, delta, l=l)
+    rng_l = float(l.max() - l.min())
+    err = np.abs(phi_b - ref["out"]).max()
+    np.testing.assert_allclose(st["alpha"][: problem.ndim], ref["alpha"], rtol=1e-6)
+    return err / rng_l, phi_b, l
+
+
+def test_dubinscar4d_full_size_step_matches_oracle():
+    p = inputs.dubinscar4d()   # 80x80x40x64, ENO2 + RK2
+    rel, _, _ = one_step_at_full_size(p, t_a=0.5)
+    assert rel <= REL_TOL
+
+
+def test_dubinscar4d_full_size_solve_properties():
+    p = inputs.dubinscar4d()
+    v, stats, _ = gpu_solve(p)
+    l = p.target_values()
+    assert stats["steps"] == 265
+    assert stats["t_final"] == 3.0
+    assert np.isfinite(v).all()
+    assert (v <= l).all()
+    # the tube grows: strictly more nodes inside than at t = 0
+    assert (v <= 0).sum() > (l <= 0).sum()
+
+
+def test_dubins3d_full_size_matches_oracle_exactly_in_steps():
+    r = check_parity(inputs.dubins3d())
+    assert r <= REL_TOL
+
+
+@pytest.mark.slow
+def test_rel6d_full_size_step_matches_oracle():
+    p = inputs.rel6d()         # 24^6, upwind + RK2
+    rel, _, _ = one_step_at_full_size(p, t_a=0.05)
+    assert rel <= REL_TOL
+
+
+def test_rel6d_full_size_solve_properties():
+    p = inputs.rel6d()
+    v, stats, _ = gpu_solve(p)
+    l = p.target_values()
+    assert 185 <= stats["steps"] <= 195
+    assert stats["t_final"] == 1.5
+    assert np.isfinite(v).all()
+    assert (v <= l).all()
+    assert stats["alpha"][0] == pytest.approx(7.0) and stats["alpha"][1] == pytest.approx(5.5)
