@@ -165,9 +165,23 @@ struct odp_grid {
     int64_t launches_per_step = 0;
 };
 
+// Make the grid's device current on the calling thread.
+static odp_status bind(const odp_grid *g)
+{
+    ODP_CUDA(cudaSetDevice(g->device));
+    return ODP_OK;
+}
+
+#define ODP_BIND(g)                      \
+    do {                                 \
+        odp_status b_ = bind(g);         \
+        if (b_ != ODP_OK) return b_;     \
+    } while (0)
+
 static void release(odp_grid *g)
 {
     if (!g) return;
+    cudaSetDevice(g->device);
     if (g->stream) cudaStreamSynchronize(g->stream);
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
@@ -231,6 +245,12 @@ extern "C" odp_status odp_grid_create(int ndim, const int32_t *n, const double *
             return bail(rc);             \
         }                                \
     } while (0)
+    // work runs on the device of the given stream (or the current device)
+    if (g->stream) {
+        int dev = -1;
+        ODP_TRY(cudaStreamGetDevice(g->stream, &dev));
+        ODP_TRY(cudaSetDevice(dev));
+    }
     ODP_TRY(cudaGetDevice(&g->device));
     const size_t bytes = size_t(total) * sizeof(float);
     ODP_TRY(cudaMalloc(&g->phi_a, bytes));
@@ -345,6 +365,7 @@ extern "C" odp_status odp_set_dynamics(odp_grid *g, odp_dyn kind, const double *
 extern "C" odp_status odp_set_target(odp_grid *g, const float *l, int64_t n_elems, int on_device)
 {
     if (!g || !l) return fail(ODP_EINVAL, "NULL argument");
+    ODP_BIND(g);
     if (n_elems != g->total) return fail(ODP_EINVAL, "target has %lld values, grid has %lld",
                                          (long long)n_elems, (long long)g->total);
     ODP_CUDA(cudaMemcpyAsync(g->l, l, size_t(n_elems) * sizeof(float),
@@ -509,6 +530,7 @@ extern "C" odp_status odp_solve_hjb(odp_grid *g, const double *tau, int n_tau, o
     if (space_order != 1 && space_order != 2) return fail(ODP_EINVAL, "space_order must be 1 or 2");
     if (time_order != 1 && time_order != 2) return fail(ODP_EINVAL, "time_order must be 1 or 2");
     if (!(cfl > 0.0 && cfl <= 1.0)) return fail(ODP_EINVAL, "cfl must lie in (0, 1]");
+    ODP_BIND(g);
 
     cudaStream_t st = g->stream;
     if (n_tau > g->tau_cap) {
@@ -591,6 +613,7 @@ extern "C" odp_status odp_solve_status(odp_grid *g, odp_solve_stats *stats)
 {
     if (!g) return fail(ODP_EINVAL, "grid is NULL");
     if (!g->solved) return fail(ODP_ESTATE, "no solve was issued on this grid");
+    ODP_BIND(g);
     SolveState h{};
     odp_status rs = read_state(g, &h);
     if (rs != ODP_OK) return rs;
@@ -629,6 +652,7 @@ extern "C" odp_status odp_value_readback(odp_grid *g, int tau_index, float *dst,
     if (tau_index < -1 || tau_index >= g->n_tau) return fail(ODP_EINVAL, "tau_index %d out of range", tau_index);
     if (tau_index == g->n_tau - 1) tau_index = -1;
     if (tau_index >= 0 && !g->keep) return fail(ODP_EINVAL, "snapshots were not kept");
+    ODP_BIND(g);
     SolveState h{};
     odp_status rs = read_state(g, &h);
     if (rs != ODP_OK) return rs;
@@ -646,6 +670,7 @@ extern "C" odp_status odp_time_stage(odp_grid *g, int stage, int reps, double *m
     if (reps < 1) return fail(ODP_EINVAL, "reps must be >= 1");
     if ((g->time_order == 1) != (stage == 0) || stage < 0 || stage > 2)
         return fail(ODP_EINVAL, "stage %d does not belong to a time order %d solve", stage, g->time_order);
+    ODP_BIND(g);
     cudaStream_t s = g->capture_stream;
     ODP_CUDA(cudaStreamSynchronize(g->stream));
     ODP_CUDA(cudaEventRecord(g->ev0, s));
