@@ -68,7 +68,7 @@ def _load():
             lib.og_eval_dynamics_batch.restype = i32
             lib.og_terms.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, i32, P, P,
                                      P, P, P, P, P, P, P, P]
-            lib.og_solve.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, P, i32, i32,
+            lib.og_solve.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, P, P, i32, i32,
                                      i32, i32, f64, i64, P, P, P, P, P]
             lib.og_step.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, P, f64, i32, i32,
                                     i32, P, P]
@@ -206,10 +206,11 @@ def step(problem, phi, dt, l=None) -> dict:
 
 
 def solve(problem, l=None, snapshots: bool = False, max_steps: int = 10_000_000,
-          raise_on_error: bool = True) -> dict:
+          raise_on_error: bool = True, phi0=None) -> dict:
     """Run the full solve of ``problem`` (an ``inputs.Problem``).
 
     ``l`` defaults to ``problem.target_values()`` (float32) promoted to float64.
+    ``phi0`` (optional) is the value to start from instead of ``l``.
     Returns dict(final, snapshots (or None), steps (per segment), alpha,
     last_dt, rc).
     """
@@ -219,6 +220,7 @@ def solve(problem, l=None, snapshots: bool = False, max_steps: int = 10_000_000,
     if l is None:
         l = p.target_values()
     l64 = np.ascontiguousarray(l, dtype=np.float64).reshape(-1)
+    p0 = None if phi0 is None else np.ascontiguousarray(phi0, dtype=np.float64).reshape(-1)
     tau = np.ascontiguousarray(p.tau, dtype=np.float64)
     prm = np.ascontiguousarray(p.params, dtype=np.float64)
     N = l64.size
@@ -229,7 +231,8 @@ def solve(problem, l=None, snapshots: bool = False, max_steps: int = 10_000_000,
     last_dt = ctypes.c_double(0.0)
     rc = lib.og_solve(len(n_a), _ptr(n_a), _ptr(lo_a), _ptr(hi_a), _ptr(per_a),
                       DYN_IDS[p.dynamics], _ptr(prm), len(prm), MODE_IDS[p.u_mode],
-                      MODE_IDS[p.d_mode], _ptr(l64), _ptr(tau), len(tau), SET_IDS[p.set_kind],
+                      MODE_IDS[p.d_mode], _ptr(l64), _ptr(p0), _ptr(tau), len(tau),
+                      SET_IDS[p.set_kind],
                       p.space_order, p.time_order, float(p.cfl), int(max_steps), _ptr(snaps),
                       _ptr(final), _ptr(steps), _ptr(alpha), ctypes.byref(last_dt))
     if rc and raise_on_error:

@@ -580,7 +580,9 @@ int og_step(int ndim, const int64_t *n, const double *lo, const double *hi, cons
 }
 
 /* Full solve (Algorithm 1 with the BRS / BRT post-step of Section 4.3).
- *  l           target l(z), total nodes; phi(z, 0) = l(z)
+ *  l           target l(z), total nodes
+ *  phi0        NULL: phi(z, 0) = l(z); else the value to start from (resuming a
+ *              solve at a kept tau: the schedule then counts from that tau)
  *  tau         n_tau look-back times, tau[0] = 0, strictly increasing
  *  set_kind    OG_BRS (plain PDE) or OG_BRT (phi <- min(phi, l) after each step,
  *              the HJ variational inequality)
@@ -592,8 +594,8 @@ int og_step(int ndim, const int64_t *n, const double *lo, const double *hi, cons
  */
 int og_solve(int ndim, const int64_t *n, const double *lo, const double *hi,
              const int *periodic, int kind, const double *prm, int n_prm, int umode,
-             int dmode, const double *l, const double *tau, int n_tau, int set_kind,
-             int space_order, int time_order, double cfl, int64_t max_steps,
+             int dmode, const double *l, const double *phi0, const double *tau, int n_tau,
+             int set_kind, int space_order, int time_order, double cfl, int64_t max_steps,
              double *snapshots, double *final_out, int64_t *steps_out,
              double *alpha_out, double *last_dt)
 {
@@ -614,7 +616,7 @@ int og_solve(int ndim, const int64_t *n, const double *lo, const double *hi,
     double *phi1 = malloc(sizeof(double) * N);
     double *L = malloc(sizeof(double) * N);
     if (!phi || !phi1 || !L) { free(phi); free(phi1); free(L); return OG_ENOMEM; }
-    memcpy(phi, l, sizeof(double) * N);
+    memcpy(phi, phi0 ? phi0 : l, sizeof(double) * N);
     if (snapshots) memcpy(snapshots, phi, sizeof(double) * N);
 
     double alpha[OG_MAXD] = {0}, alpha2[OG_MAXD] = {0};

@@ -1,12 +1,180 @@
 // hj_kernels.cuh -- kernels of one solve: the fused stage pass (K2), the
 // alpha reductions (K1) and their launch helpers.  Instantiated per model in
 // kern_<model>.cu so that the translation units compile in parallel.
+//
+// Thread layout of the stage pass: one thread owns four consecutive nodes of
+// a row (the last axis), loads them and each neighbour row with one 16-byte
+// access, and keeps everything in registers.  The Hamiltonian of every model
+// here is a sum of per-axis terms, H = sum_d (a_d(z) pbar_d + S_d |pbar_d|)
+// (drift coefficient a_d, and S_d = +-bound of the input acting on axis d,
+// Algorithm 1 with the bang-bang inputs folded in), and so is the
+// Lax-Friedrichs dissipation; the update L = H + 1/2 sum_d alpha_d (p+_d - p-_d)
+// is therefore accumulated axis by axis without keeping every derivative.
 #pragma once
 
 #include "hj_device.cuh"
 #include "odp_launch.h"
 
 namespace odp {
+
+__device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+
+__device__ __forceinline__ float lane(const float4 &v, int k)
+{
+    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+
+// Neighbour row of a four-node segment along a non-last axis: periodic wrap or
+// sign-keeping ghost extrapolation (Section 3.1.1), lane by lane.
+__device__ __forceinline__ float4 row_shift4(const float *__restrict__ src, int base, int id, int stride, int n,
+                                             int periodic, int off)
+{
+    int j = id + off;
+    if (periodic) {
+        if (j < 0) j += n;
+        if (j < 0) j += n;
+        if (j >= n) j -= n;
+        if (j >= n) j -= n;
+        return ld4(src + base + (j - id) * stride);
+    }
+    if (j >= 0 && j < n) return ld4(src + base + off * stride);
+    const int b = (j < 0) ? 0 : n - 1;
+    const int in = (j < 0) ? 1 : n - 2;
+    const float k = (j < 0) ? float(-j) : float(j - (n - 1));
+    const float4 pb = ld4(src + base + (b - id) * stride);
+    const float4 pi = ld4(src + base + (in - id) * stride);
+    float4 r;
+    r.x = pb.x + k * (pb.x >= 0.0f ? 1.0f : -1.0f) * fabsf(pb.x - pi.x);
+    r.y = pb.y + k * (pb.y >= 0.0f ? 1.0f : -1.0f) * fabsf(pb.y - pi.y);
+    r.z = pb.z + k * (pb.z >= 0.0f ? 1.0f : -1.0f) * fabsf(pb.z - pi.z);
+    r.w = pb.w + k * (pb.w >= 0.0f ? 1.0f : -1.0f) * fabsf(pb.w - pi.w);
+    return r;
+}
+
+// Node j (possibly outside [0, n)) of the last axis of a row.
+__device__ __forceinline__ float last_axis_value(const float *__restrict__ row, int j, int n, int periodic)
+{
+    if (j >= 0 && j < n) return __ldg(row + j);
+    if (periodic) {
+        while (j < 0) j += n;
+        while (j >= n) j -= n;
+        return __ldg(row + j);
+    }
+    const int b = (j < 0) ? 0 : n - 1;
+    const int in = (j < 0) ? 1 : n - 2;
+    const float k = (j < 0) ? float(-j) : float(j - (n - 1));
+    const float pb = __ldg(row + b), pi = __ldg(row + in);
+    return pb + k * (pb >= 0.0f ? 1.0f : -1.0f) * fabsf(pb - pi);
+}
+
+// Unscaled one-sided differences of one node from its five-point window
+// (ENO2) or three-point window (upwind): dm = h p-, dp = h p+.
+template <int ORDER>
+__device__ __forceinline__ void diffs(float fm2, float fm1, float f0, float fp1, float fp2, float &dm, float &dp)
+{
+    const float a = f0 - fm1, b = fp1 - f0;
+    if (ORDER == 1) {
+        dm = a;
+        dp = b;
+    } else {
+        const float d2l = a - (fm1 - fm2);
+        const float d2m = b - a;
+        const float d2r = (fp2 - fp1) - b;
+        const float cm = (fabsf(d2l) < fabsf(d2m)) ? d2l : d2m;
+        const float cp = (fabsf(d2r) < fabsf(d2m)) ? d2r : d2m;
+        dm = a + 0.5f * cm;
+        dp = b - 0.5f * cp;
+    }
+}
+
+// Contribution of one axis to L at one node: a pbar + S |pbar| + 1/2 alpha (p+ - p-).
+__device__ __forceinline__ float axis_term(float dm, float dp, float inv_h, float a, float S, float half_alpha)
+{
+    const float pm = dm * inv_h, pp = dp * inv_h;
+    const float pb = 0.5f * (pp + pm);
+    return a * pb + S * fabsf(pb) + half_alpha * (pp - pm);
+}
+
+// Drift coefficients a_d of the four nodes of a segment and the signed input
+// bounds S_d (Appendix dynamics; Section 4.2 modes).
+template <int DYN, int ND>
+__device__ __forceinline__ void drift(const GridDesc &g, const DynDesc &dy, const int *idx, float a[ND][4],
+                                      float S[ND])
+{
+    const float su = mode_sign(dy.umode), sd = mode_sign(dy.dmode);
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        S[d] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[d][k] = 0.0f;
+    }
+    const int s0 = idx[ND - 1];
+    if (DYN == DYN_SINGLE_INT) {
+#pragma unroll
+        for (int d = 0; d < ND; ++d) S[d] = su * dy.prm[0];
+    } else if (DYN == DYN_ADVECTION) {
+#pragma unroll
+        for (int d = 0; d < ND; ++d)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a[d][k] = dy.prm[d];
+    } else if (DYN == DYN_DUBINS3D) {          // (x, y, th), th last
+        const float4 c = ld4(g.cos_tab + s0), s = ld4(g.sin_tab + s0);
+        const float v = dy.prm[0];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            a[0][k] = v * lane(c, k);
+            a[1][k] = v * lane(s, k);
+        }
+        S[2] = su * dy.prm[1];
+    } else if (DYN == DYN_DUBINSCAR4D) {       // (x, y, v, th), th last
+        const float4 c = ld4(g.cos_tab + s0), s = ld4(g.sin_tab + s0);
+        const float v = __ldg(g.coord[2] + idx[2]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            a[0][k] = v * lane(c, k);
+            a[1][k] = v * lane(s, k);
+        }
+        S[2] = su * dy.prm[0];
+        S[3] = su * dy.prm[1];
+    } else {                                   // Rel6D (x, y, th, v_p, w_p, v_e), v_e last
+        const float x = __ldg(g.coord[0] + idx[0]);
+        const float y = __ldg(g.coord[1] + idx[1]);
+        const float c = __ldg(g.cos_tab + idx[2]);
+        const float s = __ldg(g.sin_tab + idx[2]);
+        const float vp = __ldg(g.coord[3] + idx[3]);
+        const float wp = __ldg(g.coord[4] + idx[4]);
+        const float4 ve = ld4(g.coord[5] + s0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            a[0][k] = -vp + lane(ve, k) * c + wp * y;
+            a[1][k] = lane(ve, k) * s - wp * x;
+            a[2][k] = -wp;
+        }
+        S[2] = sd * dy.prm[3];
+        S[3] = su * dy.prm[0];
+        S[4] = su * dy.prm[1];
+        S[5] = sd * dy.prm[2];
+    }
+}
+
+// Multi-index of a thread's segment: idx[0..ND-2] of its row, idx[ND-1] the
+// first node of its segment; returns the storage offset of that node.
+template <int ND>
+__device__ __forceinline__ int segment_index(const GridDesc &g, uint32_t t, int *idx)
+{
+    uint32_t row = fast_div(t, g.div_segs);
+    const int seg = int(t - row * uint32_t(g.segs));
+    const int base = int(row) * g.n_pad + 4 * seg;
+#pragma unroll
+    for (int d = ND - 2; d > 0; --d) {
+        const uint32_t q = fast_div(row, g.div[d]);
+        idx[d] = int(row - q * uint32_t(g.n[d]));
+        row = q;
+    }
+    if (ND >= 2) idx[0] = int(row);
+    idx[ND - 1] = 4 * seg;
+    return base;
+}
 
 // Fused stage pass (Algorithm 1, one Euler or TVD-RK2 stage, Section 3.1.3):
 // derivatives, pbar, H, Lax-Friedrichs dissipation with the grid alpha,
@@ -18,32 +186,104 @@ template <int ND, int ORDER, int DYN>
 __global__ void __launch_bounds__(256) k_stage(GridDesc g, DynDesc dy, SolveState *st,
                                                const float *__restrict__ l, int stage, int brt)
 {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= uint32_t(g.total)) return;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= uint32_t(g.nthreads)) return;
     const float *__restrict__ src = (stage == 2) ? st->nxt : st->cur;
     float *dst = (stage == 2) ? st->cur : st->nxt;
     const unsigned *ab = st->alpha_bits[stage == 2 ? 1 : 0];
 
     int idx[ND];
-    unflatten(g, ND, i, idx);
-    float pm[ND], pp[ND], pbar[ND];
+    const int base = segment_index<ND>(g, t, idx);
+    float a[ND][4], S[ND];
+    drift<DYN, ND>(g, dy, idx, a, S);
+
+    const float4 c4 = ld4(src + base);
+    const float f[4] = {c4.x, c4.y, c4.z, c4.w};
+    float L[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+
+    // axes other than the last: neighbour rows
 #pragma unroll
-    for (int d = 0; d < ND; ++d) {
-        one_sided<ORDER>(src, int(i), idx[d], g.stride[d], g.n[d], g.periodic[d], g.inv_dz[d],
-                         pm[d], pp[d]);
-        pbar[d] = 0.5f * (pp[d] + pm[d]);
+    for (int d = 0; d < ND - 1; ++d) {
+        const float ha = 0.5f * __uint_as_float(ab[d]);
+        const float4 m1 = row_shift4(src, base, idx[d], g.stride[d], g.n[d], g.periodic[d], -1);
+        const float4 p1 = row_shift4(src, base, idx[d], g.stride[d], g.n[d], g.periodic[d], +1);
+        float4 m2 = m1, p2 = p1;
+        if (ORDER == 2) {
+            m2 = row_shift4(src, base, idx[d], g.stride[d], g.n[d], g.periodic[d], -2);
+            p2 = row_shift4(src, base, idx[d], g.stride[d], g.n[d], g.periodic[d], +2);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float dm, dp;
+            diffs<ORDER>(lane(m2, k), lane(m1, k), f[k], lane(p1, k), lane(p2, k), dm, dp);
+            L[k] += axis_term(dm, dp, g.inv_dz[d], a[d][k], S[d], ha);
+        }
     }
-    const float h = hamiltonian<DYN, ND>(g, dy, idx, pbar);
-    float diss = 0.0f;
+
+    // last axis: an eight-node window w[j] = phi(first node - 2 + j)
+    const int nl = g.n[ND - 1];
+    const int s0 = idx[ND - 1];
+    float w[8];
+    w[2] = f[0];
+    w[3] = f[1];
+    w[4] = f[2];
+    w[5] = f[3];
+    const float *row = src + (base - s0);
+    if (s0 >= 2 && s0 + 5 < nl) {
+        const float2 lh = __ldg(reinterpret_cast<const float2 *>(src + base - 2));
+        const float2 rh = __ldg(reinterpret_cast<const float2 *>(src + base + 4));
+        w[0] = lh.x;
+        w[1] = lh.y;
+        w[6] = rh.x;
+        w[7] = rh.y;
+    } else {
+        const int per = g.periodic[ND - 1];
 #pragma unroll
-    for (int d = 0; d < ND; ++d) diss += __uint_as_float(ab[d]) * (pp[d] - pm[d]);
-    const float L = h + 0.5f * diss;
+        for (int j = 0; j < 8; ++j)
+            if (j < 2 || j >= 6 || s0 + j - 2 >= nl) w[j] = last_axis_value(row, s0 + j - 2, nl, per);
+    }
+    {
+        const float ha = 0.5f * __uint_as_float(ab[ND - 1]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float dm, dp;
+            diffs<ORDER>(w[k], w[k + 1], w[k + 2], w[k + 3], w[k + 4], dm, dp);
+            L[k] += axis_term(dm, dp, g.inv_dz[ND - 1], a[ND - 1][k], S[ND - 1], ha);
+        }
+    }
+
+    // update, Heun average, non-finite flag, BRT min
     const float dt = float(st->dt);
-    float v = src[i] + dt * L;
-    if (stage == 2) v = 0.5f * (st->cur[i] + v);
-    if (!isfinite(v)) atomicOr(&st->flags, FLAG_NONFINITE);
-    if (brt && stage != 1) v = fminf(v, __ldg(l + i));
-    dst[i] = v;
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = f[k] + dt * L[k];
+    if (stage == 2) {
+        const float4 b4 = *reinterpret_cast<const float4 *>(st->cur + base);
+        v[0] = 0.5f * (b4.x + v[0]);
+        v[1] = 0.5f * (b4.y + v[1]);
+        v[2] = 0.5f * (b4.z + v[2]);
+        v[3] = 0.5f * (b4.w + v[3]);
+    }
+    const int nvalid = min(4, nl - s0);
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (k < nvalid && !isfinite(v[k])) bad = true;
+    if (bad) atomicOr(&st->flags, FLAG_NONFINITE);
+    if (brt && stage != 1) {
+        const float4 l4 = ld4(l + base);
+        v[0] = fminf(v[0], l4.x);
+        v[1] = fminf(v[1], l4.y);
+        v[2] = fminf(v[2], l4.z);
+        v[3] = fminf(v[3], l4.w);
+    }
+    if (nvalid == 4) {
+        *reinterpret_cast<float4 *>(dst + base) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (k < nvalid) dst[base + k] = v[k];
+    }
 }
 
 // Grid-wide max of the static alpha components into both stage slots.
@@ -63,11 +303,11 @@ __global__ void __launch_bounds__(256) k_alpha_static(GridDesc g, DynDesc dy, So
 #pragma unroll
         for (int d = 0; d < ND; ++d) a[d] = fmaxf(a[d], la[d]);
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane_id = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
         a[d] = warp_max(a[d]);
-        if (lane == 0) red[warp][d] = a[d];
+        if (lane_id == 0) red[warp][d] = a[d];
     }
     __syncthreads();
     if (threadIdx.x < ND) {
@@ -78,24 +318,37 @@ __global__ void __launch_bounds__(256) k_alpha_static(GridDesc g, DynDesc dy, So
     }
 }
 
-// Rel6D heading-rate alpha of phi (slot 0: cur, slot 1: nxt = phi1).
+// Rel6D heading-rate alpha of phi (slot 0: cur) or phi1 (slot 1: nxt), from
+// the p_th interval of every node; four nodes per thread, grid-stride.
 template <int ORDER>
 __global__ void __launch_bounds__(256) k_alpha_rel6d(GridDesc g, DynDesc dy, SolveState *st, int slot)
 {
     __shared__ float red[8];
     const float *__restrict__ src = slot ? st->nxt : st->cur;
-    float a = 0.0f;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < uint32_t(g.total);
-         i += gridDim.x * blockDim.x) {
+    float amax = 0.0f;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < uint32_t(g.nthreads);
+         t += gridDim.x * blockDim.x) {
         int idx[6];
-        unflatten(g, 6, i, idx);
-        float pm, pp;
-        one_sided<ORDER>(src, int(i), idx[2], g.stride[2], g.n[2], g.periodic[2], g.inv_dz[2], pm, pp);
+        const int base = segment_index<6>(g, t, idx);
+        const float4 c4 = ld4(src + base);
+        const float4 m1 = row_shift4(src, base, idx[2], g.stride[2], g.n[2], g.periodic[2], -1);
+        const float4 p1 = row_shift4(src, base, idx[2], g.stride[2], g.n[2], g.periodic[2], +1);
+        float4 m2 = m1, p2 = p1;
+        if (ORDER == 2) {
+            m2 = row_shift4(src, base, idx[2], g.stride[2], g.n[2], g.periodic[2], -2);
+            p2 = row_shift4(src, base, idx[2], g.stride[2], g.n[2], g.periodic[2], +2);
+        }
         const float wp = __ldg(g.coord[4] + idx[4]);
-        a = fmaxf(a, rel6d_theta_alpha(dy, wp, fminf(pm, pp), fmaxf(pm, pp)));
+        const int nvalid = min(4, g.n[5] - idx[5]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float dm, dp;
+            diffs<ORDER>(lane(m2, k), lane(m1, k), lane(c4, k), lane(p1, k), lane(p2, k), dm, dp);
+            if (k < nvalid) amax = fmaxf(amax, rel6d_theta_alpha(dy, wp, fminf(dm, dp), fmaxf(dm, dp)));
+        }
     }
-    a = warp_max(a);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    amax = warp_max(amax);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
     __syncthreads();
     if (threadIdx.x == 0) {
         float m = 0.0f;
@@ -116,7 +369,7 @@ template <int ND, int DYN>
 cudaError_t launch_stage_t(const GridDesc &g, const DynDesc &dy, SolveState *st, const float *l,
                            int order, int stage, int brt, cudaStream_t s)
 {
-    const int blocks = blocks_for(g.total, 256);
+    const int blocks = blocks_for(g.nthreads, 256);
     if (order == 1)
         k_stage<ND, 1, DYN><<<blocks, 256, 0, s>>>(g, dy, st, l, stage, brt);
     else

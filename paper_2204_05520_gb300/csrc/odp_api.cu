@@ -137,7 +137,10 @@ struct odp_grid {
     int n[ODP_MAXD] = {0};
     double lo[ODP_MAXD] = {0}, hi[ODP_MAXD] = {0};
     int periodic[ODP_MAXD] = {0};
-    int64_t total = 0;
+    int64_t total = 0;                // nodes
+    int64_t total_pad = 0;            // stored floats (last axis padded to n_pad)
+    int n_last = 0, n_pad = 0;
+    int64_t rows = 0;
     cudaStream_t stream = nullptr;
     int device = 0;
 
@@ -252,47 +255,60 @@ extern "C" odp_status odp_grid_create(int ndim, const int32_t *n, const double *
         ODP_TRY(cudaSetDevice(dev));
     }
     ODP_TRY(cudaGetDevice(&g->device));
-    const size_t bytes = size_t(total) * sizeof(float);
+    g->n_last = n[ndim - 1];
+    g->n_pad = (g->n_last + 3) / 4 * 4;
+    g->rows = total / g->n_last;
+    g->total_pad = g->rows * g->n_pad;
+    const size_t bytes = size_t(g->total_pad) * sizeof(float);
     ODP_TRY(cudaMalloc(&g->phi_a, bytes));
     ODP_TRY(cudaMalloc(&g->phi_b, bytes));
     ODP_TRY(cudaMalloc(&g->l, bytes));
+    ODP_TRY(cudaMemset(g->phi_a, 0, bytes));
+    ODP_TRY(cudaMemset(g->phi_b, 0, bytes));
+    ODP_TRY(cudaMemset(g->l, 0, bytes));
     ODP_TRY(cudaMalloc(&g->state, sizeof(SolveState)));
     ODP_TRY(cudaStreamCreateWithFlags(&g->capture_stream, cudaStreamNonBlocking));
     ODP_TRY(cudaEventCreate(&g->ev0));
     ODP_TRY(cudaEventCreate(&g->ev1));
 
-    // node tables: coordinates of every axis, then cos / sin of every axis
-    // (only the angle axis is used); float64 on the host, rounded once.
+    // node tables: per axis, coordinates then cos and sin of the coordinates
+    // (only an angle axis uses the trig tables), each table padded to a
+    // multiple of 4 entries so that four-node segments load them as one
+    // vector; float64 on the host, rounded once.
     int64_t tab_len = 0;
-    for (int d = 0; d < ndim; ++d) tab_len += 3 * int64_t(n[d]);
-    std::vector<float> tab(static_cast<size_t>(tab_len));
+    for (int d = 0; d < ndim; ++d) tab_len += 3 * int64_t((n[d] + 3) / 4 * 4);
+    std::vector<float> tab(static_cast<size_t>(tab_len), 0.0f);
     GridDesc &D = g->desc;
     D.ndim = ndim;
     D.total = int(total);
+    D.n_pad = g->n_pad;
+    D.rows = int(g->rows);
+    D.segs = g->n_pad / 4;
+    D.nthreads = int(g->rows * (g->n_pad / 4));
+    D.div_segs = make_fastdiv(uint32_t(D.segs));
     int64_t off = 0;
-    std::vector<int64_t> coord_off(ndim), trig_off(ndim);
+    std::vector<int64_t> coord_off(ndim);
     for (int d = 0; d < ndim; ++d) {
         const double h = periodic[d] ? (hi[d] - lo[d]) / double(n[d]) : (hi[d] - lo[d]) / double(n[d] - 1);
+        const int64_t np = (n[d] + 3) / 4 * 4;
         D.n[d] = n[d];
         D.periodic[d] = periodic[d] ? 1 : 0;
         D.dz[d] = h;
         D.inv_dz[d] = float(1.0 / h);
         D.div[d] = make_fastdiv(uint32_t(n[d]));
         coord_off[d] = off;
-        for (int i = 0; i < n[d]; ++i) tab[size_t(off + i)] = float(lo[d] + double(i) * h);
-        off += n[d];
-        trig_off[d] = off;
         for (int i = 0; i < n[d]; ++i) {
             const double z = lo[d] + double(i) * h;
-            tab[size_t(off + i)] = float(std::cos(z));
-            tab[size_t(off + n[d] + i)] = float(std::sin(z));
+            tab[size_t(off + i)] = float(z);
+            tab[size_t(off + np + i)] = float(std::cos(z));
+            tab[size_t(off + 2 * np + i)] = float(std::sin(z));
         }
-        off += 2 * int64_t(n[d]);
+        off += 3 * np;
     }
     int64_t s = 1;
     for (int d = ndim - 1; d >= 0; --d) {
         D.stride[d] = int(s);
-        s *= n[d];
+        s *= (d == ndim - 1) ? g->n_pad : n[d];
     }
     ODP_TRY(cudaMalloc(&g->tables, size_t(tab_len) * sizeof(float)));
     ODP_TRY(cudaMemcpy(g->tables, tab.data(), size_t(tab_len) * sizeof(float), cudaMemcpyHostToDevice));
@@ -312,11 +328,13 @@ extern "C" odp_status odp_grid_destroy(odp_grid *g)
     return ODP_OK;
 }
 
+static int64_t padded4(int n) { return (int64_t(n) + 3) / 4 * 4; }
+
 static int64_t trig_offset(const odp_grid *g, int axis)
 {
     int64_t off = 0;
-    for (int d = 0; d < axis; ++d) off += 3 * int64_t(g->n[d]);
-    return off + g->n[axis];
+    for (int d = 0; d < axis; ++d) off += 3 * padded4(g->n[d]);
+    return off + padded4(g->n[axis]);
 }
 
 extern "C" odp_status odp_set_dynamics(odp_grid *g, odp_dyn kind, const double *params, int n_params,
@@ -356,7 +374,7 @@ extern "C" odp_status odp_set_dynamics(odp_grid *g, odp_dyn kind, const double *
     if (angle >= 0) {
         const int64_t off = trig_offset(g, angle);
         g->desc.cos_tab = g->tables + off;
-        g->desc.sin_tab = g->tables + off + g->n[angle];
+        g->desc.sin_tab = g->tables + off + padded4(g->n[angle]);
     }
     g->has_dyn = true;
     return ODP_OK;
@@ -368,8 +386,9 @@ extern "C" odp_status odp_set_target(odp_grid *g, const float *l, int64_t n_elem
     ODP_BIND(g);
     if (n_elems != g->total) return fail(ODP_EINVAL, "target has %lld values, grid has %lld",
                                          (long long)n_elems, (long long)g->total);
-    ODP_CUDA(cudaMemcpyAsync(g->l, l, size_t(n_elems) * sizeof(float),
-                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));
+    ODP_CUDA(cudaMemcpy2DAsync(g->l, size_t(g->n_pad) * sizeof(float), l, size_t(g->n_last) * sizeof(float),
+                               size_t(g->n_last) * sizeof(float), size_t(g->rows),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));
     g->has_target = true;
     return ODP_OK;
 }
@@ -500,8 +519,8 @@ static odp_status build_graph(odp_grid *g)
         ODP_CUDA(cudaGraphAddNode(&if_node, body, leaf.data(), nullptr, leaf.size(), &ip));
         cudaGraph_t snap_body = ip.conditional.phGraph_out[0];
         ODP_CUDA(cudaStreamBeginCaptureToGraph(s, snap_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-        const int blocks = int(std::min<int64_t>((g->total + 255) / 256, 152 * 8));
-        k_snapshot<<<blocks, 256, 0, s>>>(g->state, int(g->total));
+        const int blocks = int(std::min<int64_t>((g->total_pad + 255) / 256, 152 * 8));
+        k_snapshot<<<blocks, 256, 0, s>>>(g->state, int(g->total_pad));
         e = cudaGetLastError();
         cudaGraph_t cap2 = snap_body;
         e2 = cudaStreamEndCapture(s, &cap2);
@@ -544,7 +563,7 @@ extern "C" odp_status odp_solve_hjb(odp_grid *g, const double *tau, int n_tau, o
         cudaFree(g->snapshots);
         g->snapshots = nullptr;
         g->snap_cap = 0;
-        ODP_CUDA(cudaMalloc(&g->snapshots, sizeof(float) * size_t(n_tau) * size_t(g->total)));
+        ODP_CUDA(cudaMalloc(&g->snapshots, sizeof(float) * size_t(n_tau) * size_t(g->total_pad)));
         g->snap_cap = n_tau;
     }
     g->order = space_order;
@@ -579,7 +598,7 @@ extern "C" odp_status odp_solve_hjb(odp_grid *g, const double *tau, int n_tau, o
     h.nxt = g->phi_b;
     h.tau = g->tau;
     h.snapshots = g->keep ? g->snapshots : nullptr;
-    const size_t bytes = size_t(g->total) * sizeof(float);
+    const size_t bytes = size_t(g->total_pad) * sizeof(float);
     ODP_CUDA(cudaMemcpyAsync(g->tau, tau, sizeof(double) * size_t(n_tau), cudaMemcpyHostToDevice, st));
     ODP_CUDA(cudaMemcpyAsync(g->state, &h, sizeof(h), cudaMemcpyHostToDevice, st));
     ODP_CUDA(cudaMemcpyAsync(g->phi_a, g->l, bytes, cudaMemcpyDeviceToDevice, st));
@@ -656,9 +675,10 @@ extern "C" odp_status odp_value_readback(odp_grid *g, int tau_index, float *dst,
     SolveState h{};
     odp_status rs = read_state(g, &h);
     if (rs != ODP_OK) return rs;
-    const float *src = (tau_index >= 0) ? g->snapshots + size_t(tau_index) * size_t(g->total) : h.cur;
-    ODP_CUDA(cudaMemcpyAsync(dst, src, size_t(n_elems) * sizeof(float),
-                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
+    const float *src = (tau_index >= 0) ? g->snapshots + size_t(tau_index) * size_t(g->total_pad) : h.cur;
+    ODP_CUDA(cudaMemcpy2DAsync(dst, size_t(g->n_last) * sizeof(float), src, size_t(g->n_pad) * sizeof(float),
+                               size_t(g->n_last) * sizeof(float), size_t(g->rows),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
     ODP_CUDA(cudaStreamSynchronize(g->stream));
     return status_of(h);
 }

@@ -46,11 +46,20 @@ __device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv &f)
     return (__umulhi(f.m, n) + n) >> f.l;
 }
 
+// Storage: C order with the last axis padded to n_pad, a multiple of 4 nodes,
+// so that every row starts on a 16-byte boundary and a thread can move four
+// consecutive nodes of a row with one vector access.  Padding lanes are never
+// read as neighbours and never written by the stage kernels.
 struct GridDesc {
     int ndim;
     int total;                   // number of nodes (< 2^31)
+    int n_pad;                   // padded length of the last axis
+    int rows;                    // product of n[0 .. ndim-2]
+    int segs;                    // n_pad / 4: four-node segments per row
+    int nthreads;                // rows * segs
+    FastDiv div_segs;
     int n[ODP_MAXD];
-    int stride[ODP_MAXD];        // C order: stride[ndim-1] == 1
+    int stride[ODP_MAXD];        // C order over the padded storage: stride[ndim-1] == 1
     int periodic[ODP_MAXD];
     float inv_dz[ODP_MAXD];      // 1 / node spacing
     double dz[ODP_MAXD];         // node spacing (float64, for the CFL step)

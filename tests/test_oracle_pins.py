@@ -487,3 +487,13 @@ def test_invalid_arguments_are_rejected():
         oracle.solve(short, l=np.zeros(20, np.float32))
     r = oracle.solve(p, max_steps=2, raise_on_error=False)
     assert r["rc"] == oracle.ETIMEOUT
+
+
+def test_resuming_from_a_kept_value_continues_the_schedule():
+    # solving (0, T1, T2) equals solving (0, T1) and resuming from its value
+    p = inputs.dubins3d(n=(21, 21, 16), tau=(0.0, 0.6, 1.1), space_order=2, time_order=2)
+    full = oracle.solve(p, snapshots=True)
+    seg = inputs.dubins3d(n=(21, 21, 16), tau=(0.0, 0.5), space_order=2, time_order=2)
+    res = oracle.solve(seg, phi0=full["snapshots"][1])
+    np.testing.assert_allclose(res["final"], full["final"], atol=1e-12)
+    assert res["steps"][0] == full["steps"][1]
