@@ -35,7 +35,8 @@
  *     g_k = phi_b + k*sign(phi_b)*|phi_b - phi_inner|, sign(0) = +1.
  *  R10 ENO2: p- = D-phi + (h/2) c, p+ = D+phi - (h/2) c', c (c') the second
  *     difference of smaller magnitude among those at i-1 and i (i and i+1);
- *     on equal magnitude the centred one (at i).
+ *     on equal magnitude the centred one (at i).  The comparison is taken in
+ *     float32 (see og_one_sided).
  */
 #include <math.h>
 #include <stdint.h>
@@ -133,8 +134,41 @@ static double og_shifted(const og_grid *g, const double *phi, const int64_t *idx
     return pb + k * sgn * fabs(pb - pin);
 }
 
+/* The same node value as the GPU kernel holds it: float32; a ghost node is
+ * formed in float32 arithmetic from the float32 boundary values (R9).  Used
+ * only for the float32 stencil decision below. */
+static float og_shifted32(const og_grid *g, const double *phi, const int64_t *idx,
+                          int64_t flat, int d, int off)
+{
+    int64_t n = g->n[d];
+    int64_t j = idx[d] + off;
+    int64_t row = flat - idx[d] * g->stride[d];
+    if (g->periodic[d]) {
+        j = ((j % n) + n) % n;
+        return (float)phi[row + j * g->stride[d]];
+    }
+    if (j >= 0 && j < n) return (float)phi[row + j * g->stride[d]];
+    int64_t b = (j < 0) ? 0 : n - 1;
+    int64_t in = (j < 0) ? 1 : n - 2;
+    float k = (j < 0) ? (float)(-j) : (float)(j - (n - 1));
+    float pb = (float)phi[row + b * g->stride[d]];
+    float pin = (float)phi[row + in * g->stride[d]];
+    float sgn = (pb >= 0.0f) ? 1.0f : -1.0f;
+    return pb + (k * sgn) * fabsf(pb - pin);
+}
+
 /* One-sided derivatives p-, p+ along axis d at a node (Section 3.1.4 and
- * Algorithm 1: first-order upwind differences, or second-order ENO R10). */
+ * Algorithm 1: first-order upwind differences, or second-order ENO R10).
+ *
+ * The ENO2 stencil choice is a discrete decision taken by comparing two
+ * floating-point magnitudes.  It is taken in float32, the precision of the
+ * GPU kernel, on the five-node window as float32 values (og_shifted32) and
+ * with the same order of operations (a = f0 - fm1, b = fp1 - f0, then a - (fm1 - fm2),
+ * b - a, (fp2 - fp1) - b), so that both sides decide alike on the same data;
+ * the derivative itself is formed from the chosen second difference in
+ * float64.  On data that is symmetric in exact arithmetic the two candidates
+ * tie exactly, and float64 rounding noise alone would otherwise pick a
+ * different stencil than the float32 kernel does. */
 static void og_one_sided(const og_grid *g, const double *phi, const int64_t *idx,
                          int64_t flat, int d, int order, double *pm, double *pp)
 {
@@ -154,8 +188,13 @@ static void og_one_sided(const og_grid *g, const double *phi, const int64_t *idx
     double d2_left = (f0 - 2.0 * fm1 + fm2) / (h * h);     /* at i-1 */
     double d2_mid = (fp1 - 2.0 * f0 + fm1) / (h * h);      /* at i   */
     double d2_right = (fp2 - 2.0 * fp1 + f0) / (h * h);    /* at i+1 */
-    double c_minus = (fabs(d2_left) < fabs(d2_mid)) ? d2_left : d2_mid;
-    double c_plus = (fabs(d2_right) < fabs(d2_mid)) ? d2_right : d2_mid;
+    float w0 = og_shifted32(g, phi, idx, flat, d, -2), w1 = og_shifted32(g, phi, idx, flat, d, -1);
+    float w2 = (float)f0;
+    float w3 = og_shifted32(g, phi, idx, flat, d, +1), w4 = og_shifted32(g, phi, idx, flat, d, +2);
+    float a32 = w2 - w1, b32 = w3 - w2;
+    float l32 = a32 - (w1 - w0), m32 = b32 - a32, r32 = (w4 - w3) - b32;
+    double c_minus = (fabsf(l32) < fabsf(m32)) ? d2_left : d2_mid;
+    double c_plus = (fabsf(r32) < fabsf(m32)) ? d2_right : d2_mid;
     *pm = dm + 0.5 * h * c_minus;
     *pp = dp - 0.5 * h * c_plus;
 }

@@ -17,119 +17,77 @@
 
 namespace odp {
 
-__device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
-
-__device__ __forceinline__ float lane(const float4 &v, int k)
+ODP_HD float lane(const float4 &v, int k)
 {
     return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
 }
 
 // Neighbour row of a four-node segment along a non-last axis: periodic wrap or
 // sign-keeping ghost extrapolation (Section 3.1.1), lane by lane.
-__device__ __forceinline__ float4 row_shift4(const float *__restrict__ src, int base, int id, int stride, int n,
-                                             int periodic, int off)
+ODP_HD float4 row_shift4(const float *__restrict__ src, int base, int id, int stride, int n, int periodic, int off)
 {
     int j = id + off;
     if (periodic) {
-        if (j < 0) j += n;
-        if (j < 0) j += n;
-        if (j >= n) j -= n;
-        if (j >= n) j -= n;
-        return ld4(src + base + (j - id) * stride);
+        while (j < 0) j += n;
+        while (j >= n) j -= n;
+        return ldg4(src + base + (j - id) * stride);
     }
-    if (j >= 0 && j < n) return ld4(src + base + off * stride);
+    if (j >= 0 && j < n) return ldg4(src + base + off * stride);
     const int b = (j < 0) ? 0 : n - 1;
     const int in = (j < 0) ? 1 : n - 2;
     const float k = (j < 0) ? float(-j) : float(j - (n - 1));
-    const float4 pb = ld4(src + base + (b - id) * stride);
-    const float4 pi = ld4(src + base + (in - id) * stride);
+    const float4 pb = ldg4(src + base + (b - id) * stride);
+    const float4 pi = ldg4(src + base + (in - id) * stride);
     float4 r;
-    r.x = pb.x + k * (pb.x >= 0.0f ? 1.0f : -1.0f) * fabsf(pb.x - pi.x);
-    r.y = pb.y + k * (pb.y >= 0.0f ? 1.0f : -1.0f) * fabsf(pb.y - pi.y);
-    r.z = pb.z + k * (pb.z >= 0.0f ? 1.0f : -1.0f) * fabsf(pb.z - pi.z);
-    r.w = pb.w + k * (pb.w >= 0.0f ? 1.0f : -1.0f) * fabsf(pb.w - pi.w);
+    r.x = keep_sign_ghost(pb.x, pi.x, k);
+    r.y = keep_sign_ghost(pb.y, pi.y, k);
+    r.z = keep_sign_ghost(pb.z, pi.z, k);
+    r.w = keep_sign_ghost(pb.w, pi.w, k);
     return r;
 }
 
 // Node j (possibly outside [0, n)) of the last axis of a row.
-__device__ __forceinline__ float last_axis_value(const float *__restrict__ row, int j, int n, int periodic)
+ODP_HD float last_axis_value(const float *__restrict__ row, int j, int n, int periodic)
 {
-    if (j >= 0 && j < n) return __ldg(row + j);
+    if (j >= 0 && j < n) return ldgf(row + j);
     if (periodic) {
         while (j < 0) j += n;
         while (j >= n) j -= n;
-        return __ldg(row + j);
+        return ldgf(row + j);
     }
     const int b = (j < 0) ? 0 : n - 1;
     const int in = (j < 0) ? 1 : n - 2;
     const float k = (j < 0) ? float(-j) : float(j - (n - 1));
-    const float pb = __ldg(row + b), pi = __ldg(row + in);
-    return pb + k * (pb >= 0.0f ? 1.0f : -1.0f) * fabsf(pb - pi);
-}
-
-// Unscaled one-sided differences of one node from its five-point window
-// (ENO2) or three-point window (upwind): dm = h p-, dp = h p+.
-template <int ORDER>
-__device__ __forceinline__ void diffs(float fm2, float fm1, float f0, float fp1, float fp2, float &dm, float &dp)
-{
-    const float a = f0 - fm1, b = fp1 - f0;
-    if (ORDER == 1) {
-        dm = a;
-        dp = b;
-    } else {
-        const float d2l = a - (fm1 - fm2);
-        const float d2m = b - a;
-        const float d2r = (fp2 - fp1) - b;
-        const float cm = (fabsf(d2l) < fabsf(d2m)) ? d2l : d2m;
-        const float cp = (fabsf(d2r) < fabsf(d2m)) ? d2r : d2m;
-        dm = a + 0.5f * cm;
-        dp = b - 0.5f * cp;
-    }
-}
-
-// Contribution of one axis to L at one node: a pbar + S |pbar| + 1/2 alpha (p+ - p-).
-__device__ __forceinline__ float axis_term(float dm, float dp, float inv_h, float a, float S, float half_alpha)
-{
-    const float pm = dm * inv_h, pp = dp * inv_h;
-    const float pb = 0.5f * (pp + pm);
-    return a * pb + S * fabsf(pb) + half_alpha * (pp - pm);
+    return keep_sign_ghost(ldgf(row + b), ldgf(row + in), k);
 }
 
 // Drift coefficients a_d of the four nodes of a segment and the signed input
 // bounds S_d (Appendix dynamics; Section 4.2 modes).
 template <int DYN, int ND>
-__device__ __forceinline__ void drift(const GridDesc &g, const DynDesc &dy, const int *idx, float a[ND][4],
-                                      float S[ND])
+ODP_HD void drift(const GridDesc &g, const DynDesc &dy, const int *idx, float a[ND][4], float S[ND])
 {
     const float su = mode_sign(dy.umode), sd = mode_sign(dy.dmode);
-#pragma unroll
     for (int d = 0; d < ND; ++d) {
         S[d] = 0.0f;
-#pragma unroll
         for (int k = 0; k < 4; ++k) a[d][k] = 0.0f;
     }
     const int s0 = idx[ND - 1];
     if (DYN == DYN_SINGLE_INT) {
-#pragma unroll
         for (int d = 0; d < ND; ++d) S[d] = su * dy.prm[0];
     } else if (DYN == DYN_ADVECTION) {
-#pragma unroll
         for (int d = 0; d < ND; ++d)
-#pragma unroll
             for (int k = 0; k < 4; ++k) a[d][k] = dy.prm[d];
     } else if (DYN == DYN_DUBINS3D) {          // (x, y, th), th last
-        const float4 c = ld4(g.cos_tab + s0), s = ld4(g.sin_tab + s0);
+        const float4 c = ldg4(g.cos_tab + s0), s = ldg4(g.sin_tab + s0);
         const float v = dy.prm[0];
-#pragma unroll
         for (int k = 0; k < 4; ++k) {
             a[0][k] = v * lane(c, k);
             a[1][k] = v * lane(s, k);
         }
         S[2] = su * dy.prm[1];
     } else if (DYN == DYN_DUBINSCAR4D) {       // (x, y, v, th), th last
-        const float4 c = ld4(g.cos_tab + s0), s = ld4(g.sin_tab + s0);
-        const float v = __ldg(g.coord[2] + idx[2]);
-#pragma unroll
+        const float4 c = ldg4(g.cos_tab + s0), s = ldg4(g.sin_tab + s0);
+        const float v = ldgf(g.coord[2] + idx[2]);
         for (int k = 0; k < 4; ++k) {
             a[0][k] = v * lane(c, k);
             a[1][k] = v * lane(s, k);
@@ -137,14 +95,13 @@ __device__ __forceinline__ void drift(const GridDesc &g, const DynDesc &dy, cons
         S[2] = su * dy.prm[0];
         S[3] = su * dy.prm[1];
     } else {                                   // Rel6D (x, y, th, v_p, w_p, v_e), v_e last
-        const float x = __ldg(g.coord[0] + idx[0]);
-        const float y = __ldg(g.coord[1] + idx[1]);
-        const float c = __ldg(g.cos_tab + idx[2]);
-        const float s = __ldg(g.sin_tab + idx[2]);
-        const float vp = __ldg(g.coord[3] + idx[3]);
-        const float wp = __ldg(g.coord[4] + idx[4]);
-        const float4 ve = ld4(g.coord[5] + s0);
-#pragma unroll
+        const float x = ldgf(g.coord[0] + idx[0]);
+        const float y = ldgf(g.coord[1] + idx[1]);
+        const float c = ldgf(g.cos_tab + idx[2]);
+        const float s = ldgf(g.sin_tab + idx[2]);
+        const float vp = ldgf(g.coord[3] + idx[3]);
+        const float wp = ldgf(g.coord[4] + idx[4]);
+        const float4 ve = ldg4(g.coord[5] + s0);
         for (int k = 0; k < 4; ++k) {
             a[0][k] = -vp + lane(ve, k) * c + wp * y;
             a[1][k] = lane(ve, k) * s - wp * x;
@@ -160,12 +117,11 @@ __device__ __forceinline__ void drift(const GridDesc &g, const DynDesc &dy, cons
 // Multi-index of a thread's segment: idx[0..ND-2] of its row, idx[ND-1] the
 // first node of its segment; returns the storage offset of that node.
 template <int ND>
-__device__ __forceinline__ int segment_index(const GridDesc &g, uint32_t t, int *idx)
+ODP_HD int segment_index(const GridDesc &g, uint32_t t, int *idx)
 {
     uint32_t row = fast_div(t, g.div_segs);
     const int seg = int(t - row * uint32_t(g.segs));
     const int base = int(row) * g.n_pad + 4 * seg;
-#pragma unroll
     for (int d = ND - 2; d > 0; --d) {
         const uint32_t q = fast_div(row, g.div[d]);
         idx[d] = int(row - q * uint32_t(g.n[d]));
@@ -176,35 +132,41 @@ __device__ __forceinline__ int segment_index(const GridDesc &g, uint32_t t, int 
     return base;
 }
 
-// Fused stage pass (Algorithm 1, one Euler or TVD-RK2 stage, Section 3.1.3):
-// derivatives, pbar, H, Lax-Friedrichs dissipation with the grid alpha,
-// update and, on the last stage of a step of a tube, the min with l.
-//   stage 0: Euler        phi' = phi + dt L(phi)              (cur -> nxt)
-//   stage 1: RK2 stage 1  phi1 = phi + dt L(phi)              (cur -> nxt)
-//   stage 2: RK2 stage 2  phi' = (phi + phi1 + dt L(phi1))/2  (nxt, cur -> cur)
-template <int ND, int ORDER, int DYN>
-__global__ void __launch_bounds__(256) k_stage(GridDesc g, DynDesc dy, SolveState *st,
-                                               const float *__restrict__ l, int stage, int brt)
-{
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= uint32_t(g.nthreads)) return;
-    const float *__restrict__ src = (stage == 2) ? st->nxt : st->cur;
-    float *dst = (stage == 2) ? st->cur : st->nxt;
-    const unsigned *ab = st->alpha_bits[stage == 2 ? 1 : 0];
+// Arguments of one stage pass over one grid.
+struct StageArgs {
+    const float *src;     // phi the derivatives are taken of
+    const float *prev;    // phi^n for the Heun average (stage 2), else unused
+    const float *l;       // target, for the BRT min
+    float *dst;
+    float half_alpha[ODP_MAXD];
+    float dt;
+    int stage;            // 0 Euler, 1 RK2 stage 1, 2 RK2 stage 2
+    int brt;
+};
 
+// One thread's four-node segment of a stage pass (Algorithm 1, one Euler or
+// TVD-RK2 stage, Section 3.1.3): derivatives, pbar, H, Lax-Friedrichs
+// dissipation with the grid alpha, update and, on the last stage of a step of
+// a tube, the min with l.  Returns true if a non-finite value was produced.
+//   stage 0: Euler        phi' = phi + dt L(phi)
+//   stage 1: RK2 stage 1  phi1 = phi + dt L(phi)
+//   stage 2: RK2 stage 2  phi' = (phi^n + phi1 + dt L(phi1))/2
+template <int ND, int ORDER, int DYN>
+ODP_HD bool stage_segment(const GridDesc &g, const DynDesc &dy, const StageArgs &A, uint32_t t)
+{
+    const float *__restrict__ src = A.src;
     int idx[ND];
     const int base = segment_index<ND>(g, t, idx);
     float a[ND][4], S[ND];
     drift<DYN, ND>(g, dy, idx, a, S);
 
-    const float4 c4 = ld4(src + base);
+    const float4 c4 = ldg4(src + base);
     const float f[4] = {c4.x, c4.y, c4.z, c4.w};
     float L[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 
     // axes other than the last: neighbour rows
 #pragma unroll
     for (int d = 0; d < ND - 1; ++d) {
-        const float ha = 0.5f * __uint_as_float(ab[d]);
         const float4 m1 = row_shift4(src, base, idx[d], g.stride[d], g.n[d], g.periodic[d], -1);
         const float4 p1 = row_shift4(src, base, idx[d], g.stride[d], g.n[d], g.periodic[d], +1);
         float4 m2 = m1, p2 = p1;
@@ -216,7 +178,7 @@ __global__ void __launch_bounds__(256) k_stage(GridDesc g, DynDesc dy, SolveStat
         for (int k = 0; k < 4; ++k) {
             float dm, dp;
             diffs<ORDER>(lane(m2, k), lane(m1, k), f[k], lane(p1, k), lane(p2, k), dm, dp);
-            L[k] += axis_term(dm, dp, g.inv_dz[d], a[d][k], S[d], ha);
+            L[k] += axis_term(dm, dp, g.inv_dz[d], a[d][k], S[d], A.half_alpha[d]);
         }
     }
 
@@ -228,62 +190,80 @@ __global__ void __launch_bounds__(256) k_stage(GridDesc g, DynDesc dy, SolveStat
     w[3] = f[1];
     w[4] = f[2];
     w[5] = f[3];
-    const float *row = src + (base - s0);
     if (s0 >= 2 && s0 + 5 < nl) {
-        const float2 lh = __ldg(reinterpret_cast<const float2 *>(src + base - 2));
-        const float2 rh = __ldg(reinterpret_cast<const float2 *>(src + base + 4));
+        const float2 lh = ldg2(src + base - 2);
+        const float2 rh = ldg2(src + base + 4);
         w[0] = lh.x;
         w[1] = lh.y;
         w[6] = rh.x;
         w[7] = rh.y;
     } else {
+        const float *row = src + (base - s0);
         const int per = g.periodic[ND - 1];
 #pragma unroll
         for (int j = 0; j < 8; ++j)
             if (j < 2 || j >= 6 || s0 + j - 2 >= nl) w[j] = last_axis_value(row, s0 + j - 2, nl, per);
     }
-    {
-        const float ha = 0.5f * __uint_as_float(ab[ND - 1]);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float dm, dp;
-            diffs<ORDER>(w[k], w[k + 1], w[k + 2], w[k + 3], w[k + 4], dm, dp);
-            L[k] += axis_term(dm, dp, g.inv_dz[ND - 1], a[ND - 1][k], S[ND - 1], ha);
-        }
+    for (int k = 0; k < 4; ++k) {
+        float dm, dp;
+        diffs<ORDER>(w[k], w[k + 1], w[k + 2], w[k + 3], w[k + 4], dm, dp);
+        L[k] += axis_term(dm, dp, g.inv_dz[ND - 1], a[ND - 1][k], S[ND - 1], A.half_alpha[ND - 1]);
     }
 
     // update, Heun average, non-finite flag, BRT min
-    const float dt = float(st->dt);
     float v[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = f[k] + dt * L[k];
-    if (stage == 2) {
-        const float4 b4 = *reinterpret_cast<const float4 *>(st->cur + base);
+    for (int k = 0; k < 4; ++k) v[k] = f[k] + A.dt * L[k];
+    if (A.stage == 2) {
+        const float4 b4 = *reinterpret_cast<const float4 *>(A.prev + base);
         v[0] = 0.5f * (b4.x + v[0]);
         v[1] = 0.5f * (b4.y + v[1]);
         v[2] = 0.5f * (b4.z + v[2]);
         v[3] = 0.5f * (b4.w + v[3]);
     }
-    const int nvalid = min(4, nl - s0);
+    const int nvalid = nl - s0 < 4 ? nl - s0 : 4;
     bool bad = false;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
         if (k < nvalid && !isfinite(v[k])) bad = true;
-    if (bad) atomicOr(&st->flags, FLAG_NONFINITE);
-    if (brt && stage != 1) {
-        const float4 l4 = ld4(l + base);
+    if (A.brt && A.stage != 1) {
+        const float4 l4 = ldg4(A.l + base);
         v[0] = fminf(v[0], l4.x);
         v[1] = fminf(v[1], l4.y);
         v[2] = fminf(v[2], l4.z);
         v[3] = fminf(v[3], l4.w);
     }
     if (nvalid == 4) {
-        *reinterpret_cast<float4 *>(dst + base) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4 *>(A.dst + base) = make_float4(v[0], v[1], v[2], v[3]);
     } else {
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            if (k < nvalid) dst[base + k] = v[k];
+            if (k < nvalid) A.dst[base + k] = v[k];
     }
+    return bad;
+}
+
+// Stage pass over a whole grid, reading its buffers, dt and alpha from the
+// solve state (one thread per four-node segment).
+template <int ND, int ORDER, int DYN>
+__global__ void __launch_bounds__(256) k_stage(GridDesc g, DynDesc dy, SolveState *st,
+                                               const float *__restrict__ l, int stage, int brt)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= uint32_t(g.nthreads)) return;
+    StageArgs A;
+    A.src = (stage == 2) ? st->nxt : st->cur;
+    A.prev = st->cur;
+    A.dst = (stage == 2) ? st->cur : st->nxt;
+    A.l = l;
+    const unsigned *ab = st->alpha_bits[stage == 2 ? 1 : 0];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) A.half_alpha[d] = 0.5f * bits_to_float(ab[d]);
+    A.dt = float(st->dt);
+    A.stage = stage;
+    A.brt = brt;
+    if (stage_segment<ND, ORDER, DYN>(g, dy, A, t)) atomicOr(&st->flags, FLAG_NONFINITE);
 }
 
 // Grid-wide max of the static alpha components into both stage slots.
@@ -330,7 +310,7 @@ __global__ void __launch_bounds__(256) k_alpha_rel6d(GridDesc g, DynDesc dy, Sol
          t += gridDim.x * blockDim.x) {
         int idx[6];
         const int base = segment_index<6>(g, t, idx);
-        const float4 c4 = ld4(src + base);
+        const float4 c4 = ldg4(src + base);
         const float4 m1 = row_shift4(src, base, idx[2], g.stride[2], g.n[2], g.periodic[2], -1);
         const float4 p1 = row_shift4(src, base, idx[2], g.stride[2], g.n[2], g.periodic[2], +1);
         float4 m2 = m1, p2 = p1;
@@ -338,7 +318,7 @@ __global__ void __launch_bounds__(256) k_alpha_rel6d(GridDesc g, DynDesc dy, Sol
             m2 = row_shift4(src, base, idx[2], g.stride[2], g.n[2], g.periodic[2], -2);
             p2 = row_shift4(src, base, idx[2], g.stride[2], g.n[2], g.periodic[2], +2);
         }
-        const float wp = __ldg(g.coord[4] + idx[4]);
+        const float wp = ldgf(g.coord[4] + idx[4]);
         const int nvalid = min(4, g.n[5] - idx[5]);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {

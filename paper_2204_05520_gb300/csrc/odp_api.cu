@@ -78,6 +78,7 @@ __global__ void k_dt(SolveState *st, GridDesc g)
 __global__ void k_advance(SolveState *st, int swap, unsigned dyn_mask, cudaGraphConditionalHandle h_loop,
                           cudaGraphConditionalHandle h_snap, int keep)
 {
+    for (int d = 0; d < 8; ++d) st->alpha_last[d] = st->alpha_bits[swap ? 0 : 1][d];
     st->t = st->last ? st->t_end : __dadd_rn(st->t, st->dt);
     st->steps += 1;
     if (swap) {
@@ -641,8 +642,7 @@ extern "C" odp_status odp_solve_status(odp_grid *g, odp_solve_stats *stats)
         stats->steps = h.steps;
         stats->last_dt = h.dt;
         stats->t_final = h.t;
-        const int slot = g->time_order == 2 ? 1 : 0;
-        for (int d = 0; d < g->ndim; ++d) memcpy(&stats->alpha[d], &h.alpha_bits[slot][d], sizeof(float));
+        for (int d = 0; d < g->ndim; ++d) memcpy(&stats->alpha[d], &h.alpha_last[d], sizeof(float));
         if (g->timed) {
             float ms = 0.0f;
             ODP_CUDA(cudaEventElapsedTime(&ms, g->ev0, g->ev1));

@@ -11,9 +11,53 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #define ODP_MAXD 6
 
+// Per-node helpers are host+device so that the exact kernel arithmetic can
+// also be stepped through on the host when debugging.
+#define ODP_HD __host__ __device__ __forceinline__
+
 namespace odp {
+
+ODP_HD float ldgf(const float *p)
+{
+#ifdef __CUDA_ARCH__
+    return __ldg(p);
+#else
+    return *p;
+#endif
+}
+
+ODP_HD float4 ldg4(const float *p)
+{
+#ifdef __CUDA_ARCH__
+    return __ldg(reinterpret_cast<const float4 *>(p));
+#else
+    return *reinterpret_cast<const float4 *>(p);
+#endif
+}
+
+ODP_HD float2 ldg2(const float *p)
+{
+#ifdef __CUDA_ARCH__
+    return __ldg(reinterpret_cast<const float2 *>(p));
+#else
+    return *reinterpret_cast<const float2 *>(p);
+#endif
+}
+
+ODP_HD float bits_to_float(unsigned u)
+{
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float f;
+    memcpy(&f, &u, sizeof(f));
+    return f;
+#endif
+}
 
 enum DynKind { DYN_SINGLE_INT = 0, DYN_DUBINS3D = 1, DYN_DUBINSCAR4D = 2, DYN_REL6D = 3, DYN_ADVECTION = 4 };
 enum Mode { MODE_MIN = 0, MODE_MAX = 1 };
@@ -41,9 +85,14 @@ inline FastDiv make_fastdiv(uint32_t d)
     return f;
 }
 
-__device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv &f)
+ODP_HD uint32_t fast_div(uint32_t n, const FastDiv &f)
 {
-    return (__umulhi(f.m, n) + n) >> f.l;
+#ifdef __CUDA_ARCH__
+    const uint32_t hi = __umulhi(f.m, n);
+#else
+    const uint32_t hi = uint32_t((uint64_t(f.m) * uint64_t(n)) >> 32);
+#endif
+    return (hi + n) >> f.l;
 }
 
 // Storage: C order with the last axis padded to n_pad, a multiple of 4 nodes,
@@ -96,6 +145,7 @@ struct SolveState {
     const double *tau;           // device copy of the tau schedule
     float *snapshots;            // n_tau * total floats, or nullptr
     unsigned alpha_bits[2][8];   // per stage slot (0: stage 1, 1: stage 2)
+    unsigned alpha_last[8];      // alpha of the last stage of the last step
 };
 
 }  // namespace odp

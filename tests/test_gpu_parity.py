@@ -77,9 +77,10 @@ def check_parity(problem, keep=False):
     return err / (l.max() - l.min())
 
 
-def check_parity_resync(problem, segments=None, tau=None):
+def check_parity_resync(problem, segments=None, tau=None, compare=None):
     """ENO2 route: the GPU solves over a schedule of short segments keeping
-    every snapshot; the oracle advances each kept GPU value over its segment."""
+    every snapshot; the oracle advances each kept GPU value over its segment
+    (every segment, or those listed in `compare`)."""
     if tau is None:
         tau = tuple(np.linspace(0.0, problem.tau[-1], segments + 1))
     p = dataclasses.replace(problem, tau=tuple(float(t) for t in tau))
@@ -89,13 +90,16 @@ def check_parity_resync(problem, segments=None, tau=None):
     worst = 0.0
     steps = 0
     for k in range(len(tau) - 1):
+        if compare is not None and k not in compare:
+            continue
         seg = dataclasses.replace(problem, tau=(0.0, float(tau[k + 1] - tau[k])))
         ref = oracle.solve(seg, l=l, phi0=snaps[k])
         steps += int(ref["steps"].sum())
         err = float(np.abs(snaps[k + 1] - ref["final"]).max())
         worst = max(worst, err)
         assert err <= tol, "segment %d: max err %.3g > tol %.3g" % (k, err, tol)
-    assert stats["steps"] == steps
+    if compare is None:
+        assert stats["steps"] == steps
     return worst / float(l.max() - l.min())
 
 
@@ -227,9 +231,9 @@ def test_dubinscar4d_full_size_step_matches_oracle():
 
 
 def test_dubinscar4d_full_size_segments_match_oracle():
-    # early and late segments of a full-horizon solve, a few steps each
+    # a few steps from the GPU state at t = 1 and at t = 2.95
     p = inputs.dubinscar4d()
-    rel = check_parity_resync(p, tau=(0.0, 1.0, 1.03, 2.95, 3.0))
+    rel = check_parity_resync(p, tau=(0.0, 1.0, 1.03, 2.95, 3.0), compare=(1, 3))
     assert rel <= REL_TOL
 
 
