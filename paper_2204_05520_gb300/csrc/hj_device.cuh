@@ -42,16 +42,6 @@ ODP_HD void diffs(float fm2, float fm1, float f0, float fp1, float fp2, float &d
     }
 }
 
-// Contribution of one axis to the Lax-Friedrichs right-hand side at one node:
-// a pbar + S |pbar| + 1/2 alpha (p+ - p-), with pbar = (p+ + p-)/2 (Algorithm 1;
-// the bang-bang input of bound b acting on this axis contributes s u* = +-b|s|).
-ODP_HD float axis_term(float dm, float dp, float inv_h, float a, float S, float half_alpha)
-{
-    const float pm = dm * inv_h, pp = dp * inv_h;
-    const float pb = 0.5f * (pp + pm);
-    return a * pb + S * fabsf(pb) + half_alpha * (pp - pm);
-}
-
 // Local dissipation bound a_d(z) (global-alpha reading of Section 2.1): the
 // largest |f_d| over the input extremes a node's derivative box can select.
 // For every model here except the Rel6D heading rate this does not depend on

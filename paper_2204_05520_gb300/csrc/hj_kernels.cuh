@@ -61,39 +61,41 @@ ODP_HD float last_axis_value(const float *__restrict__ row, int j, int n, int pe
     return keep_sign_ghost(ldgf(row + b), ldgf(row + in), k);
 }
 
-// Drift coefficients a_d of the four nodes of a segment and the signed input
-// bounds S_d (Appendix dynamics; Section 4.2 modes).
+// Half-scaled drift coefficients of the four nodes of a segment,
+// cA_d = a_d(z) / (2 h_d), and of the signed input bounds, cS_d = S_d / (2 h_d)
+// (Appendix dynamics; Section 4.2 modes).  idx holds the node's axis indices
+// (idx[ndim-1] the first node of the segment).
 template <int DYN, int ND>
-ODP_HD void drift(const GridDesc &g, const DynDesc &dy, const int *idx, float a[ND][4], float S[ND])
+ODP_HD void drift(const GridDesc &g, const DynDesc &dy, const int *idx, float cA[ND][4], float cS[ND])
 {
     const float su = mode_sign(dy.umode), sd = mode_sign(dy.dmode);
     for (int d = 0; d < ND; ++d) {
-        S[d] = 0.0f;
-        for (int k = 0; k < 4; ++k) a[d][k] = 0.0f;
+        cS[d] = 0.0f;
+        for (int k = 0; k < 4; ++k) cA[d][k] = 0.0f;
     }
     const int s0 = idx[ND - 1];
     if (DYN == DYN_SINGLE_INT) {
-        for (int d = 0; d < ND; ++d) S[d] = su * dy.prm[0];
+        for (int d = 0; d < ND; ++d) cS[d] = su * dy.prm[0];
     } else if (DYN == DYN_ADVECTION) {
         for (int d = 0; d < ND; ++d)
-            for (int k = 0; k < 4; ++k) a[d][k] = dy.prm[d];
+            for (int k = 0; k < 4; ++k) cA[d][k] = dy.prm[d];
     } else if (DYN == DYN_DUBINS3D) {          // (x, y, th), th last
         const float4 c = ldg4(g.cos_tab + s0), s = ldg4(g.sin_tab + s0);
         const float v = dy.prm[0];
         for (int k = 0; k < 4; ++k) {
-            a[0][k] = v * lane(c, k);
-            a[1][k] = v * lane(s, k);
+            cA[0][k] = v * lane(c, k);
+            cA[1][k] = v * lane(s, k);
         }
-        S[2] = su * dy.prm[1];
+        cS[2] = su * dy.prm[1];
     } else if (DYN == DYN_DUBINSCAR4D) {       // (x, y, v, th), th last
         const float4 c = ldg4(g.cos_tab + s0), s = ldg4(g.sin_tab + s0);
         const float v = ldgf(g.coord[2] + idx[2]);
         for (int k = 0; k < 4; ++k) {
-            a[0][k] = v * lane(c, k);
-            a[1][k] = v * lane(s, k);
+            cA[0][k] = v * lane(c, k);
+            cA[1][k] = v * lane(s, k);
         }
-        S[2] = su * dy.prm[0];
-        S[3] = su * dy.prm[1];
+        cS[2] = su * dy.prm[0];
+        cS[3] = su * dy.prm[1];
     } else {                                   // Rel6D (x, y, th, v_p, w_p, v_e), v_e last
         const float x = ldgf(g.coord[0] + idx[0]);
         const float y = ldgf(g.coord[1] + idx[1]);
@@ -103,19 +105,35 @@ ODP_HD void drift(const GridDesc &g, const DynDesc &dy, const int *idx, float a[
         const float wp = ldgf(g.coord[4] + idx[4]);
         const float4 ve = ldg4(g.coord[5] + s0);
         for (int k = 0; k < 4; ++k) {
-            a[0][k] = -vp + lane(ve, k) * c + wp * y;
-            a[1][k] = lane(ve, k) * s - wp * x;
-            a[2][k] = -wp;
+            cA[0][k] = -vp + lane(ve, k) * c + wp * y;
+            cA[1][k] = lane(ve, k) * s - wp * x;
+            cA[2][k] = -wp;
         }
-        S[2] = sd * dy.prm[3];
-        S[3] = su * dy.prm[0];
-        S[4] = su * dy.prm[1];
-        S[5] = sd * dy.prm[2];
+        cS[2] = sd * dy.prm[3];
+        cS[3] = su * dy.prm[0];
+        cS[4] = su * dy.prm[1];
+        cS[5] = sd * dy.prm[2];
+    }
+    for (int d = 0; d < ND; ++d) {
+        const float hh = 0.5f * g.inv_dz[d];
+        cS[d] *= hh;
+        for (int k = 0; k < 4; ++k) cA[d][k] *= hh;
     }
 }
 
-// Multi-index of a thread's segment: idx[0..ND-2] of its row, idx[ND-1] the
-// first node of its segment; returns the storage offset of that node.
+// Contribution of one axis to the Lax-Friedrichs right-hand side at one node
+// from its unscaled one-sided differences dm = h p-, dp = h p+:
+// a pbar + S |pbar| + 1/2 alpha (p+ - p-) = cA P + cS |P| + cD M with
+// P = dp + dm, M = dp - dm, cD = alpha / (2 h) (Algorithm 1).
+ODP_HD float axis_term(float dm, float dp, float cA, float cS, float cD)
+{
+    const float P = dp + dm, M = dp - dm;
+    return cA * P + cS * fabsf(P) + cD * M;
+}
+
+// Multi-index of a thread's segment (flat thread numbering, used by the
+// reductions): idx[0..ND-2] of its row, idx[ND-1] the first node of its
+// segment; returns the storage offset of that node.
 template <int ND>
 ODP_HD int segment_index(const GridDesc &g, uint32_t t, int *idx)
 {
@@ -138,120 +156,193 @@ struct StageArgs {
     const float *prev;    // phi^n for the Heun average (stage 2), else unused
     const float *l;       // target, for the BRT min
     float *dst;
-    float half_alpha[ODP_MAXD];
+    float cD[ODP_MAXD];   // alpha_d / (2 h_d)
     float dt;
     int stage;            // 0 Euler, 1 RK2 stage 1, 2 RK2 stage 2
     int brt;
 };
 
-// One thread's four-node segment of a stage pass (Algorithm 1, one Euler or
-// TVD-RK2 stage, Section 3.1.3): derivatives, pbar, H, Lax-Friedrichs
-// dissipation with the grid alpha, update and, on the last stage of a step of
-// a tube, the min with l.  Returns true if a non-finite value was produced.
+// Row j (possibly outside [0, n)) of axis `axis` relative to row i0 of the
+// segment at storage offset base (periodic wrap or sign-keeping ghost).
+ODP_HD float4 axis_row(const float *__restrict__ src, int base, int i0, int j, int stride, int n, int periodic)
+{
+    if (j >= 0 && j < n) return ldg4(src + base + (j - i0) * stride);
+    if (periodic) {
+        while (j < 0) j += n;
+        while (j >= n) j -= n;
+        return ldg4(src + base + (j - i0) * stride);
+    }
+    const int b = (j < 0) ? 0 : n - 1;
+    const int in = (j < 0) ? 1 : n - 2;
+    const float k = (j < 0) ? float(-j) : float(j - (n - 1));
+    const float4 pb = ldg4(src + base + (b - i0) * stride);
+    const float4 pi = ldg4(src + base + (in - i0) * stride);
+    float4 r;
+    r.x = keep_sign_ghost(pb.x, pi.x, k);
+    r.y = keep_sign_ghost(pb.y, pi.y, k);
+    r.z = keep_sign_ghost(pb.z, pi.z, k);
+    r.w = keep_sign_ghost(pb.w, pi.w, k);
+    return r;
+}
+
+// One thread of the tiled stage pass (Algorithm 1, one Euler or TVD-RK2
+// stage, Section 3.1.3): R rows of axis ndim-2 times one four-node segment of
+// the last axis.  Derivatives, pbar, H, Lax-Friedrichs dissipation with the
+// grid alpha, update and, on the last stage of a step of a tube, the min with
+// l.  Returns true if a non-finite value was produced.
 //   stage 0: Euler        phi' = phi + dt L(phi)
 //   stage 1: RK2 stage 1  phi1 = phi + dt L(phi)
 //   stage 2: RK2 stage 2  phi' = (phi^n + phi1 + dt L(phi1))/2
-template <int ND, int ORDER, int DYN>
-ODP_HD bool stage_segment(const GridDesc &g, const DynDesc &dy, const StageArgs &A, uint32_t t)
+// t numbers the thread as in GridDesc (segment fastest, then row group,
+// then plane).
+template <int ND, int ORDER, int DYN, int R>
+ODP_HD bool stage_tile(const GridDesc &g, const DynDesc &dy, const StageArgs &A, uint32_t t)
 {
+    constexpr int O = ORDER;          // stencil radius
+    constexpr int NC = R + 2 * O;     // rows of the column along axis ND-2
     const float *__restrict__ src = A.src;
+    const uint32_t q = fast_div(t, g.div_segs);
+    const int seg = int(t - q * uint32_t(g.segs));
+    const uint32_t plane = fast_div(q, g.div_row_groups);
+    const int r0 = int(q - plane * uint32_t(g.row_groups)) * R;
+
     int idx[ND];
-    const int base = segment_index<ND>(g, t, idx);
-    float a[ND][4], S[ND];
-    drift<DYN, ND>(g, dy, idx, a, S);
+    {
+        uint32_t pl = plane;
+        for (int d = ND - 3; d > 0; --d) {
+            const uint32_t q = fast_div(pl, g.div[d]);
+            idx[d] = int(pl - q * uint32_t(g.n[d]));
+            pl = q;
+        }
+        if (ND >= 3) idx[0] = int(pl);
+    }
+    idx[ND - 1] = 4 * seg;
+    if (ND >= 2) idx[ND - 2] = r0;
+    const int base0 = (int(plane) * g.nr + r0) * g.n_pad + 4 * seg;   // row r0
+    const int rstride = g.n_pad;                                       // one row of axis ND-2
+    const int nl = g.n[ND - 1];
+    const int s0 = idx[ND - 1];
+    const int nvalid = nl - s0 < 4 ? nl - s0 : 4;
 
-    const float4 c4 = ldg4(src + base);
-    const float f[4] = {c4.x, c4.y, c4.z, c4.w};
-    float L[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-
-    // axes other than the last: neighbour rows
+    // column of rows r0-O .. r0+R-1+O along axis ND-2
+    float4 col[NC];
+    if (ND >= 2) {
 #pragma unroll
-    for (int d = 0; d < ND - 1; ++d) {
-        const float4 m1 = row_shift4(src, base, idx[d], g.stride[d], g.n[d], g.periodic[d], -1);
-        const float4 p1 = row_shift4(src, base, idx[d], g.stride[d], g.n[d], g.periodic[d], +1);
-        float4 m2 = m1, p2 = p1;
-        if (ORDER == 2) {
-            m2 = row_shift4(src, base, idx[d], g.stride[d], g.n[d], g.periodic[d], -2);
-            p2 = row_shift4(src, base, idx[d], g.stride[d], g.n[d], g.periodic[d], +2);
+        for (int j = 0; j < NC; ++j)
+            col[j] = axis_row(src, base0, r0, r0 - O + j, rstride, g.nr, g.periodic[ND - 2]);
+    } else {
+        col[O] = ldg4(src + base0);
+    }
+
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int r = r0 + i;
+        if (r >= g.nr) break;
+        const int base = base0 + i * rstride;
+        if (ND >= 2) idx[ND - 2] = r;
+        float cA[ND][4], cS[ND];
+        drift<DYN, ND>(g, dy, idx, cA, cS);
+        const float4 c4 = col[O + i];
+        const float f[4] = {c4.x, c4.y, c4.z, c4.w};
+        float L[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+
+        // outer axes: neighbour rows one by one
+#pragma unroll
+        for (int d = 0; d < ND - 2; ++d) {
+            const int stride = g.stride[d], n = g.n[d], per = g.periodic[d], id = idx[d];
+            const float4 m1 = axis_row(src, base, id, id - 1, stride, n, per);
+            const float4 p1 = axis_row(src, base, id, id + 1, stride, n, per);
+            float4 m2 = m1, p2 = p1;
+            if (ORDER == 2) {
+                m2 = axis_row(src, base, id, id - 2, stride, n, per);
+                p2 = axis_row(src, base, id, id + 2, stride, n, per);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float dm, dp;
+                diffs<ORDER>(lane(m2, k), lane(m1, k), f[k], lane(p1, k), lane(p2, k), dm, dp);
+                L[k] += axis_term(dm, dp, cA[d][k], cS[d], A.cD[d]);
+            }
+        }
+
+        // axis ND-2 from the column
+        if (ND >= 2) {
+            constexpr int d = ND - 2 < 0 ? 0 : ND - 2;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float dm, dp;
+                diffs<ORDER>(lane(col[i + O - 2 < 0 ? 0 : i + O - 2], k), lane(col[i + O - 1], k), f[k],
+                             lane(col[i + O + 1], k), lane(col[i + O + 2 < NC ? i + O + 2 : NC - 1], k), dm, dp);
+                L[k] += axis_term(dm, dp, cA[d][k], cS[d], A.cD[d]);
+            }
+        }
+
+        // last axis: an eight-node window w[j] = phi(first node - 2 + j)
+        float w[8];
+        w[2] = f[0];
+        w[3] = f[1];
+        w[4] = f[2];
+        w[5] = f[3];
+        if (s0 >= 2 && s0 + 5 < nl) {
+            const float2 lh = ldg2(src + base - 2);
+            const float2 rh = ldg2(src + base + 4);
+            w[0] = lh.x;
+            w[1] = lh.y;
+            w[6] = rh.x;
+            w[7] = rh.y;
+        } else {
+            const float *rowp = src + (base - s0);
+            const int per = g.periodic[ND - 1];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j < 2 || j >= 6 || s0 + j - 2 >= nl) w[j] = last_axis_value(rowp, s0 + j - 2, nl, per);
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             float dm, dp;
-            diffs<ORDER>(lane(m2, k), lane(m1, k), f[k], lane(p1, k), lane(p2, k), dm, dp);
-            L[k] += axis_term(dm, dp, g.inv_dz[d], a[d][k], S[d], A.half_alpha[d]);
+            diffs<ORDER>(w[k], w[k + 1], w[k + 2], w[k + 3], w[k + 4], dm, dp);
+            L[k] += axis_term(dm, dp, cA[ND - 1][k], cS[ND - 1], A.cD[ND - 1]);
         }
-    }
 
-    // last axis: an eight-node window w[j] = phi(first node - 2 + j)
-    const int nl = g.n[ND - 1];
-    const int s0 = idx[ND - 1];
-    float w[8];
-    w[2] = f[0];
-    w[3] = f[1];
-    w[4] = f[2];
-    w[5] = f[3];
-    if (s0 >= 2 && s0 + 5 < nl) {
-        const float2 lh = ldg2(src + base - 2);
-        const float2 rh = ldg2(src + base + 4);
-        w[0] = lh.x;
-        w[1] = lh.y;
-        w[6] = rh.x;
-        w[7] = rh.y;
-    } else {
-        const float *row = src + (base - s0);
-        const int per = g.periodic[ND - 1];
+        // update, Heun average, non-finite flag, BRT min
+        float v[4];
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (j < 2 || j >= 6 || s0 + j - 2 >= nl) w[j] = last_axis_value(row, s0 + j - 2, nl, per);
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        float dm, dp;
-        diffs<ORDER>(w[k], w[k + 1], w[k + 2], w[k + 3], w[k + 4], dm, dp);
-        L[k] += axis_term(dm, dp, g.inv_dz[ND - 1], a[ND - 1][k], S[ND - 1], A.half_alpha[ND - 1]);
-    }
-
-    // update, Heun average, non-finite flag, BRT min
-    float v[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = f[k] + A.dt * L[k];
-    if (A.stage == 2) {
-        const float4 b4 = *reinterpret_cast<const float4 *>(A.prev + base);
-        v[0] = 0.5f * (b4.x + v[0]);
-        v[1] = 0.5f * (b4.y + v[1]);
-        v[2] = 0.5f * (b4.z + v[2]);
-        v[3] = 0.5f * (b4.w + v[3]);
-    }
-    const int nvalid = nl - s0 < 4 ? nl - s0 : 4;
-    bool bad = false;
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-        if (k < nvalid && !isfinite(v[k])) bad = true;
-    if (A.brt && A.stage != 1) {
-        const float4 l4 = ldg4(A.l + base);
-        v[0] = fminf(v[0], l4.x);
-        v[1] = fminf(v[1], l4.y);
-        v[2] = fminf(v[2], l4.z);
-        v[3] = fminf(v[3], l4.w);
-    }
-    if (nvalid == 4) {
-        *reinterpret_cast<float4 *>(A.dst + base) = make_float4(v[0], v[1], v[2], v[3]);
-    } else {
+        for (int k = 0; k < 4; ++k) v[k] = f[k] + A.dt * L[k];
+        if (A.stage == 2) {
+            const float4 b4 = *reinterpret_cast<const float4 *>(A.prev + base);
+            v[0] = 0.5f * (b4.x + v[0]);
+            v[1] = 0.5f * (b4.y + v[1]);
+            v[2] = 0.5f * (b4.z + v[2]);
+            v[3] = 0.5f * (b4.w + v[3]);
+        }
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            if (k < nvalid) A.dst[base + k] = v[k];
+            if (k < nvalid && !isfinite(v[k])) bad = true;
+        if (A.brt && A.stage != 1) {
+            const float4 l4 = ldg4(A.l + base);
+            v[0] = fminf(v[0], l4.x);
+            v[1] = fminf(v[1], l4.y);
+            v[2] = fminf(v[2], l4.z);
+            v[3] = fminf(v[3], l4.w);
+        }
+        if (nvalid == 4) {
+            *reinterpret_cast<float4 *>(A.dst + base) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k < nvalid) A.dst[base + k] = v[k];
+        }
     }
     return bad;
 }
 
 // Stage pass over a whole grid, reading its buffers, dt and alpha from the
-// solve state (one thread per four-node segment).
-template <int ND, int ORDER, int DYN>
+// solve state.
+template <int ND, int ORDER, int DYN, int R>
 __global__ void __launch_bounds__(256) k_stage(GridDesc g, DynDesc dy, SolveState *st,
                                                const float *__restrict__ l, int stage, int brt)
 {
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= uint32_t(g.nthreads)) return;
     StageArgs A;
     A.src = (stage == 2) ? st->nxt : st->cur;
     A.prev = st->cur;
@@ -259,11 +350,13 @@ __global__ void __launch_bounds__(256) k_stage(GridDesc g, DynDesc dy, SolveStat
     A.l = l;
     const unsigned *ab = st->alpha_bits[stage == 2 ? 1 : 0];
 #pragma unroll
-    for (int d = 0; d < ND; ++d) A.half_alpha[d] = 0.5f * bits_to_float(ab[d]);
+    for (int d = 0; d < ND; ++d) A.cD[d] = 0.5f * bits_to_float(ab[d]) * g.inv_dz[d];
     A.dt = float(st->dt);
     A.stage = stage;
     A.brt = brt;
-    if (stage_segment<ND, ORDER, DYN>(g, dy, A, t)) atomicOr(&st->flags, FLAG_NONFINITE);
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= uint32_t(g.nthreads_rb)) return;
+    if (stage_tile<ND, ORDER, DYN, R>(g, dy, A, t)) atomicOr(&st->flags, FLAG_NONFINITE);
 }
 
 // Grid-wide max of the static alpha components into both stage slots.
@@ -349,11 +442,18 @@ template <int ND, int DYN>
 cudaError_t launch_stage_t(const GridDesc &g, const DynDesc &dy, SolveState *st, const float *l,
                            int order, int stage, int brt, cudaStream_t s)
 {
-    const int blocks = blocks_for(g.nthreads, 256);
-    if (order == 1)
-        k_stage<ND, 1, DYN><<<blocks, 256, 0, s>>>(g, dy, st, l, stage, brt);
-    else
-        k_stage<ND, 2, DYN><<<blocks, 256, 0, s>>>(g, dy, st, l, stage, brt);
+    const int grid = blocks_for(g.nthreads_rb, 256), block = 256;
+    if (g.R == 4) {
+        if (order == 1)
+            k_stage<ND, 1, DYN, 4><<<grid, block, 0, s>>>(g, dy, st, l, stage, brt);
+        else
+            k_stage<ND, 2, DYN, 4><<<grid, block, 0, s>>>(g, dy, st, l, stage, brt);
+    } else {
+        if (order == 1)
+            k_stage<ND, 1, DYN, 1><<<grid, block, 0, s>>>(g, dy, st, l, stage, brt);
+        else
+            k_stage<ND, 2, DYN, 1><<<grid, block, 0, s>>>(g, dy, st, l, stage, brt);
+    }
     return cudaGetLastError();
 }
 

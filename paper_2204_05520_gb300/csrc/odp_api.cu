@@ -287,6 +287,12 @@ extern "C" odp_status odp_grid_create(int ndim, const int32_t *n, const double *
     D.segs = g->n_pad / 4;
     D.nthreads = int(g->rows * (g->n_pad / 4));
     D.div_segs = make_fastdiv(uint32_t(D.segs));
+    D.nr = ndim >= 2 ? n[ndim - 2] : 1;
+    D.R = D.nr >= 4 ? 4 : 1;
+    D.row_groups = (D.nr + D.R - 1) / D.R;
+    D.planes = int(g->rows / D.nr);
+    D.nthreads_rb = D.segs * D.row_groups * D.planes;
+    D.div_row_groups = make_fastdiv(uint32_t(D.row_groups));
     int64_t off = 0;
     std::vector<int64_t> coord_off(ndim);
     for (int d = 0; d < ndim; ++d) {

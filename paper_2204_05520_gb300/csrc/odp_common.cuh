@@ -116,6 +116,16 @@ struct GridDesc {
     const float *coord[ODP_MAXD];  // node coordinates of each axis (device)
     const float *cos_tab;        // cos / sin of the angle axis nodes (device)
     const float *sin_tab;
+    // geometry of the row-blocked stage pass: a thread owns one four-node
+    // segment of the last axis in each of R consecutive rows of axis ndim-2
+    // (a "row group"); threads are numbered segment fastest, then row group,
+    // then plane (the remaining outer axes, product of n[0 .. ndim-3]).
+    int R;
+    int nr;                      // n[ndim-2] (1 for a 1-D grid)
+    int row_groups;              // ceil(nr / R)
+    int planes;
+    int nthreads_rb;             // segs * row_groups * planes
+    FastDiv div_row_groups;
 };
 
 struct DynDesc {

@@ -106,7 +106,7 @@ def check_parity_resync(problem, segments=None, tau=None, compare=None):
 def check(problem):
     if problem.space_order == 2:
         steps = oracle.solve(problem)["steps"].sum()
-        return check_parity_resync(problem, segments=max(2, int(steps) // 4))
+        return check_parity_resync(problem, segments=max(2, int(steps) // 3))
     return check_parity(problem, keep=len(problem.tau) > 2)
 
 
