@@ -438,10 +438,25 @@ inline int reduce_blocks(int64_t n)
     return b < 152 * 8 ? b : 152 * 8;
 }
 
+}  // namespace odp
+
+#include "hj_plane.cuh"
+
+namespace odp {
+
 template <int ND, int DYN>
 cudaError_t launch_stage_t(const GridDesc &g, const DynDesc &dy, SolveState *st, const float *l,
                            int order, int stage, int brt, cudaStream_t s)
 {
+    if constexpr (ND >= 3) {
+        if (g.pg.use && g.pg.smem[order - 1] > 0) {
+            if (order == 1)
+                k_stage_plane<ND, 1, DYN><<<g.pg.items, g.pg.threads, g.pg.smem[0], s>>>(g, dy, st, l, stage, brt);
+            else
+                k_stage_plane<ND, 2, DYN><<<g.pg.items, g.pg.threads, g.pg.smem[1], s>>>(g, dy, st, l, stage, brt);
+            return cudaGetLastError();
+        }
+    }
     const int grid = blocks_for(g.nthreads_rb, 256), block = 256;
     if (g.R == 4) {
         if (order == 1)
@@ -455,6 +470,19 @@ cudaError_t launch_stage_t(const GridDesc &g, const DynDesc &dy, SolveState *st,
             k_stage<ND, 2, DYN, 1><<<grid, block, 0, s>>>(g, dy, st, l, stage, brt);
     }
     return cudaGetLastError();
+}
+
+// Allow the plane-streaming kernels of one model the shared memory they need.
+template <int ND, int DYN>
+cudaError_t configure_stage_t()
+{
+    if constexpr (ND >= 3) {
+        const int bytes = 227 * 1024;
+        cudaError_t e = cudaFuncSetAttribute(k_stage_plane<ND, 1, DYN>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(k_stage_plane<ND, 2, DYN>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    }
+    return cudaSuccess;
 }
 
 template <int ND, int DYN>

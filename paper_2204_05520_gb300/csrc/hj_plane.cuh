@@ -1,0 +1,366 @@
+// hj_plane.cuh -- plane-streaming stage pass (K2) for grids of 3 or more
+// dimensions whose last two axes ("the plane") fit in shared memory.
+//
+// A CTA owns one pencil: fixed indices of axes 0..nd-4, a chunk of axis nd-3
+// (the stream axis).  It walks the chunk plane by plane.  Every plane it needs
+// is moved global -> shared by one bulk asynchronous copy (cp.async.bulk with
+// an mbarrier counting the bytes): the planes s-r .. s+r of the stream axis
+// live in a ring (one new plane per step of the walk), the planes at +-1, +-2
+// along every other outer axis are loaded per output plane.  Planes outside a
+// non-periodic axis are ghost planes formed in shared memory from the
+// boundary and inner planes (Section 3.1.1); the output plane is copied into a
+// halo-padded buffer whose halo rows and columns hold the wrap or ghost
+// values of the two in-plane axes.  The per-node arithmetic then reads only
+// shared memory, without boundary branches.
+#pragma once
+
+#include "hj_kernels.cuh"
+
+namespace odp {
+
+// ---------------------------------------------------------------------------
+// bulk asynchronous copy and mbarrier (inline PTX, sm_90+ forms)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity, giving up after a bounded number
+// of polls (the copies it waits for are then reported as failed).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t it = 0; it < (1u << 26); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// ghost plane k cells outside boundary plane pb with inner plane pi (Section 3.1.1)
+__device__ __forceinline__ void ghost_plane(float *dst, const float *pb, const float *pi, float k, int n,
+                                            int tid, int nthreads)
+{
+    for (int i = tid; i < n; i += nthreads) dst[i] = keep_sign_ghost(pb[i], pi[i], k);
+}
+
+// One plane-streaming stage pass.  ND >= 3.
+template <int ND, int ORDER, int DYN>
+__global__ void __launch_bounds__(256) k_stage_plane(GridDesc g, DynDesc dy, SolveState *st,
+                                                     const float *__restrict__ l, int stage, int brt)
+{
+    const PlaneGeom &pg = g.pg;
+    constexpr int O = ORDER;
+    constexpr int RING = 2 * O + 1;
+    constexpr int NOUT = ND - 3;            // outer axes with loaded neighbour planes
+    constexpr int NNB = NOUT * 2 * O;       // neighbour planes per output plane
+    extern __shared__ __align__(16) float smem[];
+    float *ring = smem;                                  // RING planes
+    float *nb = ring + RING * pg.plane;                  // NNB planes
+    float *ctr = nb + NNB * pg.plane;                    // (nr + 2 O) x cp, halo-padded output plane
+    uint64_t *bar = reinterpret_cast<uint64_t *>(ctr + (g.nr + 2 * O) * pg.cp);
+
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const float *__restrict__ src = (stage == 2) ? st->nxt : st->cur;
+    float *dst = (stage == 2) ? st->cur : st->nxt;
+    const float *prev = st->cur;
+    const unsigned *ab = st->alpha_bits[stage == 2 ? 1 : 0];
+    float cD[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) cD[d] = 0.5f * bits_to_float(ab[d]) * g.inv_dz[d];
+    const float dt = float(st->dt);
+
+    // this CTA's pencil: outer indices of axes 0..ND-4 and its chunk of axis ND-3
+    const uint32_t item = blockIdx.x;
+    const uint32_t outer = fast_div(item, pg.div_nchunks);
+    const int chunk = int(item - outer * uint32_t(pg.nchunks));
+    int idx[ND];
+    {
+        uint32_t o = outer;
+        for (int d = ND - 4; d > 0; --d) {
+            const uint32_t q = fast_div(o, g.div[d]);
+            idx[d] = int(o - q * uint32_t(g.n[d]));
+            o = q;
+        }
+        if (ND >= 4) idx[0] = int(o);
+    }
+    const int sa = ND - 3;                    // stream axis
+    const int s_begin = chunk * pg.chunk;
+    const int s_end = min(pg.ns, s_begin + pg.chunk);
+    const long long pencil = (long long)outer * pg.ns;   // plane index of (outer, s = 0)
+    const uint32_t pbytes = uint32_t(pg.plane) * 4u;
+
+    if (tid == 0) mbar_init(bar, 1);
+    __syncthreads();
+    uint32_t parity = 0;
+    bool ok = true;
+
+    auto ring_slot = [&](int p) -> float * {
+        int q = p % RING;
+        if (q < 0) q += RING;
+        return ring + q * pg.plane;
+    };
+    auto plane_ptr = [&](int s) -> const float * { return src + (pencil + s) * (long long)pg.plane; };
+
+    for (int s = s_begin; s < s_end && ok; ++s) {
+        // ---- issue the copies of this output plane -------------------------
+        const int first = (s == s_begin) ? s - O : s + O;   // ring planes still missing
+        if (tid == 0) {
+            fence_proxy_async();
+            uint32_t bytes = 0;
+            for (int p = first; p <= s + O; ++p) {
+                int q = p;
+                if (g.periodic[sa]) q = ((q % pg.ns) + pg.ns) % pg.ns;
+                if (q >= 0 && q < pg.ns) bytes += pbytes;
+            }
+#pragma unroll
+            for (int d = 0; d < NOUT; ++d)
+                for (int o = -O; o <= O; ++o) {
+                    if (o == 0) continue;
+                    int j = idx[d] + o;
+                    if (g.periodic[d]) j = ((j % g.n[d]) + g.n[d]) % g.n[d];
+                    if (j >= 0 && j < g.n[d]) bytes += pbytes;
+                }
+            mbar_arrive_expect_tx(bar, bytes);
+            for (int p = first; p <= s + O; ++p) {
+                int q = p;
+                if (g.periodic[sa]) q = ((q % pg.ns) + pg.ns) % pg.ns;
+                if (q >= 0 && q < pg.ns) bulk_g2s(ring_slot(p), plane_ptr(q), pbytes, bar);
+            }
+#pragma unroll
+            for (int d = 0; d < NOUT; ++d) {
+                int k = 0;
+                for (int o = -O; o <= O; ++o) {
+                    if (o == 0) continue;
+                    int j = idx[d] + o;
+                    if (g.periodic[d]) j = ((j % g.n[d]) + g.n[d]) % g.n[d];
+                    if (j >= 0 && j < g.n[d])
+                        bulk_g2s(nb + (d * 2 * O + k) * pg.plane,
+                                 plane_ptr(s) + (long long)(j - idx[d]) * g.stride[d], pbytes, bar);
+                    ++k;
+                }
+            }
+        }
+        ok = __syncthreads_and(mbar_wait_bounded(bar, parity) ? 1 : 0) != 0;
+        parity ^= 1u;
+        if (!ok) {
+            if (tid == 0) atomicOr(&st->flags, FLAG_COPY);
+            break;
+        }
+
+        // ---- ghost planes of non-periodic outer axes ------------------------
+        if (!g.periodic[sa]) {
+            for (int p = first; p <= s + O; ++p) {
+                if (p < 0) ghost_plane(ring_slot(p), ring_slot(0), ring_slot(1), float(-p), pg.plane, tid, nth);
+                if (p >= pg.ns)
+                    ghost_plane(ring_slot(p), ring_slot(pg.ns - 1), ring_slot(pg.ns - 2), float(p - pg.ns + 1),
+                                pg.plane, tid, nth);
+            }
+        }
+        const float *center = ring_slot(s);
+#pragma unroll
+        for (int d = 0; d < NOUT; ++d) {
+            if (g.periodic[d]) continue;
+            float *base = nb + d * 2 * O * pg.plane;   // slots: -O .. -1, +1 .. +O
+            auto slot = [&](int o) -> float * { return base + (o < 0 ? o + O : o + O - 1) * pg.plane; };
+            auto plane_at = [&](int j) -> const float * {   // plane at index j along d (j in range)
+                const int o = j - idx[d];
+                return o == 0 ? center : slot(o);
+            };
+            for (int o = -O; o <= O; ++o) {
+                if (o == 0) continue;
+                const int j = idx[d] + o;
+                if (j < 0) ghost_plane(slot(o), plane_at(0), plane_at(1), float(-j), pg.plane, tid, nth);
+                if (j >= g.n[d])
+                    ghost_plane(slot(o), plane_at(g.n[d] - 1), plane_at(g.n[d] - 2), float(j - g.n[d] + 1),
+                                pg.plane, tid, nth);
+            }
+        }
+
+        // ---- halo-padded copy of the output plane -----------------------------
+        const int nr = g.nr, npad = g.n_pad, nl = g.n[ND - 1], cp = pg.cp;
+        float *c0 = ctr + O * cp + 4;          // row 0, column 0
+        for (int u = tid; u < nr * (npad / 4); u += nth) {
+            const int r = int(fast_div(uint32_t(u), g.div_segs));
+            const int c = (u - r * (npad / 4)) * 4;
+            *reinterpret_cast<float4 *>(c0 + r * cp + c) =
+                *reinterpret_cast<const float4 *>(center + r * npad + c);
+        }
+        __syncthreads();
+        // halo rows (axis ND-2) and halo columns (last axis)
+        for (int u = tid; u < 2 * O * nl; u += nth) {
+            const int h = u / nl, c = u - h * nl;                // h: 0..2O-1
+            const int jr = (h < O) ? h - O : nr + (h - O);       // row outside [0, nr)
+            float v;
+            if (g.periodic[ND - 2]) {
+                const int q = ((jr % nr) + nr) % nr;
+                v = c0[q * cp + c];
+            } else if (jr < 0) {
+                v = keep_sign_ghost(c0[c], c0[cp + c], float(-jr));
+            } else {
+                v = keep_sign_ghost(c0[(nr - 1) * cp + c], c0[(nr - 2) * cp + c], float(jr - nr + 1));
+            }
+            c0[jr * cp + c] = v;
+        }
+        for (int u = tid; u < 2 * O * nr; u += nth) {
+            const int r = u / (2 * O), h = u - r * (2 * O);
+            const int jc = (h < O) ? h - O : nl + (h - O);
+            float *row = c0 + r * cp;
+            float v;
+            if (g.periodic[ND - 1]) {
+                const int q = ((jc % nl) + nl) % nl;
+                v = row[q];
+            } else if (jc < 0) {
+                v = keep_sign_ghost(row[0], row[1], float(-jc));
+            } else {
+                v = keep_sign_ghost(row[nl - 1], row[nl - 2], float(jc - nl + 1));
+            }
+            row[jc] = v;
+        }
+        __syncthreads();
+
+        // ---- per-node update --------------------------------------------------
+        idx[sa] = s;
+        const long long gplane = (pencil + s) * (long long)pg.plane;
+        for (int u = tid; u < nr * (npad / 4); u += nth) {
+            const int r = int(fast_div(uint32_t(u), g.div_segs));
+            const int s0 = (u - r * (npad / 4)) * 4;
+            if (s0 >= nl) continue;
+            idx[ND - 2] = r;
+            idx[ND - 1] = s0;
+            float cA[ND][4], cS[ND];
+            drift<DYN, ND>(g, dy, idx, cA, cS);
+            const float *C = c0 + r * cp + s0;
+            const float4 c4 = *reinterpret_cast<const float4 *>(C);
+            const float f[4] = {c4.x, c4.y, c4.z, c4.w};
+            float L[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            const int off = r * npad + s0;
+
+            // stream axis from the ring, outer axes from the neighbour planes
+#pragma unroll
+            for (int d = 0; d <= NOUT; ++d) {
+                float4 m1, p1, m2, p2;
+                if (d == NOUT) {
+                    m1 = *reinterpret_cast<const float4 *>(ring_slot(s - 1) + off);
+                    p1 = *reinterpret_cast<const float4 *>(ring_slot(s + 1) + off);
+                    m2 = (O == 2) ? *reinterpret_cast<const float4 *>(ring_slot(s - 2) + off) : m1;
+                    p2 = (O == 2) ? *reinterpret_cast<const float4 *>(ring_slot(s + 2) + off) : p1;
+                } else {
+                    const float *base = nb + d * 2 * O * pg.plane + off;
+                    m1 = *reinterpret_cast<const float4 *>(base + (O - 1) * pg.plane);
+                    p1 = *reinterpret_cast<const float4 *>(base + O * pg.plane);
+                    m2 = (O == 2) ? *reinterpret_cast<const float4 *>(base) : m1;
+                    p2 = (O == 2) ? *reinterpret_cast<const float4 *>(base + (2 * O - 1) * pg.plane) : p1;
+                }
+                const int ax = (d == NOUT) ? sa : d;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float dm, dp;
+                    diffs<ORDER>(lane(m2, k), lane(m1, k), f[k], lane(p1, k), lane(p2, k), dm, dp);
+                    L[k] += axis_term(dm, dp, cA[ax][k], cS[ax], cD[ax]);
+                }
+            }
+            // in-plane row axis (ND-2)
+            {
+                const float4 m1 = *reinterpret_cast<const float4 *>(C - cp);
+                const float4 p1 = *reinterpret_cast<const float4 *>(C + cp);
+                const float4 m2 = (O == 2) ? *reinterpret_cast<const float4 *>(C - 2 * cp) : m1;
+                const float4 p2 = (O == 2) ? *reinterpret_cast<const float4 *>(C + 2 * cp) : p1;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float dm, dp;
+                    diffs<ORDER>(lane(m2, k), lane(m1, k), f[k], lane(p1, k), lane(p2, k), dm, dp);
+                    L[k] += axis_term(dm, dp, cA[ND - 2][k], cS[ND - 2], cD[ND - 2]);
+                }
+            }
+            // last axis: window w[j] = phi(s0 - 2 + j); halo columns are in place
+            {
+                const float2 lh = *reinterpret_cast<const float2 *>(C - 2);
+                const float2 rh = *reinterpret_cast<const float2 *>(C + 4);
+                float w[8] = {lh.x, lh.y, f[0], f[1], f[2], f[3], rh.x, rh.y};
+                // a partial last segment: the window continues with the halo columns
+                if (s0 + 4 > nl) {
+#pragma unroll
+                    for (int j = 2; j < 8; ++j)
+                        if (s0 + j - 2 >= nl) w[j] = C[j - 2];
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float dm, dp;
+                    diffs<ORDER>(w[k], w[k + 1], w[k + 2], w[k + 3], w[k + 4], dm, dp);
+                    L[k] += axis_term(dm, dp, cA[ND - 1][k], cS[ND - 1], cD[ND - 1]);
+                }
+            }
+            // update, Heun average, non-finite flag, BRT min
+            const long long gi = gplane + off;
+            float v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = f[k] + dt * L[k];
+            if (stage == 2) {
+                const float4 b4 = *reinterpret_cast<const float4 *>(prev + gi);
+                v[0] = 0.5f * (b4.x + v[0]);
+                v[1] = 0.5f * (b4.y + v[1]);
+                v[2] = 0.5f * (b4.z + v[2]);
+                v[3] = 0.5f * (b4.w + v[3]);
+            }
+            const int nvalid = nl - s0 < 4 ? nl - s0 : 4;
+            bool bad = false;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k < nvalid && !isfinite(v[k])) bad = true;
+            if (bad) atomicOr(&st->flags, FLAG_NONFINITE);
+            if (brt && stage != 1) {
+                const float4 l4 = ldg4(l + gi);
+                v[0] = fminf(v[0], l4.x);
+                v[1] = fminf(v[1], l4.y);
+                v[2] = fminf(v[2], l4.z);
+                v[3] = fminf(v[3], l4.w);
+            }
+            if (nvalid == 4) {
+                *reinterpret_cast<float4 *>(dst + gi) = make_float4(v[0], v[1], v[2], v[3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k < nvalid) dst[gi + k] = v[k];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace odp

@@ -11,6 +11,12 @@ cudaError_t launch_stage_dubins(int nd, const GridDesc &g, const DynDesc &dy, So
     return launch_stage_t<4, DYN_DUBINSCAR4D>(g, dy, st, l, order, stage, brt, s);
 }
 
+cudaError_t configure_stage_dubins(int nd)
+{
+    if (nd == 3) return configure_stage_t<3, DYN_DUBINS3D>();
+    return configure_stage_t<4, DYN_DUBINSCAR4D>();
+}
+
 cudaError_t launch_alpha_static_dubins(int nd, const GridDesc &g, const DynDesc &dy,
                                        SolveState *st, cudaStream_t s)
 {

@@ -10,6 +10,8 @@ cudaError_t launch_stage_rel6d(const GridDesc &g, const DynDesc &dy, SolveState 
     return launch_stage_t<6, DYN_REL6D>(g, dy, st, l, order, stage, brt, s);
 }
 
+cudaError_t configure_stage_rel6d() { return configure_stage_t<6, DYN_REL6D>(); }
+
 cudaError_t launch_alpha_static_rel6d(const GridDesc &g, const DynDesc &dy, SolveState *st,
                                       cudaStream_t s)
 {

@@ -24,6 +24,14 @@ cudaError_t launch_stage_si(int nd, const GridDesc &g, const DynDesc &dy, SolveS
     ODP_ND_SWITCH(nd, (launch_stage_t<ND, DYN_ADVECTION>(g, dy, st, l, order, stage, brt, s)))
 }
 
+cudaError_t configure_stage_si(int nd, int kind)
+{
+    if (kind == DYN_SINGLE_INT) {
+        ODP_ND_SWITCH(nd, (configure_stage_t<ND, DYN_SINGLE_INT>()))
+    }
+    ODP_ND_SWITCH(nd, (configure_stage_t<ND, DYN_ADVECTION>()))
+}
+
 cudaError_t launch_alpha_static_si(int nd, const GridDesc &g, const DynDesc &dy, SolveState *st,
                                    cudaStream_t s)
 {

@@ -182,6 +182,41 @@ static odp_status bind(const odp_grid *g)
         if (b_ != ODP_OK) return b_;     \
     } while (0)
 
+// Geometry of the plane-streaming pass (hj_plane.cuh): planes are the last
+// two axes; a CTA streams a chunk of axis ndim-3 for fixed outer indices.  The
+// chunk length is chosen so that a launch has about four CTAs per SM.  Grids
+// whose planes do not fit in shared memory use the row-blocked pass instead.
+static void plane_geometry(GridDesc &D, int sms)
+{
+    PlaneGeom &pg = D.pg;
+    pg = PlaneGeom{};
+    if (D.ndim < 3) return;
+    pg.plane = D.nr * D.n_pad;
+    pg.cp = D.n_pad + 8;
+    const int nout = D.ndim - 3;
+    for (int o = 1; o <= 2; ++o) {
+        const long long bytes = (long long)((2 * o + 1) + 2 * o * nout) * pg.plane * 4 +
+                                (long long)(D.nr + 2 * o) * pg.cp * 4 + 16;
+        pg.smem[o - 1] = bytes <= 200 * 1024 ? int(bytes) : 0;
+    }
+    if (pg.smem[0] == 0 && pg.smem[1] == 0) return;
+    pg.ns = D.n[D.ndim - 3];
+    long long pencils = 1;
+    for (int d = 0; d < D.ndim - 3; ++d) pencils *= D.n[d];
+    const long long target = 4LL * sms;
+    long long chunk = (pencils * pg.ns + target - 1) / target;
+    if (chunk < 1) chunk = 1;
+    if (chunk > pg.ns) chunk = pg.ns;
+    pg.chunk = int(chunk);
+    pg.nchunks = (pg.ns + pg.chunk - 1) / pg.chunk;
+    pg.items = int(pencils * pg.nchunks);
+    pg.div_nchunks = make_fastdiv(uint32_t(pg.nchunks));
+    const int work = D.nr * D.segs;
+    int th = (work + 31) / 32 * 32;
+    pg.threads = th < 64 ? 64 : (th > 256 ? 256 : th);
+    pg.use = 1;
+}
+
 static void release(odp_grid *g)
 {
     if (!g) return;
@@ -293,6 +328,7 @@ extern "C" odp_status odp_grid_create(int ndim, const int32_t *n, const double *
     D.planes = int(g->rows / D.nr);
     D.nthreads_rb = D.segs * D.row_groups * D.planes;
     D.div_row_groups = make_fastdiv(uint32_t(D.row_groups));
+    plane_geometry(D, 152);
     int64_t off = 0;
     std::vector<int64_t> coord_off(ndim);
     for (int d = 0; d < ndim; ++d) {
@@ -383,6 +419,16 @@ extern "C" odp_status odp_set_dynamics(odp_grid *g, odp_dyn kind, const double *
         g->desc.cos_tab = g->tables + off;
         g->desc.sin_tab = g->tables + off + padded4(g->n[angle]);
     }
+    cudaError_t ce = cudaSuccess;
+    ODP_BIND(g);
+    switch (dy.kind) {
+    case DYN_SINGLE_INT:
+    case DYN_ADVECTION: ce = configure_stage_si(g->ndim, dy.kind); break;
+    case DYN_DUBINS3D:
+    case DYN_DUBINSCAR4D: ce = configure_stage_dubins(g->ndim); break;
+    default: ce = configure_stage_rel6d(); break;
+    }
+    if (ce != cudaSuccess) return fail(ODP_ECUDA, "configuring the stage kernels: %s", cudaGetErrorString(ce));
     g->has_dyn = true;
     return ODP_OK;
 }
@@ -629,6 +675,7 @@ static odp_status read_state(odp_grid *g, SolveState *h)
 
 static odp_status status_of(const SolveState &h)
 {
+    if (h.flags & FLAG_COPY) return fail(ODP_ECUDA, "a bulk copy into shared memory did not complete");
     if (h.flags & FLAG_NONFINITE) return fail(ODP_ENUMERIC, "a non-finite value appeared in the solve");
     if (h.flags & FLAG_TIMEOUT)
         return fail(ODP_ETIMEOUT, "step limit %lld reached at t = %g", (long long)h.max_steps, h.t);

@@ -63,7 +63,7 @@ enum DynKind { DYN_SINGLE_INT = 0, DYN_DUBINS3D = 1, DYN_DUBINSCAR4D = 2, DYN_RE
 enum Mode { MODE_MIN = 0, MODE_MAX = 1 };
 
 // Error flags raised on the device.
-enum : int { FLAG_NONFINITE = 1, FLAG_TIMEOUT = 2 };
+enum : int { FLAG_NONFINITE = 1, FLAG_TIMEOUT = 2, FLAG_COPY = 4 };
 
 // Unsigned division by an invariant divisor through a multiply-high
 // (Granlund and Montgomery, "Division by invariant integers using
@@ -94,6 +94,20 @@ ODP_HD uint32_t fast_div(uint32_t n, const FastDiv &f)
 #endif
     return (hi + n) >> f.l;
 }
+
+// Geometry of the plane-streaming stage pass (hj_plane.cuh; host computed).
+struct PlaneGeom {
+    int use;           // 1: the grid runs the plane-streaming pass
+    int ns;            // length of the stream axis (axis ndim-3)
+    int chunk;         // output planes per CTA
+    int nchunks;       // ceil(ns / chunk)
+    int items;         // outer pencils * nchunks (CTAs per launch)
+    int plane;         // floats per plane: nr * n_pad
+    int cp;            // pitch of the halo-padded output plane: n_pad + 8
+    int threads;       // CTA size
+    int smem[2];       // dynamic shared memory bytes for stencil radius 1, 2
+    FastDiv div_nchunks;
+};
 
 // Storage: C order with the last axis padded to n_pad, a multiple of 4 nodes,
 // so that every row starts on a 16-byte boundary and a thread can move four
@@ -126,6 +140,7 @@ struct GridDesc {
     int planes;
     int nthreads_rb;             // segs * row_groups * planes
     FastDiv div_row_groups;
+    PlaneGeom pg;
 };
 
 struct DynDesc {

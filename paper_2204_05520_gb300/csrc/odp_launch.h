@@ -15,6 +15,12 @@ cudaError_t launch_stage_dubins(int nd, const GridDesc &g, const DynDesc &dy, So
 cudaError_t launch_stage_rel6d(const GridDesc &g, const DynDesc &dy, SolveState *st,
                                const float *l, int order, int stage, int brt, cudaStream_t s);
 
+// Shared-memory limits of the plane-streaming kernels of a model (call before
+// launching or capturing them on the current device).
+cudaError_t configure_stage_si(int nd, int kind);
+cudaError_t configure_stage_dubins(int nd);
+cudaError_t configure_stage_rel6d();
+
 // Grid-wide max of the phi-independent alpha components (K1, once per solve).
 cudaError_t launch_alpha_static_si(int nd, const GridDesc &g, const DynDesc &dy, SolveState *st,
                                    cudaStream_t s);
