@@ -117,6 +117,14 @@ const char *odp_version(void);
 odp_status odp_grid_create(int ndim, const int32_t *n, const double *lo, const double *hi,
                            const uint8_t *periodic, void *cuda_stream, odp_grid **out);
 
+/* Launch geometry the library would use for a grid of this shape (host only,
+ * no CUDA call; no paper counterpart).  out[0..11] = padded last axis, rows
+ * per thread of the row-blocked pass, its row groups, its planes, its threads,
+ * plane-streaming pass used (0/1), stream-axis length, chunk, CTAs, threads
+ * per CTA, shared bytes for stencil radius 1 and 2.  n_out >= 12.
+ * Errors: ODP_EINVAL. */
+odp_status odp_plan_geometry(int ndim, const int32_t *n, int64_t *out, int n_out);
+
 /* Free a grid and all device memory it owns (synchronises its stream).
  * NULL is accepted. */
 odp_status odp_grid_destroy(odp_grid *g);

@@ -27,6 +27,7 @@
 #include "../../include/odp.h"
 #include "odp_common.cuh"
 #include "odp_launch.h"
+#include "odp_time.cuh"
 
 using namespace odp;
 
@@ -62,13 +63,9 @@ static odp_status fail(odp_status code, const char *fmt, ...)
 // CFL step of Algorithm 1 from the stage-1 alpha, clipped to the segment end.
 __global__ void k_dt(SolveState *st, GridDesc g)
 {
-    double s = 0.0;
-    for (int d = 0; d < g.ndim; ++d)
-        s = __dadd_rn(s, __ddiv_rn(double(__uint_as_float(st->alpha_bits[0][d])), g.dz[d]));
-    const double rem = __dsub_rn(st->t_end, st->t);
-    const double dt_cfl = (s > 0.0) ? __ddiv_rn(st->cfl, s) : INFINITY;
-    const int last = !(dt_cfl < rem);
-    st->dt = last ? rem : dt_cfl;
+    const double dt_cfl = cfl_dt(st->alpha_bits[0], g.dz, g.ndim, st->cfl);
+    int last = 0;
+    st->dt = clipped_step(dt_cfl, st->t, st->t_end, &last);
     st->last = last;
 }
 
@@ -79,7 +76,7 @@ __global__ void k_advance(SolveState *st, int swap, unsigned dyn_mask, cudaGraph
                           cudaGraphConditionalHandle h_snap, int keep)
 {
     for (int d = 0; d < 8; ++d) st->alpha_last[d] = st->alpha_bits[swap ? 0 : 1][d];
-    st->t = st->last ? st->t_end : __dadd_rn(st->t, st->dt);
+    st->t = after_step(st->t, st->dt, st->t_end, st->last);
     st->steps += 1;
     if (swap) {
         float *tmp = st->cur;
@@ -92,7 +89,7 @@ __global__ void k_advance(SolveState *st, int swap, unsigned dyn_mask, cudaGraph
             st->alpha_bits[1][d] = 0u;
         }
     int go = 1, snap = 0;
-    if (!(__dsub_rn(st->t_end, st->t) > __dmul_rn(1e-12, st->t_end))) {
+    if (segment_done(st->t, st->t_end)) {
         snap = keep;
         st->snap_index = st->seg + 1;
         st->seg += 1;
@@ -203,6 +200,10 @@ static void plane_geometry(GridDesc &D, int sms)
     pg.ns = D.n[D.ndim - 3];
     long long pencils = 1;
     for (int d = 0; d < D.ndim - 3; ++d) pencils *= D.n[d];
+    if (pg.ns < 1 || pencils < 1 || pg.plane < 4) {
+        pg = PlaneGeom{};
+        return;
+    }
     const long long target = 4LL * sms;
     long long chunk = (pencils * pg.ns + target - 1) / target;
     if (chunk < 1) chunk = 1;
@@ -242,6 +243,33 @@ extern "C" const char *odp_last_error(void) { return g_last_error.c_str(); }
 extern "C" const char *odp_version(void) { return "libodp 0.1 (sm_103a)"; }
 
 extern "C" int64_t odp_grid_points(const odp_grid *g) { return g ? g->total : 0; }
+
+extern "C" odp_status odp_plan_geometry(int ndim, const int32_t *n, int64_t *out, int n_out)
+{
+    if (ndim < 1 || ndim > ODP_MAXD || !n || !out || n_out < 12) return fail(ODP_EINVAL, "bad arguments");
+    GridDesc D{};
+    D.ndim = ndim;
+    int64_t total = 1;
+    for (int d = 0; d < ndim; ++d) {
+        if (n[d] < 1) return fail(ODP_EINVAL, "axis %d has no nodes", d);
+        total *= n[d];
+        D.n[d] = n[d];
+    }
+    const int nl = n[ndim - 1];
+    D.n_pad = (nl + 3) / 4 * 4;
+    D.segs = D.n_pad / 4;
+    D.nr = ndim >= 2 ? n[ndim - 2] : 1;
+    D.R = D.nr >= 4 ? 4 : 1;
+    D.row_groups = (D.nr + D.R - 1) / D.R;
+    D.planes = int(total / nl / D.nr);
+    D.nthreads_rb = D.segs * D.row_groups * D.planes;
+    plane_geometry(D, 152);
+    const PlaneGeom &pg = D.pg;
+    const int64_t v[12] = {D.n_pad, D.R, D.row_groups, D.planes, D.nthreads_rb, pg.use, pg.ns,
+                           pg.chunk, pg.items, pg.threads, pg.smem[0], pg.smem[1]};
+    for (int k = 0; k < 12; ++k) out[k] = v[k];
+    return ODP_OK;
+}
 
 extern "C" odp_status odp_grid_create(int ndim, const int32_t *n, const double *lo, const double *hi,
                                       const uint8_t *periodic, void *cuda_stream, odp_grid **out)
@@ -328,7 +356,6 @@ extern "C" odp_status odp_grid_create(int ndim, const int32_t *n, const double *
     D.planes = int(g->rows / D.nr);
     D.nthreads_rb = D.segs * D.row_groups * D.planes;
     D.div_row_groups = make_fastdiv(uint32_t(D.row_groups));
-    plane_geometry(D, 152);
     int64_t off = 0;
     std::vector<int64_t> coord_off(ndim);
     for (int d = 0; d < ndim; ++d) {
@@ -353,6 +380,7 @@ extern "C" odp_status odp_grid_create(int ndim, const int32_t *n, const double *
         D.stride[d] = int(s);
         s *= (d == ndim - 1) ? g->n_pad : n[d];
     }
+    plane_geometry(D, 152);   // needs the axis sizes above
     ODP_TRY(cudaMalloc(&g->tables, size_t(tab_len) * sizeof(float)));
     ODP_TRY(cudaMemcpy(g->tables, tab.data(), size_t(tab_len) * sizeof(float), cudaMemcpyHostToDevice));
     for (int d = 0; d < ndim; ++d) D.coord[d] = g->tables + coord_off[d];
@@ -559,8 +587,13 @@ static odp_status build_graph(odp_grid *g)
     }
     cudaGraph_t captured = body;
     cudaError_t e2 = cudaStreamEndCapture(s, &captured);
-    if (e != cudaSuccess) return fail(ODP_ECUDA, "capturing the time loop: %s", cudaGetErrorString(e));
-    if (e2 != cudaSuccess) return fail(ODP_ECUDA, "ending the capture: %s", cudaGetErrorString(e2));
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        // the graph of a failed capture is dropped, not destroyed
+        cudaGetLastError();
+        g->graph = nullptr;
+        if (e != cudaSuccess) return fail(ODP_ECUDA, "capturing the time loop: %s", cudaGetErrorString(e));
+        return fail(ODP_ECUDA, "ending the capture: %s", cudaGetErrorString(e2));
+    }
 
     if (g->keep) {
         cudaGraphNodeParams ip{};
@@ -577,11 +610,20 @@ static odp_status build_graph(odp_grid *g)
         e = cudaGetLastError();
         cudaGraph_t cap2 = snap_body;
         e2 = cudaStreamEndCapture(s, &cap2);
-        if (e != cudaSuccess || e2 != cudaSuccess)
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            cudaGetLastError();
+            g->graph = nullptr;
             return fail(ODP_ECUDA, "capturing the snapshot copy: %s / %s", cudaGetErrorString(e),
                         cudaGetErrorString(e2));
+        }
     }
-    ODP_CUDA(cudaGraphInstantiate(&g->exec, g->graph, 0));
+    cudaError_t ei = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (ei != cudaSuccess) {
+        g->exec = nullptr;
+        cudaGraphDestroy(g->graph);
+        g->graph = nullptr;
+        return fail(ODP_ECUDA, "instantiating the time loop: %s", cudaGetErrorString(ei));
+    }
     g->launches_per_step = launches;
     return ODP_OK;
 }

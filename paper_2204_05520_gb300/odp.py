@@ -72,6 +72,7 @@ def load():
             "odp_solve_status": ([P, P], i32),
             "odp_value_readback": ([P, i32, P, i64, i32], i32),
             "odp_time_stage": ([P, i32, i32, P], i32),
+            "odp_plan_geometry": ([i32, P, P, i32], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -189,6 +190,19 @@ def time_stage(g, stage: int, reps: int = 20) -> float:
     ms = ctypes.c_double(0.0)
     _check(load().odp_time_stage(g, int(stage), int(reps), ctypes.byref(ms)), "odp_time_stage")
     return ms.value
+
+
+PLAN_FIELDS = ("n_pad", "rows_per_thread", "row_groups", "planes", "threads_rb", "plane_pass",
+               "stream_len", "chunk", "ctas", "cta_threads", "smem_r1", "smem_r2")
+
+
+def plan_geometry(n) -> dict:
+    """Launch geometry for a grid of shape n (host only)."""
+    nd = len(n)
+    n_a = (ctypes.c_int32 * nd)(*[int(v) for v in n])
+    out = (ctypes.c_int64 * 12)()
+    _check(load().odp_plan_geometry(nd, n_a, out, 12), "odp_plan_geometry")
+    return dict(zip(PLAN_FIELDS, list(out)))
 
 
 class Grid:

@@ -5,6 +5,7 @@ import glob
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2204_05520_gb300 import _build, odp
@@ -56,3 +57,22 @@ def test_argument_errors_need_no_gpu(lib):
     with pytest.raises(odp.OdpError) as e:
         odp.grid_create((4, 4), (1.0, 0.0), (0.0, 1.0), (False, False), stream=0)
     assert e.value.code == odp.EINVAL
+
+
+@pytest.mark.parametrize("n", [(41, 41, 36), (80, 80, 40, 64), (24,) * 6, (37,), (13, 11),
+                               (101, 101, 64), (31, 31, 37), (2, 2, 5), (3, 4, 3, 3, 2, 4)])
+def test_launch_geometry_covers_the_grid(lib, n):
+    g = odp.plan_geometry(n)
+    nl = n[-1]
+    assert g["n_pad"] % 4 == 0 and nl <= g["n_pad"] < nl + 4
+    nr = n[-2] if len(n) >= 2 else 1
+    assert g["row_groups"] * g["rows_per_thread"] >= nr
+    assert g["threads_rb"] == (g["n_pad"] // 4) * g["row_groups"] * g["planes"]
+    if len(n) >= 3 and g["plane_pass"]:
+        ns = n[-3]
+        pencils = int(np.prod(n[:-3])) if len(n) > 3 else 1
+        assert 1 <= g["chunk"] <= ns
+        assert g["ctas"] == pencils * -(-ns // g["chunk"])
+        assert 64 <= g["cta_threads"] <= 256 and g["cta_threads"] % 32 == 0
+        assert 0 < g["smem_r1"] <= g["smem_r2"] or g["smem_r2"] == 0
+        assert g["smem_r1"] <= 200 * 1024
