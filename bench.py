@@ -44,7 +44,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("dubinscar4d", "dubins3d", "rel6d"), default="dubinscar4d")
+    ap.add_argument("--workload", choices=("dubinscar4d", "dubins3d", "rel6d", "batch512"),
+                    default="dubinscar4d")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -339,10 +340,76 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """512 independent Dubins3D BRT solves (seed 0): one batched persistent
+    launch against the same solves issued one at a time."""
+    import torch
+
+    from paper_2204_05520_gb300 import _build, inputs, odp
+
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    dist = dist_setup(world, True)
+    _build.build()
+    odp.load()
+    problems = inputs.batch_problems(count=512, seed=0)
+    stream = torch.cuda.Stream()
+    grids = []
+    for p in problems:
+        g = odp.Grid.for_problem(p, stream=stream)
+        g.set_target(torch.from_numpy(p.target_values()).cuda())
+        grids.append(g)
+    horizons = [p.tau[-1] for p in problems]
+    for _ in range(args.warmup):
+        st = odp.batch_solve(grids, horizons)
+    torch.cuda.synchronize()
+    barrier(dist)
+    t0 = time.perf_counter()
+    dev_ms = 0.0
+    for _ in range(args.steps):
+        st = odp.batch_solve(grids, horizons)
+        dev_ms += st["device_ms"]
+    batched_s = max_over_ranks(dist, (time.perf_counter() - t0) / args.steps, torch.device("cuda", local))
+    # one at a time through the single-solve graph
+    for g, p in zip(grids, problems):
+        g.solve_problem(p)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps // 5)):
+        for g, p in zip(grids, problems):
+            g.solve_problem(p)
+        torch.cuda.synchronize()
+    single_s = (time.perf_counter() - t0) / max(1, args.steps // 5)
+    single_s = max_over_ranks(dist, single_s, torch.device("cuda", local))
+    if rank == 0:
+        n = len(problems)
+        line = {
+            "metric": "batched solves/s", "value": world * n / batched_s, "unit": "solves/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * batched_s, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch512_dubins3d", "solves": n, "nodes": sum(p.points for p in problems),
+                       "rounds": st["rounds"], "ctas_per_sm": st["ctas_per_sm"]},
+            "point_updates_per_s": st["point_updates"] / batched_s,
+            "device_ms_per_batch": dev_ms / args.steps,
+            "one_at_a_time": {"solves_per_s": n / single_s, "s_per_batch": single_s},
+            "speedup_vs_one_at_a_time": single_s / batched_s,
+            "roofline": {"bound": "hbm", "achieved": st["bytes"] / (dev_ms / args.steps / 1000.0) / 1e9,
+                         "peak": hbm_peak()[0], "unit": "GB/s",
+                         "frac": st["bytes"] / (dev_ms / args.steps / 1000.0) / 1e9 / hbm_peak()[0]},
+        }
+        print(json.dumps(line), flush=True)
+    for g in grids:
+        g.close()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch512":
+        return run_batch(args)
     return run_ours(args)
 
 

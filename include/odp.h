@@ -183,6 +183,37 @@ odp_status odp_solve_status(odp_grid *g, odp_solve_stats *stats);
 odp_status odp_value_readback(odp_grid *g, int tau_index, float *dst, int64_t n_elems,
                               int on_device);
 
+/* ------------------------------------------------------------------------
+ * Batched solves (no paper counterpart: many independent Algorithm 1 solves
+ * advanced together).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    double device_ms;      /* device time of the persistent launch            */
+    int64_t rounds;        /* lockstep rounds (the largest step count)        */
+    int32_t ctas_per_sm;   /* launch shape chosen by the autotuner            */
+    int32_t rows_per_thread;
+    double point_updates;  /* sum over grids of nodes x steps                  */
+    double bytes;          /* algorithmic HBM bytes                            */
+} odp_batch_stats;
+
+/* Solve n independent grids over [0, T[i]] in one persistent cooperative
+ * launch.  Every grid must have its dynamics and target set and live on the
+ * same device; work is issued on grids[0]'s stream and the call synchronises
+ * it.  Each grid takes exactly the step sequence of a single odp_solve_hjb
+ * over tau = {0, T[i]} (same float64 step schedule, same per-node kernel
+ * arithmetic) and its final value is read back with odp_value_readback(g, -1).
+ * Supported models: Dubins3D, DubinsCar4D, and the 2-3D single integrator
+ * (Rel6D needs a per-stage alpha pass and is refused).  The launch shape
+ * (CTAs per SM) is autotuned on the first rounds of a batch and cached per
+ * batch signature.  stats may be NULL.
+ * Errors: ODP_EINVAL, ODP_ESTATE, ODP_ENOMEM, ODP_ECUDA. */
+odp_status odp_batch_solve(odp_grid *const *grids, int n, const double *T, odp_set set, int space_order,
+                           int time_order, double cfl, odp_batch_stats *stats);
+
+/* Turn the batched solve's autotuner on (1, default) or off (0: the
+ * occupancy limit is used). */
+odp_status odp_batch_set_autotune(int enabled);
+
 /* Measurement helper (no paper counterpart): launch the fused stage kernel of
  * the grid's last solve `reps` times on its stream, outside the graph, and
  * return the mean device time of one launch in *ms_out (CUDA events; the call

@@ -1,0 +1,514 @@
+// batch.cu -- many independent solves advanced together in one persistent
+// cooperative launch (odp_batch_solve).
+//
+// Every grid keeps its own arrays, dynamics, alpha and dt.  A prepare kernel
+// (one CTA per grid) reduces each grid's static alpha and precomputes its
+// whole step schedule in float64 with the same functions the single-solve
+// graph uses (odp_time.cuh), so every grid takes exactly the steps it would
+// take alone.  The persistent kernel then runs lockstep rounds: in round r
+// every grid with more than r steps takes its step r (Euler: one pass; TVD-RK2:
+// stage 1 in phase A, stage 2 in phase B), its work split into items of 256
+// threads of the row-blocked stage pass.  Grids are sorted by step count, so
+// the active items of a round are a prefix of the item list.  CTAs take items
+// round robin and meet at a grid-wide barrier between phases; the barrier
+// spin is bounded and reports a failure instead of hanging.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "hj_kernels.cuh"
+#include "odp_internal.h"
+#include "odp_time.cuh"
+
+namespace odp {
+
+struct BatchGrid {
+    GridDesc g;
+    DynDesc dy;
+    float *a, *b;             // value buffers (the grid's phi_a, phi_b)
+    const float *l;           // target
+    SolveState *state;        // the grid's solve state (written at the end)
+    double T, dt_cfl, dt_last;
+    int n_steps;
+    int kind, time_order, brt, items;
+    unsigned alpha_bits[8];
+    float cD[ODP_MAXD];
+};
+
+struct BatchBarrier {
+    unsigned arrive;
+    unsigned gen;
+    int flags;                // 1: a barrier wait gave up
+};
+
+// ---------------------------------------------------------------------------
+// prepare: static alpha and the step schedule of each grid
+// ---------------------------------------------------------------------------
+template <int DYN, int ND>
+__device__ void batch_alpha(const GridDesc &g, const DynDesc &dy, float *a)
+{
+    for (int d = 0; d < ND; ++d) a[d] = 0.0f;
+    for (uint32_t i = threadIdx.x; i < uint32_t(g.total); i += blockDim.x) {
+        int idx[ND];
+        unflatten(g, ND, i, idx);
+        float la[ND];
+        static_alpha<DYN, ND>(g, dy, idx, la);
+        for (int d = 0; d < ND; ++d) a[d] = fmaxf(a[d], la[d]);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_batch_prepare(BatchGrid *bg, double cfl)
+{
+    __shared__ float red[8][ODP_MAXD];
+    BatchGrid &B = bg[blockIdx.x];
+    float a[ODP_MAXD];
+    for (int d = 0; d < ODP_MAXD; ++d) a[d] = 0.0f;
+    switch (B.kind) {
+    case DYN_DUBINS3D: batch_alpha<DYN_DUBINS3D, 3>(B.g, B.dy, a); break;
+    case DYN_DUBINSCAR4D: batch_alpha<DYN_DUBINSCAR4D, 4>(B.g, B.dy, a); break;
+    case DYN_SINGLE_INT:
+        if (B.g.ndim == 2) batch_alpha<DYN_SINGLE_INT, 2>(B.g, B.dy, a);
+        else batch_alpha<DYN_SINGLE_INT, 3>(B.g, B.dy, a);
+        break;
+    default: break;
+    }
+    const int nd = B.g.ndim;
+    for (int d = 0; d < nd; ++d) {
+        const float m = warp_max(a[d]);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][d] = m;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int d = 0; d < 8; ++d) B.alpha_bits[d] = 0u;
+        for (int d = 0; d < nd; ++d) {
+            float m = 0.0f;
+            for (int w = 0; w < (blockDim.x >> 5); ++w) m = fmaxf(m, red[w][d]);
+            B.alpha_bits[d] = __float_as_uint(m);
+            B.cD[d] = 0.5f * m * B.g.inv_dz[d];
+        }
+        // the step schedule of a solve over [0, T] (as k_dt / k_advance take it)
+        const double dt_cfl = cfl_dt(B.alpha_bits, B.g.dz, nd, cfl);
+        double t = 0.0, dt = 0.0;
+        int steps = 0, last = 0;
+        do {
+            dt = clipped_step(dt_cfl, t, B.T, &last);
+            t = after_step(t, dt, B.T, last);
+            ++steps;
+        } while (!segment_done(t, B.T) && steps < (1 << 30));
+        B.n_steps = steps;
+        B.dt_cfl = dt_cfl;
+        B.dt_last = dt;
+        B.state->flags = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the persistent kernel
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The
+// arrival counter only grows: generation k ends when it reaches
+// nblocks * (k + 1).  The wait gives up after a bounded number of polls.
+__device__ bool grid_barrier(BatchBarrier *bar, unsigned &gen)
+{
+    __syncthreads();
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        const unsigned target = gen + 1;
+        __threadfence();
+        const unsigned prev = atomicAdd(&bar->arrive, 1u);
+        if (prev == gridDim.x * target - 1) {
+            atomicExch(&bar->gen, target);
+        } else {
+            unsigned it = 0;
+            while (ld_acquire(&bar->gen) < target) {
+                if (++it > (1u << 22)) {
+                    ok = 0;
+                    atomicOr(&bar->flags, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    gen += 1;
+    return __syncthreads_and(ok) != 0;
+}
+
+template <int ORDER, int R>
+__device__ bool batch_item(const BatchGrid &B, int blk, int round, int phase)
+{
+    const uint32_t t = uint32_t(blk) * blockDim.x + threadIdx.x;
+    if (t >= uint32_t(B.g.nthreads_rb)) return false;
+    StageArgs A;
+    const bool first = (round == 0);
+    if (B.time_order == 1) {
+        A.stage = 0;
+        A.src = first ? B.l : ((round & 1) ? B.b : B.a);
+        A.dst = (round & 1) ? B.a : B.b;
+        A.prev = A.src;
+    } else if (phase == 0) {
+        A.stage = 1;
+        A.src = first ? B.l : B.a;
+        A.dst = B.b;
+        A.prev = A.src;
+    } else {
+        A.stage = 2;
+        A.src = B.b;
+        A.prev = first ? B.l : B.a;
+        A.dst = B.a;
+    }
+    A.l = B.l;
+    A.brt = B.brt;
+    A.dt = float(round == B.n_steps - 1 ? B.dt_last : B.dt_cfl);
+    for (int d = 0; d < ODP_MAXD; ++d) A.cD[d] = B.cD[d];
+    switch (B.kind) {
+    case DYN_DUBINS3D: return stage_tile<3, ORDER, DYN_DUBINS3D, R>(B.g, B.dy, A, t);
+    case DYN_DUBINSCAR4D: return stage_tile<4, ORDER, DYN_DUBINSCAR4D, R>(B.g, B.dy, A, t);
+    case DYN_SINGLE_INT:
+        if (B.g.ndim == 2) return stage_tile<2, ORDER, DYN_SINGLE_INT, R>(B.g, B.dy, A, t);
+        return stage_tile<3, ORDER, DYN_SINGLE_INT, R>(B.g, B.dy, A, t);
+    default: return false;
+    }
+}
+
+// Rounds [round0, round1) of the batch.  sorted: grid ids by step count
+// (descending); item_start: first item of each sorted grid (n + 1 entries);
+// active: active items of every round.
+template <int ORDER, int R>
+__global__ void __launch_bounds__(256) k_batch_run(const BatchGrid *__restrict__ bg, const int *__restrict__ sorted,
+                                                   const int *__restrict__ item_start, int n,
+                                                   const int *__restrict__ active, const int *__restrict__ active_rk2,
+                                                   int round0, int round1, BatchBarrier *bar)
+{
+    __shared__ BatchGrid sB;
+    unsigned gen = 0;
+    for (int r = round0; r < round1; ++r) {
+        for (int phase = 0; phase < 2; ++phase) {
+            const int items = phase == 0 ? active[r] : active_rk2[r];
+            if (phase == 1 && items == 0) break;
+            for (int i = blockIdx.x; i < items; i += gridDim.x) {
+                // sorted grid holding item i: last k with item_start[k] <= i
+                int lo = 0, hi = n - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (item_start[mid] <= i) lo = mid; else hi = mid - 1;
+                }
+                const int gid = sorted[lo];
+                {
+                    const int words = int(sizeof(BatchGrid) / 4);
+                    const unsigned *srcw = reinterpret_cast<const unsigned *>(bg + gid);
+                    unsigned *dstw = reinterpret_cast<unsigned *>(&sB);
+                    for (int w = threadIdx.x; w < words; w += blockDim.x) dstw[w] = srcw[w];
+                }
+                __syncthreads();
+                if (!(phase == 1 && sB.time_order != 2)) {
+                    if (batch_item<ORDER, R>(sB, i - item_start[lo], r, phase))
+                        atomicOr(&sB.state->flags, FLAG_NONFINITE);
+                }
+                __syncthreads();
+            }
+            if (!grid_barrier(bar, gen)) return;
+        }
+    }
+}
+
+__global__ void k_batch_finish(const BatchGrid *bg, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const BatchGrid &B = bg[i];
+    SolveState *st = B.state;
+    const bool in_b = (B.time_order == 1) && (B.n_steps & 1);
+    st->cur = in_b ? B.b : B.a;
+    st->nxt = in_b ? B.a : B.b;
+    st->t = B.T;
+    st->t_end = B.T;
+    st->dt = B.dt_last;
+    st->steps = B.n_steps;
+    st->seg = 1;
+    st->n_seg = 1;
+    for (int d = 0; d < 8; ++d) st->alpha_last[d] = B.alpha_bits[d];
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct BatchWorkspace {
+    std::mutex mu;
+    int device = -1;
+    BatchGrid *bg = nullptr;
+    int *ints = nullptr;
+    BatchBarrier *bar = nullptr;
+    size_t cap_grids = 0, cap_ints = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+static BatchWorkspace &workspace()
+{
+    static BatchWorkspace w;
+    return w;
+}
+
+template <int ORDER, int R>
+static cudaError_t launch_run(int ctas, const BatchGrid *bg, const int *sorted, const int *item_start, int n,
+                              const int *active, const int *active_rk2, int r0, int r1, BatchBarrier *bar,
+                              cudaStream_t s)
+{
+    void *args[] = {(void *)&bg, (void *)&sorted, (void *)&item_start, (void *)&n, (void *)&active,
+                    (void *)&active_rk2, (void *)&r0, (void *)&r1, (void *)&bar};
+    return cudaLaunchCooperativeKernel((const void *)k_batch_run<ORDER, R>, dim3(ctas), dim3(256), args, 0, s);
+}
+
+template <int ORDER, int R>
+static int max_ctas_per_sm()
+{
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_run<ORDER, R>, 256, 0);
+    return nb;
+}
+
+// Autotuned launch shape, cached per batch signature (scheme, rows per
+// thread, total items): CTAs per SM from 1 to the occupancy limit, timed on
+// the first rounds of the real batch.
+struct TuneKey {
+    int order, R, sms;
+    long long items0;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(order, R, sms, items0) < std::tie(o.order, o.R, o.sms, o.items0);
+    }
+};
+
+}  // namespace odp
+
+#include <map>
+#include <tuple>
+
+using namespace odp;
+
+#define ODP_TRY_CUDA(call)                                                                          \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return fail(e_ == cudaErrorMemoryAllocation ? ODP_ENOMEM : ODP_ECUDA, "%s: %s", #call, \
+                        cudaGetErrorString(e_));                                                    \
+    } while (0)
+
+static std::map<TuneKey, int> g_tuned;
+static std::mutex g_tuned_mu;
+static int g_tune_enabled = 1;
+
+extern "C" odp_status odp_batch_set_autotune(int enabled)
+{
+    g_tune_enabled = enabled ? 1 : 0;
+    return ODP_OK;
+}
+
+extern "C" odp_status odp_batch_solve(odp_grid *const *grids, int n, const double *T, odp_set set,
+                                      int space_order, int time_order, double cfl, odp_batch_stats *stats)
+{
+    if (!grids || !T || n < 1) return fail(ODP_EINVAL, "need n >= 1 grids and horizons");
+    if (set != ODP_BRS && set != ODP_BRT) return fail(ODP_EINVAL, "set must be ODP_BRS or ODP_BRT");
+    if (space_order != 1 && space_order != 2) return fail(ODP_EINVAL, "space_order must be 1 or 2");
+    if (time_order != 1 && time_order != 2) return fail(ODP_EINVAL, "time_order must be 1 or 2");
+    if (!(cfl > 0.0 && cfl <= 1.0)) return fail(ODP_EINVAL, "cfl must lie in (0, 1]");
+    const int device = grids[0] ? grids[0]->device : 0;
+    int all_r4 = 1;
+    for (int i = 0; i < n; ++i) {
+        const odp_grid *g = grids[i];
+        if (!g) return fail(ODP_EINVAL, "grid %d is NULL", i);
+        if (!g->has_dyn || !g->has_target) return fail(ODP_ESTATE, "grid %d lacks dynamics or target", i);
+        if (g->device != device) return fail(ODP_EINVAL, "grid %d is on another device", i);
+        if (!(T[i] > 0.0) || !std::isfinite(T[i])) return fail(ODP_EINVAL, "horizon %d must be finite and > 0", i);
+        const int k = g->dyn.kind;
+        const bool ok = k == DYN_DUBINS3D || k == DYN_DUBINSCAR4D ||
+                        (k == DYN_SINGLE_INT && (g->ndim == 2 || g->ndim == 3));
+        if (!ok) return fail(ODP_EINVAL, "grid %d: the batched solve supports Dubins3D, DubinsCar4D and 2-3D "
+                                         "single integrators", i);
+        if (g->desc.R != 4) all_r4 = 0;
+    }
+    const int R = all_r4 ? 4 : 1;
+    cudaStream_t s = grids[0]->stream;
+    BatchWorkspace &W = workspace();
+    std::lock_guard<std::mutex> lock(W.mu);
+    ODP_TRY_CUDA(cudaSetDevice(device));
+
+    // per-grid records
+    std::vector<BatchGrid> hb(static_cast<size_t>(n));
+    for (int i = 0; i < n; ++i) {
+        odp_grid *g = grids[i];
+        BatchGrid &B = hb[size_t(i)];
+        memset(&B, 0, sizeof(B));
+        B.g = g->desc;
+        if (R == 1) {   // row-blocked geometry with one row per thread
+            B.g.R = 1;
+            B.g.row_groups = B.g.nr;
+            B.g.nthreads_rb = B.g.segs * B.g.row_groups * B.g.planes;
+            B.g.div_row_groups = make_fastdiv(uint32_t(B.g.row_groups));
+        }
+        B.dy = g->dyn;
+        B.a = g->phi_a;
+        B.b = g->phi_b;
+        B.l = g->l;
+        B.state = g->state;
+        B.T = T[i];
+        B.kind = g->dyn.kind;
+        B.time_order = time_order;
+        B.brt = set == ODP_BRT ? 1 : 0;
+        B.items = (B.g.nthreads_rb + 255) / 256;
+    }
+    if (size_t(n) > W.cap_grids || W.device != device) {
+        cudaFree(W.bg);
+        W.bg = nullptr;
+        W.cap_grids = 0;
+        ODP_TRY_CUDA(cudaMalloc(&W.bg, sizeof(BatchGrid) * size_t(n)));
+        W.cap_grids = size_t(n);
+    }
+    if (!W.bar || W.device != device) {
+        cudaFree(W.bar);
+        W.bar = nullptr;
+        ODP_TRY_CUDA(cudaMalloc(&W.bar, sizeof(BatchBarrier)));
+        if (!W.ev0) cudaEventCreate(&W.ev0);
+        if (!W.ev1) cudaEventCreate(&W.ev1);
+    }
+    W.device = device;
+    ODP_TRY_CUDA(cudaMemcpyAsync(W.bg, hb.data(), sizeof(BatchGrid) * size_t(n), cudaMemcpyHostToDevice, s));
+    k_batch_prepare<<<n, 256, 0, s>>>(W.bg, cfl);
+    ODP_TRY_CUDA(cudaGetLastError());
+    ODP_TRY_CUDA(cudaMemcpyAsync(hb.data(), W.bg, sizeof(BatchGrid) * size_t(n), cudaMemcpyDeviceToHost, s));
+    ODP_TRY_CUDA(cudaStreamSynchronize(s));
+
+    // items sorted by step count, active prefixes per round
+    std::vector<int> sorted(static_cast<size_t>(n));
+    std::iota(sorted.begin(), sorted.end(), 0);
+    std::stable_sort(sorted.begin(), sorted.end(),
+                     [&](int x, int y) { return hb[size_t(x)].n_steps > hb[size_t(y)].n_steps; });
+    const int rounds = hb[size_t(sorted[0])].n_steps;
+    std::vector<int> item_start(static_cast<size_t>(n) + 1, 0), active(static_cast<size_t>(rounds), 0),
+        active_rk2(static_cast<size_t>(rounds), 0);
+    for (int k = 0; k < n; ++k) item_start[size_t(k) + 1] = item_start[size_t(k)] + hb[size_t(sorted[size_t(k)])].items;
+    {
+        int k = n;
+        for (int r = 0; r < rounds; ++r) {
+            while (k > 0 && hb[size_t(sorted[size_t(k) - 1])].n_steps <= r) --k;
+            active[size_t(r)] = item_start[size_t(k)];
+            active_rk2[size_t(r)] = time_order == 2 ? active[size_t(r)] : 0;
+        }
+    }
+    const size_t nints = size_t(n) + size_t(n) + 1 + 2 * size_t(rounds);
+    if (nints > W.cap_ints) {
+        cudaFree(W.ints);
+        W.ints = nullptr;
+        W.cap_ints = 0;
+        ODP_TRY_CUDA(cudaMalloc(&W.ints, sizeof(int) * nints));
+        W.cap_ints = nints;
+    }
+    std::vector<int> packed;
+    packed.reserve(nints);
+    packed.insert(packed.end(), sorted.begin(), sorted.end());
+    packed.insert(packed.end(), item_start.begin(), item_start.end());
+    packed.insert(packed.end(), active.begin(), active.end());
+    packed.insert(packed.end(), active_rk2.begin(), active_rk2.end());
+    ODP_TRY_CUDA(cudaMemcpyAsync(W.ints, packed.data(), sizeof(int) * nints, cudaMemcpyHostToDevice, s));
+    const int *d_sorted = W.ints, *d_start = W.ints + n, *d_active = W.ints + 2 * n + 1;
+    const int *d_active_rk2 = d_active + rounds;
+
+    int sms = 0;
+    ODP_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    const int max_per_sm = space_order == 1 ? (R == 4 ? max_ctas_per_sm<1, 4>() : max_ctas_per_sm<1, 1>())
+                                            : (R == 4 ? max_ctas_per_sm<2, 4>() : max_ctas_per_sm<2, 1>());
+    if (max_per_sm < 1) return fail(ODP_ECUDA, "the batched kernel cannot be resident");
+    auto run = [&](int per_sm, int r0, int r1) -> cudaError_t {
+        cudaError_t e = cudaMemsetAsync(W.bar, 0, sizeof(BatchBarrier), s);
+        if (e != cudaSuccess) return e;
+        const int ctas = per_sm * sms;
+        if (space_order == 1)
+            return R == 4 ? launch_run<1, 4>(ctas, W.bg, d_sorted, d_start, n, d_active, d_active_rk2, r0, r1, W.bar, s)
+                          : launch_run<1, 1>(ctas, W.bg, d_sorted, d_start, n, d_active, d_active_rk2, r0, r1, W.bar, s);
+        return R == 4 ? launch_run<2, 4>(ctas, W.bg, d_sorted, d_start, n, d_active, d_active_rk2, r0, r1, W.bar, s)
+                      : launch_run<2, 1>(ctas, W.bg, d_sorted, d_start, n, d_active, d_active_rk2, r0, r1, W.bar, s);
+    };
+
+    // autotune the CTAs per SM on the first rounds of this batch
+    TuneKey key{space_order, R, sms, item_start[size_t(n)]};
+    int per_sm = max_per_sm;
+    bool tuned = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tuned_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            per_sm = std::min(it->second, max_per_sm);
+            tuned = true;
+        }
+    }
+    if (!tuned && g_tune_enabled && rounds >= 2) {
+        const int probe = std::min(rounds, 3);
+        float best = 1e30f;
+        for (int c = 1; c <= max_per_sm; ++c) {
+            ODP_TRY_CUDA(cudaEventRecord(W.ev0, s));
+            ODP_TRY_CUDA(run(c, 0, probe));
+            ODP_TRY_CUDA(cudaEventRecord(W.ev1, s));
+            ODP_TRY_CUDA(cudaEventSynchronize(W.ev1));
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, W.ev0, W.ev1);
+            if (ms < best) {
+                best = ms;
+                per_sm = c;
+            }
+        }
+        std::lock_guard<std::mutex> lk(g_tuned_mu);
+        g_tuned[key] = per_sm;
+    }
+
+    ODP_TRY_CUDA(cudaEventRecord(W.ev0, s));
+    ODP_TRY_CUDA(run(per_sm, 0, rounds));
+    ODP_TRY_CUDA(cudaEventRecord(W.ev1, s));
+    k_batch_finish<<<(n + 127) / 128, 128, 0, s>>>(W.bg, n);
+    ODP_TRY_CUDA(cudaGetLastError());
+    BatchBarrier hbar{};
+    ODP_TRY_CUDA(cudaMemcpyAsync(&hbar, W.bar, sizeof(hbar), cudaMemcpyDeviceToHost, s));
+    ODP_TRY_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < n; ++i) {
+        odp_grid *g = grids[i];
+        g->solved = true;
+        g->n_tau = 2;
+        g->keep = 0;
+        g->time_order = time_order;
+        g->order = space_order;
+        g->brt = set == ODP_BRT ? 1 : 0;
+        g->timed = false;
+    }
+    if (hbar.flags) return fail(ODP_ECUDA, "a grid-wide barrier of the batched solve gave up waiting");
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, W.ev0, W.ev1);
+        stats->device_ms = ms;
+        stats->rounds = rounds;
+        stats->ctas_per_sm = per_sm;
+        stats->rows_per_thread = R;
+        double updates = 0.0, bytes = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const double nodes = double(grids[i]->total) * double(hb[size_t(i)].n_steps);
+            updates += nodes;
+            const double per = (time_order == 1 ? 8.0 : 20.0) + (set == ODP_BRT ? 4.0 : 0.0);
+            bytes += per * nodes;
+        }
+        stats->point_updates = updates;
+        stats->bytes = bytes;
+    }
+    return ODP_OK;
+}

@@ -1,0 +1,63 @@
+// odp_internal.h -- the grid object shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/odp.h"
+#include "odp_common.cuh"
+
+namespace odp {
+// Record a message for odp_last_error() and return code.
+odp_status fail(odp_status code, const char *fmt, ...);
+}  // namespace odp
+
+// Kernel arguments (grid and dynamics descriptors) are frozen into the graph
+// when it is captured, so any change of scheme or dynamics rebuilds it.
+struct GraphKey {
+    int order = 0, time_order = 0, brt = 0, keep = 0;
+    long long dyn_version = -1;
+    bool operator==(const GraphKey &o) const
+    {
+        return order == o.order && time_order == o.time_order && brt == o.brt && keep == o.keep &&
+               dyn_version == o.dyn_version;
+    }
+};
+
+struct odp_grid {
+    int ndim = 0;
+    int n[ODP_MAXD] = {0};
+    double lo[ODP_MAXD] = {0}, hi[ODP_MAXD] = {0};
+    int periodic[ODP_MAXD] = {0};
+    int64_t total = 0;                // nodes
+    int64_t total_pad = 0;            // stored floats (last axis padded to n_pad)
+    int n_last = 0, n_pad = 0;
+    int64_t rows = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+
+    float *phi_a = nullptr, *phi_b = nullptr, *l = nullptr;
+    float *tables = nullptr;          // all node-coordinate and trig tables
+    odp::SolveState *state = nullptr;
+    double *tau = nullptr;
+    int tau_cap = 0;
+    float *snapshots = nullptr;
+    int snap_cap = 0;
+
+    odp::GridDesc desc{};
+    odp::DynDesc dyn{};
+    bool has_dyn = false, has_target = false, solved = false;
+    long long dyn_version = 0;
+    int64_t max_steps = 10000000;
+    int n_tau = 0, keep = 0, time_order = 1, order = 1, brt = 0;
+    bool timed = false;
+
+    cudaStream_t capture_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    GraphKey key;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int64_t launches_per_step = 0;
+};
+

@@ -44,6 +44,15 @@ class SolveStats(ctypes.Structure):
                 "launches": self.launches}
 
 
+class BatchStats(ctypes.Structure):
+    _fields_ = [("device_ms", ctypes.c_double), ("rounds", ctypes.c_int64),
+                ("ctas_per_sm", ctypes.c_int32), ("rows_per_thread", ctypes.c_int32),
+                ("point_updates", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -73,6 +82,8 @@ def load():
             "odp_value_readback": ([P, i32, P, i64, i32], i32),
             "odp_time_stage": ([P, i32, i32, P], i32),
             "odp_plan_geometry": ([i32, P, P, i32], i32),
+            "odp_batch_solve": ([P, i32, P, i32, i32, i32, f64, P], i32),
+            "odp_batch_set_autotune": ([i32], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -190,6 +201,21 @@ def time_stage(g, stage: int, reps: int = 20) -> float:
     ms = ctypes.c_double(0.0)
     _check(load().odp_time_stage(g, int(stage), int(reps), ctypes.byref(ms)), "odp_time_stage")
     return ms.value
+
+
+def batch_solve(grids, horizons, set_kind="brt", space_order=1, time_order=1, cfl=0.8) -> dict:
+    """Solve many grids (``Grid`` objects or handles) in one persistent launch."""
+    hs = [g.handle if isinstance(g, Grid) else g for g in grids]
+    arr = (ctypes.c_void_p * len(hs))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in hs])
+    T = (ctypes.c_double * len(hs))(*[float(t) for t in horizons])
+    st = BatchStats()
+    _check(load().odp_batch_solve(arr, len(hs), T, SET[set_kind], int(space_order), int(time_order),
+                                  float(cfl), ctypes.byref(st)), "odp_batch_solve")
+    return st.as_dict()
+
+
+def batch_set_autotune(enabled: bool):
+    _check(load().odp_batch_set_autotune(1 if enabled else 0), "odp_batch_set_autotune")
 
 
 PLAN_FIELDS = ("n_pad", "rows_per_thread", "row_groups", "planes", "threads_rb", "plane_pass",
