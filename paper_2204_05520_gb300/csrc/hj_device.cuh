@@ -42,6 +42,129 @@ ODP_HD void diffs(float fm2, float fm1, float f0, float fp1, float fp2, float &d
     }
 }
 
+// ---------------------------------------------------------------------------
+// Paired float32 arithmetic: two lanes per instruction on sm_100+ (FADD2,
+// FFMA2, FMUL2).  Each lane is an ordinary IEEE float32 operation, so the
+// results are those of the scalar operations.
+// ---------------------------------------------------------------------------
+ODP_HD float2 f2add(float2 a, float2 b)
+{
+#ifdef __CUDA_ARCH__
+    return __fadd2_rn(a, b);
+#else
+    return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+
+ODP_HD float2 f2fma(float2 a, float2 b, float2 c)
+{
+#ifdef __CUDA_ARCH__
+    return __ffma2_rn(a, b, c);
+#else
+    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+#endif
+}
+
+ODP_HD float2 f2mul(float2 a, float2 b)
+{
+#ifdef __CUDA_ARCH__
+    return __fmul2_rn(a, b);
+#else
+    return make_float2(a.x * b.x, a.y * b.y);
+#endif
+}
+
+// a - b, rounded once (b * -1 is exact)
+ODP_HD float2 f2sub(float2 a, float2 b) { return f2fma(b, make_float2(-1.0f, -1.0f), a); }
+
+ODP_HD float2 f2abs(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+
+ODP_HD float2 f2splat(float a) { return make_float2(a, a); }
+
+// the smaller-magnitude choice of ENO2, lane by lane: (|x| < |c|) ? x : c
+ODP_HD float2 f2pick(float2 x, float2 c)
+{
+    return make_float2(fabsf(x.x) < fabsf(c.x) ? x.x : c.x, fabsf(x.y) < fabsf(c.y) ? x.y : c.y);
+}
+
+// One axis of the Lax-Friedrichs right-hand side for two nodes from their
+// five-node (ENO2) or three-node (upwind) stencils along that axis:
+// L += cA P + cS |P| + cD M with P = dp + dm, M = dp - dm (unscaled one-sided
+// differences, see diffs()); has_a / has_s (compile-time constants at every
+// call) drop the terms a model does not have on this axis.  Same operation
+// order as diffs() for the ENO2 choice.
+template <int ORDER>
+ODP_HD void axis_pair(float2 fm2, float2 fm1, float2 f0, float2 fp1, float2 fp2, float2 cA, float cS, float cD,
+                      float2 &L, bool has_a, bool has_s)
+{
+    const float2 a = f2sub(f0, fm1), b = f2sub(fp1, f0);
+    float2 dm = a, dp = b;
+    if (ORDER == 2) {
+        const float2 d2l = f2sub(a, f2sub(fm1, fm2));
+        const float2 d2m = f2sub(b, a);
+        const float2 d2r = f2sub(f2sub(fp2, fp1), b);
+        const float2 cm = f2pick(d2l, d2m), cp = f2pick(d2r, d2m);
+        dm = f2fma(cm, f2splat(0.5f), a);
+        dp = f2fma(cp, f2splat(-0.5f), b);
+    }
+    const float2 P = f2add(dp, dm), M = f2sub(dp, dm);
+    if (has_a) L = f2fma(cA, P, L);
+    if (has_s) L = f2fma(f2splat(cS), f2abs(P), L);
+    L = f2fma(f2splat(cD), M, L);
+}
+
+// The last axis of four consecutive nodes from their eight-node window
+// w[j] = phi(first - 2 + j), sharing the first and second differences of the
+// window between the four nodes (the same float32 operations as diffs()).
+template <int ORDER>
+ODP_HD void axis_last(const float *w, const float *cA, float cS, float cD, float *L, bool has_a, bool has_s)
+{
+    float e[7];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) e[j] = w[j + 1] - w[j];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float a = e[k + 1], b = e[k + 2];
+        float dm = a, dp = b;
+        if (ORDER == 2) {
+            const float d2l = a - e[k];
+            const float d2m = b - a;
+            const float d2r = e[k + 3] - b;
+            const float cm = (fabsf(d2l) < fabsf(d2m)) ? d2l : d2m;
+            const float cp = (fabsf(d2r) < fabsf(d2m)) ? d2r : d2m;
+            dm = fmaf(cm, 0.5f, a);
+            dp = fmaf(cp, -0.5f, b);
+        }
+        const float P = dp + dm, M = dp - dm;
+        float acc = L[k];
+        if (has_a) acc = fmaf(cA[k], P, acc);
+        if (has_s) acc = fmaf(cS, fabsf(P), acc);
+        L[k] = fmaf(cD, M, acc);
+    }
+}
+
+// Which axes carry a drift term (a_d(z) depends on the state) and which a
+// bounded input (S_d != 0), per model (Appendix dynamics).
+template <int DYN, int ND>
+constexpr bool has_drift(int d)
+{
+    return DYN == DYN_ADVECTION ? true
+         : DYN == DYN_SINGLE_INT ? false
+         : DYN == DYN_DUBINS3D ? d < 2
+         : DYN == DYN_DUBINSCAR4D ? d < 2
+         : d < 3;   // Rel6D
+}
+
+template <int DYN, int ND>
+constexpr bool has_bound(int d)
+{
+    return DYN == DYN_ADVECTION ? false
+         : DYN == DYN_SINGLE_INT ? true
+         : DYN == DYN_DUBINS3D ? d == 2
+         : DYN == DYN_DUBINSCAR4D ? d >= 2
+         : d >= 2;  // Rel6D
+}
+
 // Local dissipation bound a_d(z) (global-alpha reading of Section 2.1): the
 // largest |f_d| over the input extremes a node's derivative box can select.
 // For every model here except the Rel6D heading rate this does not depend on

@@ -162,6 +162,50 @@ struct StageArgs {
     int brt;
 };
 
+// One non-last axis of a four-node segment from its neighbour rows (as two
+// pairs of nodes).
+template <int ORDER>
+ODP_HD void segment_axis(const float4 &m2, const float4 &m1, const float4 &c, const float4 &p1, const float4 &p2,
+                         const float *cA, float cS, float cD, float2 &L01, float2 &L23, bool has_a, bool has_s)
+{
+    axis_pair<ORDER>(make_float2(m2.x, m2.y), make_float2(m1.x, m1.y), make_float2(c.x, c.y),
+                                   make_float2(p1.x, p1.y), make_float2(p2.x, p2.y), make_float2(cA[0], cA[1]),
+                                   cS, cD, L01, has_a, has_s);
+    axis_pair<ORDER>(make_float2(m2.z, m2.w), make_float2(m1.z, m1.w), make_float2(c.z, c.w),
+                                   make_float2(p1.z, p1.w), make_float2(p2.z, p2.w), make_float2(cA[2], cA[3]),
+                                   cS, cD, L23, has_a, has_s);
+}
+
+// Update of a four-node segment: phi + dt L (Euler / RK2 stage), the Heun
+// average with phi^n on RK2 stage 2, the non-finite check of the valid
+// nodes, and the min with l on the last stage of a tube.  Returns true if a
+// valid node is not finite.
+ODP_HD bool stage_epilogue(const StageArgs &A, int base, const float4 &c4, const float *L, int nvalid, float4 &out)
+{
+    const float2 dt = f2splat(A.dt);
+    float2 v01 = f2fma(dt, make_float2(L[0], L[1]), make_float2(c4.x, c4.y));
+    float2 v23 = f2fma(dt, make_float2(L[2], L[3]), make_float2(c4.z, c4.w));
+    if (A.stage == 2) {
+        const float4 b4 = *reinterpret_cast<const float4 *>(A.prev + base);
+        v01 = f2mul(f2splat(0.5f), f2add(make_float2(b4.x, b4.y), v01));
+        v23 = f2mul(f2splat(0.5f), f2add(make_float2(b4.z, b4.w), v23));
+    }
+    const float v[4] = {v01.x, v01.y, v23.x, v23.y};
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (k < nvalid && !isfinite(v[k])) bad = true;
+    out = make_float4(v[0], v[1], v[2], v[3]);
+    if (A.brt && A.stage != 1) {
+        const float4 l4 = ldg4(A.l + base);
+        out.x = fminf(out.x, l4.x);
+        out.y = fminf(out.y, l4.y);
+        out.z = fminf(out.z, l4.z);
+        out.w = fminf(out.w, l4.w);
+    }
+    return bad;
+}
+
 // Row j (possibly outside [0, n)) of axis `axis` relative to row i0 of the
 // segment at storage offset base (periodic wrap or sign-keeping ghost).
 ODP_HD float4 axis_row(const float *__restrict__ src, int base, int i0, int j, int stride, int n, int periodic)
@@ -245,7 +289,7 @@ ODP_HD bool stage_tile(const GridDesc &g, const DynDesc &dy, const StageArgs &A,
         drift<DYN, ND>(g, dy, idx, cA, cS);
         const float4 c4 = col[O + i];
         const float f[4] = {c4.x, c4.y, c4.z, c4.w};
-        float L[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        float2 L01 = make_float2(0.0f, 0.0f), L23 = make_float2(0.0f, 0.0f);
 
         // outer axes: neighbour rows one by one
 #pragma unroll
@@ -258,24 +302,15 @@ ODP_HD bool stage_tile(const GridDesc &g, const DynDesc &dy, const StageArgs &A,
                 m2 = axis_row(src, base, id, id - 2, stride, n, per);
                 p2 = axis_row(src, base, id, id + 2, stride, n, per);
             }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                float dm, dp;
-                diffs<ORDER>(lane(m2, k), lane(m1, k), f[k], lane(p1, k), lane(p2, k), dm, dp);
-                L[k] += axis_term(dm, dp, cA[d][k], cS[d], A.cD[d]);
-            }
+            segment_axis<ORDER>(m2, m1, c4, p1, p2, cA[d], cS[d], A.cD[d], L01, L23, has_drift<DYN, ND>(d), has_bound<DYN, ND>(d));
         }
 
         // axis ND-2 from the column
         if (ND >= 2) {
             constexpr int d = ND - 2 < 0 ? 0 : ND - 2;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                float dm, dp;
-                diffs<ORDER>(lane(col[i + O - 2 < 0 ? 0 : i + O - 2], k), lane(col[i + O - 1], k), f[k],
-                             lane(col[i + O + 1], k), lane(col[i + O + 2 < NC ? i + O + 2 : NC - 1], k), dm, dp);
-                L[k] += axis_term(dm, dp, cA[d][k], cS[d], A.cD[d]);
-            }
+            const float4 m2 = col[i + O - 2 < 0 ? 0 : i + O - 2], m1 = col[i + O - 1];
+            const float4 p1 = col[i + O + 1], p2 = col[i + O + 2 < NC ? i + O + 2 : NC - 1];
+            segment_axis<ORDER>(m2, m1, c4, p1, p2, cA[d], cS[d], A.cD[d], L01, L23, has_drift<DYN, ND>(d), has_bound<DYN, ND>(d));
         }
 
         // last axis: an eight-node window w[j] = phi(first node - 2 + j)
@@ -298,40 +333,19 @@ ODP_HD bool stage_tile(const GridDesc &g, const DynDesc &dy, const StageArgs &A,
             for (int j = 0; j < 8; ++j)
                 if (j < 2 || j >= 6 || s0 + j - 2 >= nl) w[j] = last_axis_value(rowp, s0 + j - 2, nl, per);
         }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float dm, dp;
-            diffs<ORDER>(w[k], w[k + 1], w[k + 2], w[k + 3], w[k + 4], dm, dp);
-            L[k] += axis_term(dm, dp, cA[ND - 1][k], cS[ND - 1], A.cD[ND - 1]);
-        }
+        float L[4] = {L01.x, L01.y, L23.x, L23.y};
+        axis_last<ORDER>(w, cA[ND - 1], cS[ND - 1], A.cD[ND - 1], L, has_drift<DYN, ND>(ND - 1), has_bound<DYN, ND>(ND - 1));
 
-        // update, Heun average, non-finite flag, BRT min
-        float v[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = f[k] + A.dt * L[k];
-        if (A.stage == 2) {
-            const float4 b4 = *reinterpret_cast<const float4 *>(A.prev + base);
-            v[0] = 0.5f * (b4.x + v[0]);
-            v[1] = 0.5f * (b4.y + v[1]);
-            v[2] = 0.5f * (b4.z + v[2]);
-            v[3] = 0.5f * (b4.w + v[3]);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (k < nvalid && !isfinite(v[k])) bad = true;
-        if (A.brt && A.stage != 1) {
-            const float4 l4 = ldg4(A.l + base);
-            v[0] = fminf(v[0], l4.x);
-            v[1] = fminf(v[1], l4.y);
-            v[2] = fminf(v[2], l4.z);
-            v[3] = fminf(v[3], l4.w);
-        }
+        float4 out;
+        const bool bad_here = stage_epilogue(A, base, c4, L, nvalid, out);
+        bad = bad || bad_here;
         if (nvalid == 4) {
-            *reinterpret_cast<float4 *>(A.dst + base) = make_float4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<float4 *>(A.dst + base) = out;
         } else {
+            const float o[4] = {out.x, out.y, out.z, out.w};
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                if (k < nvalid) A.dst[base + k] = v[k];
+                if (k < nvalid) A.dst[base + k] = o[k];
         }
     }
     return bad;

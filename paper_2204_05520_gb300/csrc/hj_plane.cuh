@@ -103,7 +103,14 @@ __global__ void __launch_bounds__(256) k_stage_plane(GridDesc g, DynDesc dy, Sol
     float cD[ND];
 #pragma unroll
     for (int d = 0; d < ND; ++d) cD[d] = 0.5f * bits_to_float(ab[d]) * g.inv_dz[d];
-    const float dt = float(st->dt);
+    StageArgs A;
+    A.src = src;
+    A.prev = prev;
+    A.dst = dst;
+    A.l = l;
+    A.dt = float(st->dt);
+    A.stage = stage;
+    A.brt = brt;
 
     // this CTA's pencil: outer indices of axes 0..ND-4 and its chunk of axis ND-3
     const uint32_t item = blockIdx.x;
@@ -257,43 +264,37 @@ __global__ void __launch_bounds__(256) k_stage_plane(GridDesc g, DynDesc dy, Sol
         // ---- per-node update --------------------------------------------------
         idx[sa] = s;
         const long long gplane = (pencil + s) * (long long)pg.plane;
+        const float *rm1 = ring_slot(s - 1), *rp1 = ring_slot(s + 1);
+        const float *rm2 = (O == 2) ? ring_slot(s - 2) : rm1, *rp2 = (O == 2) ? ring_slot(s + 2) : rp1;
         for (int u = tid; u < nr * (npad / 4); u += nth) {
             const int r = int(fast_div(uint32_t(u), g.div_segs));
             const int s0 = (u - r * (npad / 4)) * 4;
-            if (s0 >= nl) continue;
             idx[ND - 2] = r;
             idx[ND - 1] = s0;
             float cA[ND][4], cS[ND];
             drift<DYN, ND>(g, dy, idx, cA, cS);
             const float *C = c0 + r * cp + s0;
             const float4 c4 = *reinterpret_cast<const float4 *>(C);
-            const float f[4] = {c4.x, c4.y, c4.z, c4.w};
-            float L[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            float2 L01 = make_float2(0.0f, 0.0f), L23 = make_float2(0.0f, 0.0f);
             const int off = r * npad + s0;
 
-            // stream axis from the ring, outer axes from the neighbour planes
+            // outer axes from the neighbour planes
 #pragma unroll
-            for (int d = 0; d <= NOUT; ++d) {
-                float4 m1, p1, m2, p2;
-                if (d == NOUT) {
-                    m1 = *reinterpret_cast<const float4 *>(ring_slot(s - 1) + off);
-                    p1 = *reinterpret_cast<const float4 *>(ring_slot(s + 1) + off);
-                    m2 = (O == 2) ? *reinterpret_cast<const float4 *>(ring_slot(s - 2) + off) : m1;
-                    p2 = (O == 2) ? *reinterpret_cast<const float4 *>(ring_slot(s + 2) + off) : p1;
-                } else {
-                    const float *base = nb + d * 2 * O * pg.plane + off;
-                    m1 = *reinterpret_cast<const float4 *>(base + (O - 1) * pg.plane);
-                    p1 = *reinterpret_cast<const float4 *>(base + O * pg.plane);
-                    m2 = (O == 2) ? *reinterpret_cast<const float4 *>(base) : m1;
-                    p2 = (O == 2) ? *reinterpret_cast<const float4 *>(base + (2 * O - 1) * pg.plane) : p1;
-                }
-                const int ax = (d == NOUT) ? sa : d;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    float dm, dp;
-                    diffs<ORDER>(lane(m2, k), lane(m1, k), f[k], lane(p1, k), lane(p2, k), dm, dp);
-                    L[k] += axis_term(dm, dp, cA[ax][k], cS[ax], cD[ax]);
-                }
+            for (int d = 0; d < NOUT; ++d) {
+                const float *base = nb + d * 2 * O * pg.plane + off;
+                const float4 m1 = *reinterpret_cast<const float4 *>(base + (O - 1) * pg.plane);
+                const float4 p1 = *reinterpret_cast<const float4 *>(base + O * pg.plane);
+                const float4 m2 = (O == 2) ? *reinterpret_cast<const float4 *>(base) : m1;
+                const float4 p2 = (O == 2) ? *reinterpret_cast<const float4 *>(base + (2 * O - 1) * pg.plane) : p1;
+                segment_axis<ORDER>(m2, m1, c4, p1, p2, cA[d], cS[d], cD[d], L01, L23, has_drift<DYN, ND>(d), has_bound<DYN, ND>(d));
+            }
+            // stream axis from the ring
+            {
+                const float4 m1 = *reinterpret_cast<const float4 *>(rm1 + off);
+                const float4 p1 = *reinterpret_cast<const float4 *>(rp1 + off);
+                const float4 m2 = (O == 2) ? *reinterpret_cast<const float4 *>(rm2 + off) : m1;
+                const float4 p2 = (O == 2) ? *reinterpret_cast<const float4 *>(rp2 + off) : p1;
+                segment_axis<ORDER>(m2, m1, c4, p1, p2, cA[ND - 3], cS[ND - 3], cD[ND - 3], L01, L23, has_drift<DYN, ND>(ND - 3), has_bound<DYN, ND>(ND - 3));
             }
             // in-plane row axis (ND-2)
             {
@@ -301,62 +302,34 @@ __global__ void __launch_bounds__(256) k_stage_plane(GridDesc g, DynDesc dy, Sol
                 const float4 p1 = *reinterpret_cast<const float4 *>(C + cp);
                 const float4 m2 = (O == 2) ? *reinterpret_cast<const float4 *>(C - 2 * cp) : m1;
                 const float4 p2 = (O == 2) ? *reinterpret_cast<const float4 *>(C + 2 * cp) : p1;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    float dm, dp;
-                    diffs<ORDER>(lane(m2, k), lane(m1, k), f[k], lane(p1, k), lane(p2, k), dm, dp);
-                    L[k] += axis_term(dm, dp, cA[ND - 2][k], cS[ND - 2], cD[ND - 2]);
-                }
+                segment_axis<ORDER>(m2, m1, c4, p1, p2, cA[ND - 2], cS[ND - 2], cD[ND - 2], L01, L23, has_drift<DYN, ND>(ND - 2), has_bound<DYN, ND>(ND - 2));
             }
             // last axis: window w[j] = phi(s0 - 2 + j); halo columns are in place
+            float L[4] = {L01.x, L01.y, L23.x, L23.y};
             {
                 const float2 lh = *reinterpret_cast<const float2 *>(C - 2);
                 const float2 rh = *reinterpret_cast<const float2 *>(C + 4);
-                float w[8] = {lh.x, lh.y, f[0], f[1], f[2], f[3], rh.x, rh.y};
+                float w[8] = {lh.x, lh.y, c4.x, c4.y, c4.z, c4.w, rh.x, rh.y};
                 // a partial last segment: the window continues with the halo columns
                 if (s0 + 4 > nl) {
 #pragma unroll
                     for (int j = 2; j < 8; ++j)
                         if (s0 + j - 2 >= nl) w[j] = C[j - 2];
                 }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    float dm, dp;
-                    diffs<ORDER>(w[k], w[k + 1], w[k + 2], w[k + 3], w[k + 4], dm, dp);
-                    L[k] += axis_term(dm, dp, cA[ND - 1][k], cS[ND - 1], cD[ND - 1]);
-                }
+                axis_last<ORDER>(w, cA[ND - 1], cS[ND - 1], cD[ND - 1], L, has_drift<DYN, ND>(ND - 1), has_bound<DYN, ND>(ND - 1));
             }
             // update, Heun average, non-finite flag, BRT min
-            const long long gi = gplane + off;
-            float v[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) v[k] = f[k] + dt * L[k];
-            if (stage == 2) {
-                const float4 b4 = *reinterpret_cast<const float4 *>(prev + gi);
-                v[0] = 0.5f * (b4.x + v[0]);
-                v[1] = 0.5f * (b4.y + v[1]);
-                v[2] = 0.5f * (b4.z + v[2]);
-                v[3] = 0.5f * (b4.w + v[3]);
-            }
             const int nvalid = nl - s0 < 4 ? nl - s0 : 4;
-            bool bad = false;
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (k < nvalid && !isfinite(v[k])) bad = true;
-            if (bad) atomicOr(&st->flags, FLAG_NONFINITE);
-            if (brt && stage != 1) {
-                const float4 l4 = ldg4(l + gi);
-                v[0] = fminf(v[0], l4.x);
-                v[1] = fminf(v[1], l4.y);
-                v[2] = fminf(v[2], l4.z);
-                v[3] = fminf(v[3], l4.w);
-            }
+            float4 out;
+            if (stage_epilogue(A, int(gplane + off), c4, L, nvalid, out)) atomicOr(&st->flags, FLAG_NONFINITE);
+            const long long gi = gplane + off;
             if (nvalid == 4) {
-                *reinterpret_cast<float4 *>(dst + gi) = make_float4(v[0], v[1], v[2], v[3]);
+                *reinterpret_cast<float4 *>(dst + gi) = out;
             } else {
+                const float o[4] = {out.x, out.y, out.z, out.w};
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
-                    if (k < nvalid) dst[gi + k] = v[k];
+                    if (k < nvalid) dst[gi + k] = o[k];
             }
         }
         __syncthreads();
