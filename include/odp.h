@@ -214,6 +214,35 @@ odp_status odp_batch_solve(odp_grid *const *grids, int n, const double *T, odp_s
  * occupancy limit is used). */
 odp_status odp_batch_set_autotune(int enabled);
 
+/* Allocation-free single solve.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they need
+ * a solve -- code running inside a memory pool or arena it does not own (a
+ * framework's caching allocator, a serving process that partitioned its HBM
+ * up front) or code that must not call cudaMalloc/cudaFree because those
+ * calls synchronise the device.  It solves one grid over tau = {0, T} exactly
+ * as odp_grid_create + odp_set_dynamics + odp_set_target + odp_solve_hjb +
+ * odp_value_readback would (same step schedule, same kernel arithmetic), but
+ * calls no allocating routine: everything besides the caller's buffers lives
+ * in one file-scope device array of 16 MiB that every GPU loading the library
+ * holds until the process exits.
+ *  l, out       device pointers, odp_grid_points floats each, dense C order
+ *               (l: the target; out: the final value); the caller owns both
+ *  other args   as odp_grid_create / odp_set_dynamics / odp_solve_hjb; models:
+ *               Dubins3D, DubinsCar4D, 2-3D single integrator
+ *  cuda_stream  stream the work runs on (NULL: legacy default stream); the
+ *               call synchronises it before returning
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents:
+ * each call clears what must start at zero, and calls whose GPU work overlaps
+ * (for example on two streams at once) race on it.
+ * Errors: ODP_EINVAL (arguments, or a grid needing more than the array holds:
+ * about 1.3 million nodes), ODP_ENUMERIC, ODP_ECUDA. */
+odp_status odp_solve_noalloc(int ndim, const int32_t *n, const double *lo, const double *hi,
+                             const uint8_t *periodic, odp_dyn kind, const double *params, int n_params,
+                             odp_mode u_mode, odp_mode d_mode, const float *l, double T, odp_set set,
+                             int space_order, int time_order, double cfl, float *out, void *cuda_stream);
+
 /* Measurement helper (no paper counterpart): launch the fused stage kernel of
  * the grid's last solve `reps` times on its stream, outside the graph, and
  * return the mean device time of one launch in *ms_out (CUDA events; the call

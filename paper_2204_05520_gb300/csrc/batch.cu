@@ -512,3 +512,246 @@ extern "C" odp_status odp_batch_solve(odp_grid *const *grids, int n, const doubl
     }
     return ODP_OK;
 }
+
+// ===========================================================================
+// Allocation-free single solve (odp_solve_noalloc)
+//
+// Some callers cannot allocate device memory at the point where they need a
+// solve: code that runs inside a memory pool or arena it does not own (a
+// framework's caching allocator, a serving process whose HBM is partitioned
+// up front), or code that must not call cudaMalloc/cudaFree because those
+// calls synchronise the whole device.  This entry point serves them: the
+// caller passes the target and the output as device buffers, and everything
+// else the solve needs (the two value buffers, the target copy, node tables,
+// the batch record, the barrier, the solve state) lives in one file-scope
+// device array of fixed size.  It runs the same persistent batched kernel as
+// odp_batch_solve on a single grid, so its result equals odp_solve_hjb's.
+//
+// The array is held by every GPU that loads the library until the process
+// exits.  All calls share it and it keeps the last call's contents: each call
+// clears what must start at zero (barrier, flags, target padding), and calls
+// whose GPU work overlaps (for example on two streams) race on it.
+// ===========================================================================
+
+namespace odp {
+
+constexpr size_t kNoallocBytes = size_t(16) << 20;   // 16 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+// One grid's rounds from the solve's own step count (read on the device).
+template <int ORDER, int R>
+__global__ void __launch_bounds__(256) k_noalloc_run(BatchGrid *bg, BatchBarrier *bar)
+{
+    __shared__ BatchGrid sB;
+    {
+        const int words = int(sizeof(BatchGrid) / 4);
+        const unsigned *srcw = reinterpret_cast<const unsigned *>(bg);
+        unsigned *dstw = reinterpret_cast<unsigned *>(&sB);
+        for (int w = threadIdx.x; w < words; w += blockDim.x) dstw[w] = srcw[w];
+    }
+    __syncthreads();
+    unsigned gen = 0;
+    const int phases = sB.time_order == 2 ? 2 : 1;
+    for (int r = 0; r < sB.n_steps; ++r) {
+        for (int phase = 0; phase < phases; ++phase) {
+            for (int i = blockIdx.x; i < sB.items; i += gridDim.x)
+                if (batch_item<ORDER, R>(sB, i, r, phase)) atomicOr(&sB.state->flags, FLAG_NONFINITE);
+            if (!grid_barrier(bar, gen)) return;
+        }
+    }
+}
+
+// Copy the final value (a or b by step parity) into the caller's dense output.
+__global__ void k_noalloc_out(const BatchGrid *bg, float *out)
+{
+    const BatchGrid &B = *bg;
+    const float *src = ((B.time_order == 1) && (B.n_steps & 1)) ? B.b : B.a;
+    const int nl = B.g.n[B.g.ndim - 1], npad = B.g.n_pad;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.g.total; i += gridDim.x * blockDim.x) {
+        const int row = i / nl, c = i - row * nl;
+        out[i] = src[row * npad + c];
+    }
+}
+
+struct NoallocDevice {
+    std::mutex mu;
+    unsigned char *base[64] = {nullptr};
+};
+
+static NoallocDevice &noalloc_devices()
+{
+    static NoallocDevice d;
+    return d;
+}
+
+}  // namespace odp
+
+extern "C" odp_status odp_solve_noalloc(int ndim, const int32_t *n, const double *lo, const double *hi,
+                                        const uint8_t *periodic, odp_dyn kind, const double *params, int n_params,
+                                        odp_mode u_mode, odp_mode d_mode, const float *l, double T, odp_set set,
+                                        int space_order, int time_order, double cfl, float *out, void *cuda_stream)
+{
+    if (ndim < 2 || ndim > 4 || !n || !lo || !hi || !periodic || !l || !out)
+        return fail(ODP_EINVAL, "odp_solve_noalloc: bad arguments (2 to 4 dimensions, device l and out)");
+    if (!(T > 0.0) || !std::isfinite(T)) return fail(ODP_EINVAL, "odp_solve_noalloc: T must be finite and > 0");
+    if (set != ODP_BRS && set != ODP_BRT) return fail(ODP_EINVAL, "odp_solve_noalloc: set must be BRS or BRT");
+    if ((space_order != 1 && space_order != 2) || (time_order != 1 && time_order != 2))
+        return fail(ODP_EINVAL, "odp_solve_noalloc: orders must be 1 or 2");
+    if (!(cfl > 0.0 && cfl <= 1.0)) return fail(ODP_EINVAL, "odp_solve_noalloc: cfl must lie in (0, 1]");
+    if ((u_mode != ODP_MIN && u_mode != ODP_MAX) || (d_mode != ODP_MIN && d_mode != ODP_MAX))
+        return fail(ODP_EINVAL, "odp_solve_noalloc: modes must be ODP_MIN or ODP_MAX");
+    int need = 0, angle = -1;
+    if (kind == ODP_DYN_DUBINS3D && ndim == 3) {
+        need = 2;
+        angle = 2;
+    } else if (kind == ODP_DYN_DUBINSCAR4D && ndim == 4) {
+        need = 2;
+        angle = 3;
+    } else if (kind == ODP_DYN_SINGLE_INT && (ndim == 2 || ndim == 3)) {
+        need = 1;
+    } else {
+        return fail(ODP_EINVAL, "odp_solve_noalloc: supports Dubins3D, DubinsCar4D and the 2-3D single integrator");
+    }
+    if (!params || n_params < need || n_params > 8) return fail(ODP_EINVAL, "odp_solve_noalloc: missing parameters");
+    for (int k = 0; k < n_params; ++k)
+        if (!std::isfinite(params[k]) || params[k] < 0.0)
+            return fail(ODP_EINVAL, "odp_solve_noalloc: parameter %d must be finite and >= 0", k);
+    if (angle >= 0 && !periodic[angle]) return fail(ODP_EINVAL, "odp_solve_noalloc: the angle axis must be periodic");
+
+    // grid description (row-blocked pass; same rules as odp_grid_create)
+    GridDesc D{};
+    D.ndim = ndim;
+    int64_t total = 1;
+    for (int d = 0; d < ndim; ++d) {
+        if (n[d] < (periodic[d] ? 1 : 2) || !(hi[d] > lo[d]) || !std::isfinite(lo[d]) || !std::isfinite(hi[d]))
+            return fail(ODP_EINVAL, "odp_solve_noalloc: bad axis %d", d);
+        total *= n[d];
+    }
+    const int nl = n[ndim - 1], npad = (nl + 3) / 4 * 4;
+    const int64_t rows = total / nl, total_pad = rows * npad;
+    int64_t tab_len = 0;
+    for (int d = 0; d < ndim; ++d) tab_len += 3 * int64_t((n[d] + 3) / 4 * 4);
+    const size_t rec = (sizeof(BatchGrid) + 255) / 256 * 256;
+    const size_t barb = 256, stb = (sizeof(SolveState) + 255) / 256 * 256;
+    const size_t tabb = (size_t(tab_len) * 4 + 255) / 256 * 256;
+    const size_t arrb = (size_t(total_pad) * 4 + 255) / 256 * 256;
+    const size_t bytes = rec + barb + stb + tabb + 3 * arrb;
+    if (bytes > kNoallocBytes)
+        return fail(ODP_EINVAL, "odp_solve_noalloc: the grid needs %zu bytes of scratch, the fixed limit is %zu "
+                                "(about %lld nodes)", bytes, kNoallocBytes, (long long)(kNoallocBytes / 12));
+
+    int device = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (s) ODP_TRY_CUDA(cudaStreamGetDevice(s, &device));
+    else ODP_TRY_CUDA(cudaGetDevice(&device));
+    if (device < 0 || device >= 64) return fail(ODP_EINVAL, "odp_solve_noalloc: device %d out of range", device);
+    ODP_TRY_CUDA(cudaSetDevice(device));
+    NoallocDevice &ND = noalloc_devices();
+    std::lock_guard<std::mutex> lock(ND.mu);
+    if (!ND.base[device]) {
+        // set-up, once per device, with that device current: the array's
+        // device address (its host-side name is not a device address)
+        void *ptr = nullptr;
+        ODP_TRY_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+        ND.base[device] = static_cast<unsigned char *>(ptr);
+    }
+    unsigned char *base = ND.base[device];
+    BatchGrid *d_rec = reinterpret_cast<BatchGrid *>(base);
+    BatchBarrier *d_bar = reinterpret_cast<BatchBarrier *>(base + rec);
+    SolveState *d_state = reinterpret_cast<SolveState *>(base + rec + barb);
+    float *d_tab = reinterpret_cast<float *>(base + rec + barb + stb);
+    float *d_l = reinterpret_cast<float *>(base + rec + barb + stb + tabb);
+    float *d_a = reinterpret_cast<float *>(base + rec + barb + stb + tabb + arrb);
+    float *d_b = reinterpret_cast<float *>(base + rec + barb + stb + tabb + 2 * arrb);
+
+    // tables: node coordinates, cos and sin per axis (float64 rounded once)
+    std::vector<float> tab(static_cast<size_t>(tab_len), 0.0f);
+    int64_t off = 0;
+    for (int d = 0; d < ndim; ++d) {
+        const double h = periodic[d] ? (hi[d] - lo[d]) / double(n[d]) : (hi[d] - lo[d]) / double(n[d] - 1);
+        const int64_t np = (n[d] + 3) / 4 * 4;
+        D.n[d] = n[d];
+        D.periodic[d] = periodic[d] ? 1 : 0;
+        D.dz[d] = h;
+        D.inv_dz[d] = float(1.0 / h);
+        D.div[d] = make_fastdiv(uint32_t(n[d]));
+        D.coord[d] = d_tab + off;
+        for (int i = 0; i < n[d]; ++i) {
+            const double z = lo[d] + double(i) * h;
+            tab[size_t(off + i)] = float(z);
+            tab[size_t(off + np + i)] = float(std::cos(z));
+            tab[size_t(off + 2 * np + i)] = float(std::sin(z));
+        }
+        if (d == angle) {
+            D.cos_tab = d_tab + off + np;
+            D.sin_tab = d_tab + off + 2 * np;
+        }
+        off += 3 * np;
+    }
+    D.total = int(total);
+    D.n_pad = npad;
+    D.rows = int(rows);
+    D.segs = npad / 4;
+    D.nthreads = int(rows * D.segs);
+    D.div_segs = make_fastdiv(uint32_t(D.segs));
+    int64_t st = 1;
+    for (int d = ndim - 1; d >= 0; --d) {
+        D.stride[d] = int(st);
+        st *= (d == ndim - 1) ? npad : n[d];
+    }
+    D.nr = n[ndim - 2];
+    D.R = D.nr >= 4 ? 4 : 1;
+    D.row_groups = (D.nr + D.R - 1) / D.R;
+    D.planes = int(rows / D.nr);
+    D.nthreads_rb = D.segs * D.row_groups * D.planes;
+    D.div_row_groups = make_fastdiv(uint32_t(D.row_groups));
+
+    BatchGrid hb;
+    memset(&hb, 0, sizeof(hb));
+    hb.g = D;
+    hb.dy.kind = int(kind);
+    hb.dy.umode = int(u_mode);
+    hb.dy.dmode = int(d_mode);
+    hb.dy.angle_axis = angle;
+    for (int k = 0; k < n_params; ++k) hb.dy.prm[k] = float(params[k]);
+    hb.a = d_a;
+    hb.b = d_b;
+    hb.l = d_l;
+    hb.state = d_state;
+    hb.T = T;
+    hb.kind = int(kind);
+    hb.time_order = time_order;
+    hb.brt = set == ODP_BRT ? 1 : 0;
+    hb.items = (D.nthreads_rb + 255) / 256;
+
+    // upload (pageable sources are staged at once) and clear what starts at zero
+    ODP_TRY_CUDA(cudaMemcpyAsync(d_rec, &hb, sizeof(hb), cudaMemcpyHostToDevice, s));
+    ODP_TRY_CUDA(cudaMemcpyAsync(d_tab, tab.data(), size_t(tab_len) * 4, cudaMemcpyHostToDevice, s));
+    ODP_TRY_CUDA(cudaMemsetAsync(d_bar, 0, sizeof(BatchBarrier), s));
+    ODP_TRY_CUDA(cudaMemsetAsync(d_state, 0, sizeof(SolveState), s));
+    ODP_TRY_CUDA(cudaMemsetAsync(d_l, 0, size_t(total_pad) * 4, s));
+    ODP_TRY_CUDA(cudaMemcpy2DAsync(d_l, size_t(npad) * 4, l, size_t(nl) * 4, size_t(nl) * 4, size_t(rows),
+                                   cudaMemcpyDeviceToDevice, s));
+    k_batch_prepare<<<1, 256, 0, s>>>(d_rec, cfl);
+    ODP_TRY_CUDA(cudaGetLastError());
+
+    int sms = 0, per_sm = 0;
+    ODP_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    const void *fn = space_order == 1 ? (D.R == 4 ? (const void *)k_noalloc_run<1, 4> : (const void *)k_noalloc_run<1, 1>)
+                                      : (D.R == 4 ? (const void *)k_noalloc_run<2, 4> : (const void *)k_noalloc_run<2, 1>);
+    ODP_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0));
+    if (per_sm < 1) return fail(ODP_ECUDA, "odp_solve_noalloc: the kernel cannot be resident");
+    int ctas = per_sm * sms;
+    if (ctas > hb.items) ctas = hb.items;
+    void *args[] = {(void *)&d_rec, (void *)&d_bar};
+    ODP_TRY_CUDA(cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(256), args, 0, s));
+    k_noalloc_out<<<int(std::min<int64_t>((total + 255) / 256, 1024)), 256, 0, s>>>(d_rec, out);
+    ODP_TRY_CUDA(cudaGetLastError());
+    int flags[2] = {0, 0};
+    ODP_TRY_CUDA(cudaMemcpyAsync(&flags[0], &d_state->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ODP_TRY_CUDA(cudaMemcpyAsync(&flags[1], &d_bar->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ODP_TRY_CUDA(cudaStreamSynchronize(s));
+    if (flags[1]) return fail(ODP_ECUDA, "odp_solve_noalloc: a grid-wide barrier gave up waiting");
+    if (flags[0] & FLAG_NONFINITE) return fail(ODP_ENUMERIC, "odp_solve_noalloc: a non-finite value appeared");
+    return ODP_OK;
+}

@@ -84,6 +84,8 @@ def load():
             "odp_plan_geometry": ([i32, P, P, i32], i32),
             "odp_batch_solve": ([P, i32, P, i32, i32, i32, f64, P], i32),
             "odp_batch_set_autotune": ([i32], i32),
+            "odp_solve_noalloc": ([i32, P, P, P, P, i32, P, i32, i32, i32, P, f64, i32, i32, i32, f64,
+                                   P, P], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -212,6 +214,29 @@ def batch_solve(grids, horizons, set_kind="brt", space_order=1, time_order=1, cf
     _check(load().odp_batch_solve(arr, len(hs), T, SET[set_kind], int(space_order), int(time_order),
                                   float(cfl), ctypes.byref(st)), "odp_batch_solve")
     return st.as_dict()
+
+
+def solve_noalloc(problem, l, out, stream=None):
+    """Solve ``problem`` over [0, T] without allocating device memory: ``l``
+    and ``out`` are the caller's device tensors (float32, problem.n), all
+    other state lives in the library's fixed device array."""
+    nd = problem.ndim
+    n_pts = problem.points
+    lp, ldev = _buffer(l, n_pts, writable=False)
+    op, odev = _buffer(out, n_pts, writable=True)
+    if not (ldev and odev):
+        raise ValueError("l and out must be device tensors")
+    n_a = (ctypes.c_int32 * nd)(*[int(v) for v in problem.n])
+    lo_a = (ctypes.c_double * nd)(*[float(v) for v in problem.lo])
+    hi_a = (ctypes.c_double * nd)(*[float(v) for v in problem.hi])
+    per_a = (ctypes.c_uint8 * nd)(*[1 if p else 0 for p in problem.periodic])
+    prm = (ctypes.c_double * max(1, len(problem.params)))(*[float(v) for v in problem.params])
+    _check(load().odp_solve_noalloc(nd, n_a, lo_a, hi_a, per_a, DYN[problem.dynamics], prm,
+                                    len(problem.params), MODE[problem.u_mode], MODE[problem.d_mode],
+                                    lp, float(problem.tau[-1]), SET[problem.set_kind],
+                                    int(problem.space_order), int(problem.time_order),
+                                    float(problem.cfl), op, _stream_ptr(stream)), "odp_solve_noalloc")
+    return out
 
 
 def batch_set_autotune(enabled: bool):
