@@ -144,9 +144,9 @@ static void plane_geometry(GridDesc &D, int sms)
     pg.plane = D.nr * D.n_pad;
     pg.cp = D.n_pad + 8;
     const int nout = D.ndim - 3;
+    (void)nout;
     for (int o = 1; o <= 2; ++o) {
-        const long long bytes = (long long)((2 * o + 1) + 2 * o * nout) * pg.plane * 4 +
-                                (long long)(D.nr + 2 * o) * pg.cp * 4 + 16;
+        const long long bytes = (long long)(2 * o + 2) * pg.plane * 4 + (long long)(D.nr + 2 * o) * pg.cp * 4 + 16;
         pg.smem[o - 1] = bytes <= 200 * 1024 ? int(bytes) : 0;
     }
     if (pg.smem[0] == 0 && pg.smem[1] == 0) return;
