@@ -44,8 +44,13 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("dubinscar4d", "dubins3d", "rel6d", "batch512"),
+    ap.add_argument("--workload", choices=("dubinscar4d", "dubins3d", "rel6d", "batch512", "served"),
                     default="dubinscar4d")
+    ap.add_argument("--rates", default="10,30,100,300,1000,2000",
+                    help="served workload: Poisson arrival rates (req/s)")
+    ap.add_argument("--window", type=float, default=3.0,
+                    help="served workload: seconds of arrivals per rate (at most 2000 requests)")
+    ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -404,12 +409,101 @@ def run_batch(args):
     return 0
 
 
+def run_served(args):
+    """Poisson request stream (seed 1) of Dubins3D and DubinsCar4D solves
+    served with continuous batching under an HBM budget; p50/p99 latency
+    (arrival -> result ready) and completed solves/s per arrival rate."""
+    import numpy as np
+    import torch
+
+    from paper_2204_05520_gb300 import _build, inputs, odp
+
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    _build.build()
+    odp.load()
+    stream = torch.cuda.Stream()
+    rates = [float(r) for r in args.rates.split(",")]
+    points = []
+    budget = int(args.budget_gb * (1 << 30))
+    with odp.Server(budget, stream=stream) as srv:
+        for rate in rates:
+            count = int(min(2000, max(10, rate * args.window)))
+            stream_reqs = inputs.served_requests(rate, count=count, seed=1)
+            targets = [p.target_values() for _, p in stream_reqs]
+            outs = {}
+            lat, ids, arrival = [], {}, {}
+            t0 = time.monotonic()
+            nxt = 0
+            done = 0
+            deadline = t0 + 20.0 + args.window
+            while done < count and time.monotonic() < deadline:
+                now = time.monotonic() - t0
+                while nxt < count and stream_reqs[nxt][0] <= now:
+                    rid = srv.submit(stream_reqs[nxt][1], target=targets[nxt])
+                    ids[rid] = nxt
+                    arrival[rid] = t0 + stream_reqs[nxt][0]
+                    nxt += 1
+                if not ids:
+                    time.sleep(min(0.002, max(0.0, stream_reqs[nxt][0] - now)))
+                    continue
+                srv.step(rounds=8)
+                for rid in list(ids):
+                    st = srv.poll(rid)
+                    if st["state"] >= odp.REQ_DONE:
+                        p = stream_reqs[ids[rid]][1]
+                        out = outs.setdefault(p.n, np.empty(p.n, np.float32))
+                        srv.readback(rid, out)
+                        lat.append(st["t_done"] - arrival[rid])
+                        srv.release(rid)
+                        del ids[rid]
+                        done += 1
+            span = time.monotonic() - t0
+            for rid in list(ids):
+                try:
+                    srv.release(rid)
+                except odp.OdpError:
+                    pass
+            lat_sorted = sorted(lat)
+            pct = lambda q: lat_sorted[min(len(lat_sorted) - 1, int(q * len(lat_sorted)))] if lat_sorted else None
+            points.append({"rate": rate, "requests": count, "completed": done,
+                           "solves_per_s": done / span if span > 0 else None,
+                           "p50_s": pct(0.50), "p99_s": pct(0.99)})
+            # drain anything still resident before the next rate
+            while srv.info()["resident"] or srv.info()["queued"]:
+                srv.step(rounds=64)
+    # one at a time: requests of the same stream solved sequentially
+    reqs = inputs.served_requests(rates[-1], count=min(40, int(rates[-1] * args.window)), seed=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _, p in reqs:
+        with odp.Grid.for_problem(p, stream=stream) as g:
+            g.set_target(p.target_values())
+            g.solve_problem(p)
+            g.readback(np.empty(p.n, np.float32))
+    single = len(reqs) / (time.perf_counter() - t0)
+    best = max((pt["solves_per_s"] or 0.0) for pt in points)
+    if rank == 0:
+        line = {"metric": "served solves/s (saturation) with p50/p99 latency", "value": best,
+                "unit": "solves/s", "n_gpus": 1, "steps": len(points), "warmup": 0,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": "served_poisson_dubins3d_dubinscar4d", "budget_gb": args.budget_gb,
+                           "window_s": args.window, "rounds_per_launch": 8},
+                "rates": points, "one_at_a_time_solves_per_s": single,
+                "speedup_vs_one_at_a_time": best / single if single else None}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch512":
         return run_batch(args)
+    if args.workload == "served":
+        return run_served(args)
     return run_ours(args)
 
 

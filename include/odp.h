@@ -214,6 +214,89 @@ odp_status odp_batch_solve(odp_grid *const *grids, int n, const double *T, odp_s
  * occupancy limit is used). */
 odp_status odp_batch_set_autotune(int enabled);
 
+/* ------------------------------------------------------------------------
+ * Serving loop (no paper counterpart): continuous batching of solves under an
+ * HBM budget.
+ * ------------------------------------------------------------------------ */
+typedef struct odp_server odp_server;
+
+/* One solve request: a grid, a model, a target and a horizon T
+ * (tau = {0, T}).  The server runs Dubins3D (3-D) and DubinsCar4D (4-D)
+ * requests whose second-last axis has at least 4 nodes and whose angle axis
+ * (the last one) is periodic. */
+typedef struct {
+    int32_t ndim;
+    int32_t n[ODP_MAX_DIMS];
+    double lo[ODP_MAX_DIMS];
+    double hi[ODP_MAX_DIMS];
+    uint8_t periodic[ODP_MAX_DIMS];
+    odp_dyn kind;
+    int32_t n_params;
+    double params[8];
+    odp_mode u_mode, d_mode;
+    const float *target;      /* host, C order; copied by odp_server_submit */
+    double T;
+    odp_set set;
+    int32_t space_order, time_order;
+    double cfl;
+} odp_request;
+
+#define ODP_REQ_QUEUED 0      /* waiting for HBM                            */
+#define ODP_REQ_RESIDENT 1    /* admitted, advancing with the batch         */
+#define ODP_REQ_DONE 2        /* horizon reached; value resident in HBM     */
+#define ODP_REQ_FAILED 3      /* a non-finite value appeared                */
+
+typedef struct {
+    int32_t state;            /* ODP_REQ_*                                   */
+    int32_t reserved;
+    int64_t steps;            /* time steps of the solve (known once admitted) */
+    int64_t steps_done;
+    double queue_s;           /* submit -> admission                         */
+    double latency_s;         /* submit -> done                              */
+    double t_submit, t_done;  /* host monotonic clock, seconds               */
+    double bytes;             /* HBM held by the request                     */
+} odp_request_stats;
+
+typedef struct {
+    double budget_bytes, used_bytes;
+    int64_t queued, resident, launches;
+} odp_server_stats;
+
+/* Create a server whose resident solves may hold hbm_budget_bytes of device
+ * memory (allocated once, here, as one arena).  Work runs on cuda_stream.
+ * Errors: ODP_EINVAL, ODP_ENOMEM, ODP_ECUDA. */
+odp_status odp_server_create(size_t hbm_budget_bytes, void *cuda_stream, odp_server **out);
+
+/* Free the server and every request's memory (synchronises its stream). */
+odp_status odp_server_destroy(odp_server *s);
+
+/* Queue a request (the target is copied; the call returns at once).
+ * Errors: ODP_EINVAL (unsupported model or shape), ODP_ENOMEM (the request
+ * alone exceeds the budget). */
+odp_status odp_server_submit(odp_server *s, const odp_request *req, uint64_t *req_id);
+
+/* One scheduling step: admit queued requests in arrival order while their
+ * arrays fit the budget, advance every resident solve by up to `rounds` of its
+ * own time steps in one persistent launch, retire the solves that reached
+ * their horizon (their values stay in HBM).  *n_done (may be NULL) counts the
+ * requests finished by this step.  Synchronises the stream.
+ * Errors: ODP_EINVAL, ODP_ECUDA. */
+odp_status odp_server_step(odp_server *s, int rounds, int *n_done);
+
+/* State and timings of a request.  Returns ODP_ENUMERIC for a failed one. */
+odp_status odp_server_poll(odp_server *s, uint64_t req_id, odp_request_stats *out);
+
+/* Copy a finished request's value (odp C order, n_elems floats) to host or
+ * device memory.  Errors: ODP_ESTATE (not done), ODP_EINVAL. */
+odp_status odp_server_readback(odp_server *s, uint64_t req_id, float *dst, int64_t n_elems, int on_device);
+
+/* Forget a request and return its HBM to the budget (ODP_EBUSY while it is
+ * resident and unfinished). */
+odp_status odp_server_release(odp_server *s, uint64_t req_id);
+
+/* Budget, memory in use, queue and resident counts, launches so far. */
+odp_status odp_server_info(odp_server *s, odp_server_stats *out);
+
 /* Allocation-free single solve.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory when they need
  * a solve -- code running inside a memory pool or arena it does not own (a

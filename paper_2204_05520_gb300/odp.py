@@ -53,6 +53,37 @@ class BatchStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+MAXD = 6
+REQ_QUEUED, REQ_RESIDENT, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("n", ctypes.c_int32 * MAXD), ("lo", ctypes.c_double * MAXD),
+                ("hi", ctypes.c_double * MAXD), ("periodic", ctypes.c_uint8 * MAXD),
+                ("kind", ctypes.c_int), ("n_params", ctypes.c_int32), ("params", ctypes.c_double * 8),
+                ("u_mode", ctypes.c_int), ("d_mode", ctypes.c_int), ("target", ctypes.c_void_p),
+                ("T", ctypes.c_double), ("set", ctypes.c_int), ("space_order", ctypes.c_int32),
+                ("time_order", ctypes.c_int32), ("cfl", ctypes.c_double)]
+
+
+class RequestStats(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("reserved", ctypes.c_int32), ("steps", ctypes.c_int64),
+                ("steps_done", ctypes.c_int64), ("queue_s", ctypes.c_double),
+                ("latency_s", ctypes.c_double), ("t_submit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_double), ("used_bytes", ctypes.c_double),
+                ("queued", ctypes.c_int64), ("resident", ctypes.c_int64), ("launches", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -84,6 +115,14 @@ def load():
             "odp_plan_geometry": ([i32, P, P, i32], i32),
             "odp_batch_solve": ([P, i32, P, i32, i32, i32, f64, P], i32),
             "odp_batch_set_autotune": ([i32], i32),
+            "odp_server_create": ([ctypes.c_size_t, P, P], i32),
+            "odp_server_destroy": ([P], i32),
+            "odp_server_submit": ([P, P, P], i32),
+            "odp_server_step": ([P, i32, P], i32),
+            "odp_server_poll": ([P, ctypes.c_uint64, P], i32),
+            "odp_server_readback": ([P, ctypes.c_uint64, P, i64, i32], i32),
+            "odp_server_release": ([P, ctypes.c_uint64], i32),
+            "odp_server_info": ([P, P], i32),
             "odp_solve_noalloc": ([i32, P, P, P, P, i32, P, i32, i32, i32, P, f64, i32, i32, i32, f64,
                                    P, P], i32),
         }
@@ -237,6 +276,79 @@ def solve_noalloc(problem, l, out, stream=None):
                                     int(problem.space_order), int(problem.time_order),
                                     float(problem.cfl), op, _stream_ptr(stream)), "odp_solve_noalloc")
     return out
+
+
+class Server:
+    """Continuous-batching solve server (odp_server_*): submit problems, step
+    the scheduler, poll, read back, release."""
+
+    def __init__(self, hbm_budget_bytes: int, stream=None):
+        self.handle = ctypes.c_void_p()
+        _check(load().odp_server_create(int(hbm_budget_bytes), _stream_ptr(stream),
+                                        ctypes.byref(self.handle)), "odp_server_create")
+        self._targets = {}
+
+    def close(self):
+        if self.handle:
+            _check(load().odp_server_destroy(self.handle), "odp_server_destroy")
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, problem, target=None) -> int:
+        nd = problem.ndim
+        l = np.ascontiguousarray(problem.target_values() if target is None else target, dtype=np.float32)
+        q = Request()
+        q.ndim = nd
+        for d in range(nd):
+            q.n[d] = int(problem.n[d])
+            q.lo[d] = float(problem.lo[d])
+            q.hi[d] = float(problem.hi[d])
+            q.periodic[d] = 1 if problem.periodic[d] else 0
+        q.kind = DYN[problem.dynamics]
+        q.n_params = len(problem.params)
+        for k, v in enumerate(problem.params):
+            q.params[k] = float(v)
+        q.u_mode = MODE[problem.u_mode]
+        q.d_mode = MODE[problem.d_mode]
+        q.target = l.ctypes.data
+        q.T = float(problem.tau[-1])
+        q.set = SET[problem.set_kind]
+        q.space_order = int(problem.space_order)
+        q.time_order = int(problem.time_order)
+        q.cfl = float(problem.cfl)
+        rid = ctypes.c_uint64()
+        _check(load().odp_server_submit(self.handle, ctypes.byref(q), ctypes.byref(rid)), "odp_server_submit")
+        return rid.value
+
+    def step(self, rounds: int = 8) -> int:
+        done = ctypes.c_int(0)
+        _check(load().odp_server_step(self.handle, int(rounds), ctypes.byref(done)), "odp_server_step")
+        return done.value
+
+    def poll(self, rid: int) -> dict:
+        st = RequestStats()
+        _check(load().odp_server_poll(self.handle, ctypes.c_uint64(rid), ctypes.byref(st)), "odp_server_poll")
+        return st.as_dict()
+
+    def readback(self, rid: int, out):
+        ptr, dev = _buffer(out, out.size if isinstance(out, np.ndarray) else out.numel(), writable=True)
+        n = out.size if isinstance(out, np.ndarray) else out.numel()
+        _check(load().odp_server_readback(self.handle, ctypes.c_uint64(rid), ptr, n, dev),
+               "odp_server_readback")
+        return out
+
+    def release(self, rid: int):
+        _check(load().odp_server_release(self.handle, ctypes.c_uint64(rid)), "odp_server_release")
+
+    def info(self) -> dict:
+        st = ServerStats()
+        _check(load().odp_server_info(self.handle, ctypes.byref(st)), "odp_server_info")
+        return st.as_dict()
 
 
 def batch_set_autotune(enabled: bool):

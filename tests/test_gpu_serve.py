@@ -1,0 +1,113 @@
+"""Serving loop (odp_server_*): continuous batching under an HBM budget.
+
+Requests that arrive while others are on the GPU join later launches; each
+result must equal the same request solved alone (odp_solve_hjb), and the
+resident HBM never exceeds the budget."""
+import numpy as np
+import pytest
+
+from paper_2204_05520_gb300 import inputs, odp
+
+pytestmark = pytest.mark.gpu
+REL_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_05520_gb300 import _build
+
+    _build.build()
+    odp.load()
+    return torch
+
+
+def solo(problem):
+    import torch
+
+    l = problem.target_values()
+    with odp.Grid.for_problem(problem) as g:
+        g.set_target(torch.from_numpy(l).cuda())
+        g.solve_problem(problem)
+        return g.readback(torch.empty(l.shape, device="cuda")).cpu().numpy()
+
+
+def mixed_requests(count, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        if rng.uniform() < 0.5:
+            side = int(rng.integers(17, 33))
+            out.append(inputs.dubins3d(n=(side, side, side), v=float(rng.uniform(0.5, 2.0)),
+                                       w_max=float(rng.uniform(0.5, 1.5)),
+                                       radius=float(rng.uniform(0.5, 1.5)),
+                                       horizon=float(rng.uniform(0.2, 1.0))))
+        else:
+            side = int(rng.integers(9, 15))
+            out.append(inputs.dubinscar4d(n=(side,) * 4, a_max=float(rng.uniform(0.5, 1.5)),
+                                          w_max=float(rng.uniform(0.5, 1.5)),
+                                          radius=float(rng.uniform(0.5, 1.5)),
+                                          horizon=float(rng.uniform(0.2, 0.8))))
+    return out
+
+
+def test_results_are_the_same_alone_and_in_the_mix():
+    problems = mixed_requests(10, seed=5)
+    with odp.Server(hbm_budget_bytes=256 << 20) as srv:
+        ids = {}
+        # arrivals spread over the first steps: later requests join a batch
+        # that is already running
+        pending = list(enumerate(problems))
+        step = 0
+        while pending or any(srv.poll(i)["state"] < odp.REQ_DONE for i in ids.values()):
+            while pending and len(ids) < 3 * (step + 1):
+                k, p = pending.pop(0)
+                ids[k] = srv.submit(p)
+            srv.step(rounds=4)
+            step += 1
+            assert step < 10000
+        assert srv.info()["launches"] > 1
+        for k, p in enumerate(problems):
+            st = srv.poll(ids[k])
+            assert st["state"] == odp.REQ_DONE and st["steps_done"] == st["steps"]
+            v = srv.readback(ids[k], np.empty(p.n, np.float32))
+            ref = solo(p)
+            l = p.target_values()
+            assert np.abs(v - ref).max() <= REL_TOL * float(l.max() - l.min())
+            srv.release(ids[k])
+        assert srv.info()["used_bytes"] == 0
+
+
+def test_admission_respects_the_budget():
+    p = inputs.dubins3d(n=(31, 31, 32), horizon=0.5)
+    per = 4 * 3 * 31 * 31 * 32
+    with odp.Server(hbm_budget_bytes=int(per * 2.5) + (1 << 16)) as srv:
+        ids = [srv.submit(p) for _ in range(5)]
+        srv.step(rounds=1)
+        info = srv.info()
+        assert info["resident"] == 2 and info["queued"] == 3
+        assert info["used_bytes"] <= info["budget_bytes"]
+        steps = 0
+        while ids:
+            srv.step(rounds=16)
+            steps += 1
+            assert steps < 1000
+            for i in list(ids):
+                if srv.poll(i)["state"] == odp.REQ_DONE:
+                    srv.readback(i, np.empty(p.n, np.float32))
+                    srv.release(i)
+                    ids.remove(i)
+            assert srv.info()["used_bytes"] <= srv.info()["budget_bytes"]
+        assert srv.info()["used_bytes"] == 0
+
+
+def test_unsupported_and_oversized_requests_are_refused():
+    with odp.Server(hbm_budget_bytes=8 << 20) as srv:
+        with pytest.raises(odp.OdpError) as e:
+            srv.submit(inputs.rel6d(n=(4, 4, 4, 4, 4, 4)))
+        assert e.value.code == odp.EINVAL
+        with pytest.raises(odp.OdpError) as e:
+            srv.submit(inputs.dubins3d(n=(101, 101, 101)))
+        assert e.value.code == odp.ENOMEM
