@@ -118,10 +118,11 @@ odp_status odp_grid_create(int ndim, const int32_t *n, const double *lo, const d
                            const uint8_t *periodic, void *cuda_stream, odp_grid **out);
 
 /* Launch geometry the library would use for a grid of this shape (host only,
- * no CUDA call; no paper counterpart).  out[0..11] = padded last axis, rows
+ * no CUDA call; no paper counterpart).  out[0..13] = padded last axis, rows
  * per thread of the row-blocked pass, its row groups, its planes, its threads,
- * plane-streaming pass used (0/1), stream-axis length, chunk, CTAs, threads
- * per CTA, shared bytes for stencil radius 1 and 2.  n_out >= 12.
+ * plane-streaming pass used (0/1), stream-axis length, stream-axis chunk per
+ * CTA, CTAs, threads per CTA, shared bytes for stencil radius 1 and 2, rows
+ * per band, bands.  n_out >= 14.
  * Errors: ODP_EINVAL. */
 odp_status odp_plan_geometry(int ndim, const int32_t *n, int64_t *out, int n_out);
 

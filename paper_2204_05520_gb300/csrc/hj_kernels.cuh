@@ -176,17 +176,18 @@ ODP_HD void segment_axis(const float4 &m2, const float4 &m1, const float4 &c, co
                                    cS, cD, L23, has_a, has_s);
 }
 
-// Update of a four-node segment: phi + dt L (Euler / RK2 stage), the Heun
-// average with phi^n on RK2 stage 2, the non-finite check of the valid
-// nodes, and the min with l on the last stage of a tube.  Returns true if a
-// valid node is not finite.
-ODP_HD bool stage_epilogue(const StageArgs &A, int base, const float4 &c4, const float *L, int nvalid, float4 &out)
+// Update of a four-node segment from its right-hand side L: phi + dt L
+// (Euler / RK2 stage), the Heun average with phi^n (b4) on RK2 stage 2, the
+// non-finite check of the valid nodes, and the min with l (l4) when use_l
+// (the last stage of a step of a tube).  Returns true if a valid node is not
+// finite.
+ODP_HD bool update_segment(float dt_, int stage, bool use_l, const float4 &c4, const float *L, const float4 &b4,
+                           const float4 &l4, int nvalid, float4 &out)
 {
-    const float2 dt = f2splat(A.dt);
+    const float2 dt = f2splat(dt_);
     float2 v01 = f2fma(dt, make_float2(L[0], L[1]), make_float2(c4.x, c4.y));
     float2 v23 = f2fma(dt, make_float2(L[2], L[3]), make_float2(c4.z, c4.w));
-    if (A.stage == 2) {
-        const float4 b4 = *reinterpret_cast<const float4 *>(A.prev + base);
+    if (stage == 2) {
         v01 = f2mul(f2splat(0.5f), f2add(make_float2(b4.x, b4.y), v01));
         v23 = f2mul(f2splat(0.5f), f2add(make_float2(b4.z, b4.w), v23));
     }
@@ -196,14 +197,23 @@ ODP_HD bool stage_epilogue(const StageArgs &A, int base, const float4 &c4, const
     for (int k = 0; k < 4; ++k)
         if (k < nvalid && !isfinite(v[k])) bad = true;
     out = make_float4(v[0], v[1], v[2], v[3]);
-    if (A.brt && A.stage != 1) {
-        const float4 l4 = ldg4(A.l + base);
+    if (use_l) {
         out.x = fminf(out.x, l4.x);
         out.y = fminf(out.y, l4.y);
         out.z = fminf(out.z, l4.z);
         out.w = fminf(out.w, l4.w);
     }
     return bad;
+}
+
+// update_segment with phi^n and l read at storage offset base.
+ODP_HD bool stage_epilogue(const StageArgs &A, int base, const float4 &c4, const float *L, int nvalid, float4 &out)
+{
+    float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f), l4 = b4;
+    if (A.stage == 2) b4 = *reinterpret_cast<const float4 *>(A.prev + base);
+    const bool use_l = A.brt && A.stage != 1;
+    if (use_l) l4 = ldg4(A.l + base);
+    return update_segment(A.dt, A.stage, use_l, c4, L, b4, l4, nvalid, out);
 }
 
 // Row j (possibly outside [0, n)) of axis `axis` relative to row i0 of the
@@ -463,7 +473,7 @@ cudaError_t launch_stage_t(const GridDesc &g, const DynDesc &dy, SolveState *st,
                            int order, int stage, int brt, cudaStream_t s)
 {
     if constexpr (ND >= 3) {
-        if (g.pg.use && g.pg.smem[order - 1] > 0) {
+        if (g.pg.use) {
             if (order == 1)
                 k_stage_plane<ND, 1, DYN><<<g.pg.items, g.pg.threads, g.pg.smem[0], s>>>(g, dy, st, l, stage, brt);
             else
@@ -486,16 +496,11 @@ cudaError_t launch_stage_t(const GridDesc &g, const DynDesc &dy, SolveState *st,
     return cudaGetLastError();
 }
 
-// Allow the plane-streaming kernels of one model the shared memory they need.
+// Nothing to configure: the plane-streaming tiles stay below the default
+// 48 KB of dynamic shared memory.
 template <int ND, int DYN>
 cudaError_t configure_stage_t()
 {
-    if constexpr (ND >= 3) {
-        const int bytes = 227 * 1024;
-        cudaError_t e = cudaFuncSetAttribute(k_stage_plane<ND, 1, DYN>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (e != cudaSuccess) return e;
-        return cudaFuncSetAttribute(k_stage_plane<ND, 2, DYN>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    }
     return cudaSuccess;
 }
 

@@ -140,34 +140,46 @@ static void plane_geometry(GridDesc &D, int sms)
 {
     PlaneGeom &pg = D.pg;
     pg = PlaneGeom{};
-    if (D.ndim < 3) return;
-    pg.plane = D.nr * D.n_pad;
-    pg.cp = D.n_pad + 8;
-    const int nout = D.ndim - 3;
-    (void)nout;
-    for (int o = 1; o <= 2; ++o) {
-        const long long bytes = (long long)(2 * o + 2) * pg.plane * 4 + (long long)(D.nr + 2 * o) * pg.cp * 4 + 16;
-        pg.smem[o - 1] = bytes <= 200 * 1024 ? int(bytes) : 0;
+    const int nr = D.nr, segs = D.segs;
+    if (D.ndim < 3 || nr < 4 || segs > 128) return;
+    // bands of about 256 threads, at least 4 rows each (radius-2 halos come
+    // from one thread per row)
+    int rb = 256 / segs;
+    if (rb < 4) rb = 4;
+    int nb = 1;
+    if (rb >= nr) {
+        rb = nr;
+    } else {
+        nb = (nr + rb - 1) / rb;
+        rb = (nr + nb - 1) / nb;
+        while (nb > 1 && nr - (nb - 1) * rb < 4) {
+            --nb;
+            rb = (nr + nb - 1) / nb;
+        }
     }
-    if (pg.smem[0] == 0 && pg.smem[1] == 0) return;
+    const int threads = (rb * segs + 31) / 32 * 32;
+    if (threads > 512) return;
+    pg.rb = rb;
+    pg.nbands = nb;
+    pg.threads = threads;
+    pg.plane = nr * D.n_pad;
+    pg.cp = D.n_pad + 4;
+    for (int o = 1; o <= 2; ++o) pg.smem[o - 1] = 2 * (4 + (rb + 2 * o) * pg.cp) * 4;
     pg.ns = D.n[D.ndim - 3];
     long long pencils = 1;
     for (int d = 0; d < D.ndim - 3; ++d) pencils *= D.n[d];
-    if (pg.ns < 1 || pencils < 1 || pg.plane < 4) {
-        pg = PlaneGeom{};
-        return;
-    }
-    const long long target = 4LL * sms;
-    long long chunk = (pencils * pg.ns + target - 1) / target;
-    if (chunk < 1) chunk = 1;
+    // chunks of the stream axis: about twelve CTAs per SM per launch
+    const long long base = pencils * nb;
+    const long long target = 12LL * sms;
+    long long chunk = (base * pg.ns + target - 1) / target;
+    const int cmin = pg.ns < 4 ? pg.ns : 4;
+    if (chunk < cmin) chunk = cmin;
     if (chunk > pg.ns) chunk = pg.ns;
     pg.chunk = int(chunk);
     pg.nchunks = (pg.ns + pg.chunk - 1) / pg.chunk;
-    pg.items = int(pencils * pg.nchunks);
+    pg.items = int(base * pg.nchunks);
     pg.div_nchunks = make_fastdiv(uint32_t(pg.nchunks));
-    const int work = D.nr * D.segs;
-    int th = (work + 31) / 32 * 32;
-    pg.threads = th < 64 ? 64 : (th > 256 ? 256 : th);
+    pg.div_nbands = make_fastdiv(uint32_t(pg.nbands));
     pg.use = 1;
 }
 
@@ -199,7 +211,7 @@ extern "C" int64_t odp_grid_points(const odp_grid *g) { return g ? g->total : 0;
 
 extern "C" odp_status odp_plan_geometry(int ndim, const int32_t *n, int64_t *out, int n_out)
 {
-    if (ndim < 1 || ndim > ODP_MAXD || !n || !out || n_out < 12) return fail(ODP_EINVAL, "bad arguments");
+    if (ndim < 1 || ndim > ODP_MAXD || !n || !out || n_out < 14) return fail(ODP_EINVAL, "bad arguments");
     GridDesc D{};
     D.ndim = ndim;
     int64_t total = 1;
@@ -218,9 +230,9 @@ extern "C" odp_status odp_plan_geometry(int ndim, const int32_t *n, int64_t *out
     D.nthreads_rb = D.segs * D.row_groups * D.planes;
     plane_geometry(D, 152);
     const PlaneGeom &pg = D.pg;
-    const int64_t v[12] = {D.n_pad, D.R, D.row_groups, D.planes, D.nthreads_rb, pg.use, pg.ns,
-                           pg.chunk, pg.items, pg.threads, pg.smem[0], pg.smem[1]};
-    for (int k = 0; k < 12; ++k) out[k] = v[k];
+    const int64_t v[14] = {D.n_pad, D.R, D.row_groups, D.planes, D.nthreads_rb, pg.use, pg.ns,
+                           pg.chunk, pg.items, pg.threads, pg.smem[0], pg.smem[1], pg.rb, pg.nbands};
+    for (int k = 0; k < 14; ++k) out[k] = v[k];
     return ODP_OK;
 }
 
@@ -240,6 +252,10 @@ extern "C" odp_status odp_grid_create(int ndim, const int32_t *n, const double *
         total *= n[d];
         if (total >= (int64_t(1) << 31)) return fail(ODP_EINVAL, "grid has 2^31 nodes or more");
     }
+    // the kernels index the padded storage (last axis rounded up to a
+    // multiple of 4) with 32-bit offsets
+    if (total / n[ndim - 1] * ((n[ndim - 1] + 3) / 4 * 4) >= (int64_t(1) << 31))
+        return fail(ODP_EINVAL, "padded grid storage has 2^31 floats or more");
     odp_grid *g = new (std::nothrow) odp_grid();
     if (!g) return fail(ODP_ENOMEM, "host allocation failed");
     g->ndim = ndim;

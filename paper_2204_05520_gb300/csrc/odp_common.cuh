@@ -96,17 +96,21 @@ ODP_HD uint32_t fast_div(uint32_t n, const FastDiv &f)
 }
 
 // Geometry of the plane-streaming stage pass (hj_plane.cuh; host computed).
+// A CTA covers a band of rb rows of the plane (the last band may be shorter,
+// never below 4 rows) for a chunk of the stream axis at fixed outer indices.
 struct PlaneGeom {
     int use;           // 1: the grid runs the plane-streaming pass
     int ns;            // length of the stream axis (axis ndim-3)
-    int chunk;         // output planes per CTA
+    int chunk;         // stream-axis planes per CTA
     int nchunks;       // ceil(ns / chunk)
-    int items;         // outer pencils * nchunks (CTAs per launch)
+    int rb;            // rows per band
+    int nbands;        // ceil(nr / rb)
+    int items;         // outer pencils * nbands * nchunks (CTAs per launch)
     int plane;         // floats per plane: nr * n_pad
-    int cp;            // pitch of the halo-padded output plane: n_pad + 8
-    int threads;       // CTA size
-    int smem[2];       // dynamic shared memory bytes for stencil radius 1, 2
-    FastDiv div_nchunks;
+    int cp;            // tile row pitch: n_pad + 4
+    int threads;       // CTA size: rb * segs rounded up to a warp
+    int smem[2];       // dynamic shared bytes (two tiles) for stencil radius 1, 2
+    FastDiv div_nchunks, div_nbands;
 };
 
 // Storage: C order with the last axis padded to n_pad, a multiple of 4 nodes,

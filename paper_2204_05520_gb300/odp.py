@@ -356,15 +356,15 @@ def batch_set_autotune(enabled: bool):
 
 
 PLAN_FIELDS = ("n_pad", "rows_per_thread", "row_groups", "planes", "threads_rb", "plane_pass",
-               "stream_len", "chunk", "ctas", "cta_threads", "smem_r1", "smem_r2")
+               "stream_len", "chunk", "ctas", "cta_threads", "smem_r1", "smem_r2", "band_rows", "bands")
 
 
 def plan_geometry(n) -> dict:
     """Launch geometry for a grid of shape n (host only)."""
     nd = len(n)
     n_a = (ctypes.c_int32 * nd)(*[int(v) for v in n])
-    out = (ctypes.c_int64 * 12)()
-    _check(load().odp_plan_geometry(nd, n_a, out, 12), "odp_plan_geometry")
+    out = (ctypes.c_int64 * len(PLAN_FIELDS))()
+    _check(load().odp_plan_geometry(nd, n_a, out, len(PLAN_FIELDS)), "odp_plan_geometry")
     return dict(zip(PLAN_FIELDS, list(out)))
 
 

@@ -60,7 +60,8 @@ def test_argument_errors_need_no_gpu(lib):
 
 
 @pytest.mark.parametrize("n", [(41, 41, 36), (80, 80, 40, 64), (24,) * 6, (37,), (13, 11),
-                               (101, 101, 64), (31, 31, 37), (2, 2, 5), (3, 4, 3, 3, 2, 4)])
+                               (101, 101, 64), (31, 31, 37), (2, 2, 5), (3, 4, 3, 3, 2, 4),
+                               (4, 13, 200), (6, 101, 64), (5, 3, 40)])
 def test_launch_geometry_covers_the_grid(lib, n):
     g = odp.plan_geometry(n)
     nl = n[-1]
@@ -71,8 +72,11 @@ def test_launch_geometry_covers_the_grid(lib, n):
     if len(n) >= 3 and g["plane_pass"]:
         ns = n[-3]
         pencils = int(np.prod(n[:-3])) if len(n) > 3 else 1
+        segs = g["n_pad"] // 4
+        rb, nb = g["band_rows"], g["bands"]
         assert 1 <= g["chunk"] <= ns
-        assert g["ctas"] == pencils * -(-ns // g["chunk"])
-        assert 64 <= g["cta_threads"] <= 256 and g["cta_threads"] % 32 == 0
-        assert 0 < g["smem_r1"] <= g["smem_r2"] or g["smem_r2"] == 0
-        assert g["smem_r1"] <= 200 * 1024
+        # bands cover the rows; every band (the last one too) has 4 rows or more
+        assert rb * nb >= nr and rb * (nb - 1) < nr and nr - rb * (nb - 1) >= 4
+        assert g["ctas"] == pencils * nb * -(-ns // g["chunk"])
+        assert g["cta_threads"] == -(-rb * segs // 32) * 32 and g["cta_threads"] <= 512
+        assert 0 < g["smem_r1"] < g["smem_r2"] <= 48 * 1024
