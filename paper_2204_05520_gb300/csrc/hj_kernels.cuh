@@ -206,6 +206,35 @@ ODP_HD bool update_segment(float dt_, int stage, bool use_l, const float4 &c4, c
     return bad;
 }
 
+// The same update without a per-node finite test: x - x of every valid
+// updated node (0 when finite, NaN otherwise) is added to fin instead.
+ODP_HD float4 update_nodes(float dt_, int stage, bool use_l, const float4 &c4, const float *L, const float4 &b4,
+                           const float4 &l4, int nvalid, float2 &fin)
+{
+    const float2 dt = f2splat(dt_);
+    float2 v01 = f2fma(dt, make_float2(L[0], L[1]), make_float2(c4.x, c4.y));
+    float2 v23 = f2fma(dt, make_float2(L[2], L[3]), make_float2(c4.z, c4.w));
+    if (stage == 2) {
+        v01 = f2mul(f2splat(0.5f), f2add(make_float2(b4.x, b4.y), v01));
+        v23 = f2mul(f2splat(0.5f), f2add(make_float2(b4.z, b4.w), v23));
+    }
+    float2 z01 = f2sub(v01, v01), z23 = f2sub(v23, v23);
+    if (nvalid < 4) {
+        if (nvalid < 4) z23.y = 0.0f;
+        if (nvalid < 3) z23.x = 0.0f;
+        if (nvalid < 2) z01.y = 0.0f;
+    }
+    fin = f2add(fin, f2add(z01, z23));
+    float4 out = make_float4(v01.x, v01.y, v23.x, v23.y);
+    if (use_l) {
+        out.x = fminf(out.x, l4.x);
+        out.y = fminf(out.y, l4.y);
+        out.z = fminf(out.z, l4.z);
+        out.w = fminf(out.w, l4.w);
+    }
+    return out;
+}
+
 // update_segment with phi^n and l read at storage offset base.
 ODP_HD bool stage_epilogue(const StageArgs &A, int base, const float4 &c4, const float *L, int nvalid, float4 &out)
 {
@@ -474,10 +503,19 @@ cudaError_t launch_stage_t(const GridDesc &g, const DynDesc &dy, SolveState *st,
 {
     if constexpr (ND >= 3) {
         if (g.pg.use) {
-            if (order == 1)
-                k_stage_plane<ND, 1, DYN><<<g.pg.items, g.pg.threads, g.pg.smem[0], s>>>(g, dy, st, l, stage, brt);
-            else
-                k_stage_plane<ND, 2, DYN><<<g.pg.items, g.pg.threads, g.pg.smem[1], s>>>(g, dy, st, l, stage, brt);
+            const int blocks = g.pg.items, th = g.pg.threads, sm = g.pg.smem[order - 1];
+            const bool full = g.n[ND - 1] % 4 == 0;
+            if (order == 1) {
+                if (full)
+                    k_stage_plane<ND, 1, DYN, true><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
+                else
+                    k_stage_plane<ND, 1, DYN, false><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
+            } else {
+                if (full)
+                    k_stage_plane<ND, 2, DYN, true><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
+                else
+                    k_stage_plane<ND, 2, DYN, false><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
+            }
             return cudaGetLastError();
         }
     }

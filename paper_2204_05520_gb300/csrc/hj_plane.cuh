@@ -19,6 +19,8 @@
 // indices for Dubins3D and DubinsCar4D, so they are computed once per thread.
 #pragma once
 
+#include <type_traits>
+
 #include "hj_kernels.cuh"
 
 namespace odp {
@@ -58,9 +60,28 @@ __device__ __forceinline__ float4 stream_value(const float *__restrict__ src, in
                        keep_sign_ghost(pb.z, pi.z, k), keep_sign_ghost(pb.w, pi.w, k));
 }
 
+// The k-th ghost row outside boundary row pb with inner row pi, lane by lane
+// (Section 3.1.1).
+__device__ __forceinline__ float4 ghost4(const float4 &pb, const float4 &pi, float k)
+{
+    return make_float4(keep_sign_ghost(pb.x, pi.x, k), keep_sign_ghost(pb.y, pi.y, k),
+                       keep_sign_ghost(pb.z, pi.z, k), keep_sign_ghost(pb.w, pi.w, k));
+}
+
 // One plane-streaming stage pass.  ND >= 3.  The launch geometry (bands,
-// chunks, threads, shared bytes) is PlaneGeom, computed on the host.
-template <int ND, int ORDER, int DYN>
+// chunks, threads, shared bytes) is PlaneGeom, computed on the host.  FULL:
+// the last axis is a multiple of 4 nodes (no partial segment).
+//
+// Halo rows of a band: rows of the neighbouring band (or wrapped rows of a
+// periodic row axis) are loaded one plane ahead by the band's edge threads;
+// ghost rows outside a non-periodic row axis are formed by the threads that
+// use them, from their own column of the tile.  Halo columns (FULL): a
+// periodic last axis is read at the wrapped columns of the tile row, ghost
+// columns are formed from the segment's own values; otherwise the row's
+// first and last segments write them into the tile one plane ahead.
+// Non-finite values are detected by accumulating x - x over the updated nodes
+// (0 for finite x, NaN otherwise) and testing the sum once at the end.
+template <int ND, int ORDER, int DYN, bool FULL>
 __global__ void __launch_bounds__(512) k_stage_plane(GridDesc g, DynDesc dy, SolveState *st,
                                                      const float *__restrict__ l, int stage, int brt)
 {
@@ -106,6 +127,7 @@ __global__ void __launch_bounds__(512) k_stage_plane(GridDesc g, DynDesc dy, Sol
     const int nr = g.nr, npad = g.n_pad, nl = g.n[ND - 1];
     const int band_lo = band * pg.rb;
     const int band_rows = min(pg.rb, nr - band_lo);
+    const int per_r = g.periodic[ND - 2], per_l = g.periodic[ND - 1], per_s = g.periodic[sa];
 
     // this thread's segment: row band_lo + j, nodes s0 .. s0+3
     const int j = int(fast_div(uint32_t(tid), g.div_segs));
@@ -114,18 +136,44 @@ __global__ void __launch_bounds__(512) k_stage_plane(GridDesc g, DynDesc dy, Sol
     const int r = band_lo + (active ? j : 0);
     const int base = int(outer) * ns * plane + r * npad + s0;   // offset on stream plane 0
     const int so = 4 + (O + j) * cp + s0;                       // offset in a tile
-    const int nvalid = min(4, nl - s0);
-    // halo duties: a band edge row writes one halo row; a row's first and
-    // last segments write its halo columns
-    const bool hrow_duty = active && (j < O || j >= band_rows - O);
-    const int hrow = (j < O) ? band_lo - O + j : band_lo + band_rows + (j - (band_rows - O));
-    const int hso = 4 + (O + hrow - band_lo) * cp + s0;
-    const bool lcol = active && s0 == 0;
-    const bool rcol = active && s0 + 4 >= nl;
-    const int per_r = g.periodic[ND - 2], per_l = g.periodic[ND - 1], per_s = g.periodic[sa];
+    const int nvalid = FULL ? 4 : min(4, nl - s0);
+
+    // halo-row duty: a band edge row loads the neighbouring band's row (or the
+    // wrapped row) into the tile's halo rows; ghost rows have no loader
+    bool hrow_duty = false;
+    int hdelta = 0, hso = 0;
+    if (active && (j < O || j >= band_rows - O)) {
+        const int hrow = (j < O) ? band_lo - O + j : band_lo + band_rows + (j - (band_rows - O));
+        int q = hrow;
+        if (per_r) q = (q < 0) ? q + nr : (q >= nr ? q - nr : q);
+        if (q >= 0 && q < nr) {
+            hrow_duty = true;
+            hdelta = (q - r) * npad;
+            hso = 4 + (O + hrow - band_lo) * cp + s0;
+        }
+    }
+    // ghost rows this thread forms: 1 on the boundary row, 2 on the next one
+    const int gtop = (!per_r && r < O) ? r + 1 : 0;
+    const int gbot = (!per_r && r >= nr - O) ? nr - r : 0;
+    // halo columns
+    int lh_off = -2, rh_off = 4;   // relative to the segment's first node in the tile
+    bool lghost = false, rghost = false, lcol = false, rcol = false;
+    if (FULL) {
+        if (per_l) {
+            if (s0 == 0) lh_off = nl - 2;
+            if (s0 + 4 == nl) rh_off = 4 - nl;
+        } else {
+            lghost = s0 == 0;
+            rghost = s0 + 4 == nl;
+        }
+    } else {
+        lcol = active && s0 == 0;
+        rcol = active && s0 + 4 >= nl;
+    }
 
     // neighbours along the outer axes (same offsets for every plane)
     NbPlane nbq[NOUT > 0 ? NOUT : 1][2 * O];
+    bool inner = true;
 #pragma unroll
     for (int d = 0; d < NOUT; ++d) {
         int k = 0;
@@ -147,6 +195,7 @@ __global__ void __launch_bounds__(512) k_stage_plane(GridDesc g, DynDesc dy, Sol
                 q.k = jd < 0 ? float(-jd) : float(jd - (g.n[d] - 1));
                 q.db = (b - idx[d]) * sd;
                 q.di = (in - idx[d]) * sd;
+                inner = false;
             }
             nbq[d][k++] = q;
         }
@@ -159,17 +208,21 @@ __global__ void __launch_bounds__(512) k_stage_plane(GridDesc g, DynDesc dy, Sol
     idx[ND - 1] = s0;
     drift<DYN, ND>(g, dy, idx, cA, cS);
 
-    // halo values of plane p for this thread's duties
+    // halo values of plane p for this thread's duties (loaded one plane ahead)
     float4 hx = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 hl = make_float2(0.f, 0.f), hr = make_float2(0.f, 0.f);
     auto load_halos = [&](int p) {
         const int pb = base + p * plane;
-        if (hrow_duty) hx = axis_row(src, pb, r, hrow, npad, nr, per_r);
-        const float *rowg = src + pb - s0;
-        if (lcol) hl = make_float2(last_axis_value(rowg, -2, nl, per_l), last_axis_value(rowg, -1, nl, per_l));
-        if (rcol) hr = make_float2(last_axis_value(rowg, nl, nl, per_l), last_axis_value(rowg, nl + 1, nl, per_l));
+        if (hrow_duty) hx = ldg4(src + pb + hdelta);
+        if (!FULL) {
+            const float *rowg = src + pb - s0;
+            if (lcol) hl = make_float2(last_axis_value(rowg, -2, nl, per_l), last_axis_value(rowg, -1, nl, per_l));
+            if (rcol)
+                hr = make_float2(last_axis_value(rowg, nl, nl, per_l), last_axis_value(rowg, nl + 1, nl, per_l));
+        }
     };
 
+    // stream-axis window: w[(m + i) % Q] holds plane s - O + i at step m = s - s_begin
     float4 w[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) w[k] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -179,93 +232,124 @@ __global__ void __launch_bounds__(512) k_stage_plane(GridDesc g, DynDesc dy, Sol
         load_halos(s_begin);
     }
 
-    bool bad = false;
-    for (int s = s_begin; s < s_end; ++s) {
-        float *T = smem + (((s - s_begin) & 1) ? tile : 0);
-        const int gi = base + s * plane;
-        float4 nb[NOUT > 0 ? NOUT : 1][2 * O];
-        float4 lx = make_float4(0.f, 0.f, 0.f, 0.f), px = lx, nx = lx;
-        if (active) {
-            *reinterpret_cast<float4 *>(T + so) = w[O];
-            if (hrow_duty) *reinterpret_cast<float4 *>(T + hso) = hx;
-            if (lcol) {
-                T[so - 2] = hl.x;
-                T[so - 1] = hl.y;
-            }
-            if (rcol) {
-                T[so - s0 + nl] = hr.x;
-                T[so - s0 + nl + 1] = hr.y;
-            }
-            // loads for this plane's update and for the next plane
+    float2 fin = make_float2(0.f, 0.f);   // sum of x - x over the updated nodes
+    auto run = [&](auto inner_tag) {
+        constexpr bool INNER = decltype(inner_tag)::value;
+        for (int s0p = s_begin; s0p < s_end; s0p += Q) {
 #pragma unroll
-            for (int d = 0; d < NOUT; ++d)
+            for (int u = 0; u < Q; ++u) {
+                const int s = s0p + u;
+                if (s >= s_end) break;
+                float *T = smem + (((s - s_begin) & 1) ? tile : 0);
+                const int gi = base + s * plane;
+                const float4 c4 = w[(u + O) % Q];
+                float4 nb[NOUT > 0 ? NOUT : 1][2 * O];
+                float4 lx = make_float4(0.f, 0.f, 0.f, 0.f), px = lx, nx = lx;
+                if (active) {
+                    *reinterpret_cast<float4 *>(T + so) = c4;
+                    if (hrow_duty) *reinterpret_cast<float4 *>(T + hso) = hx;
+                    if (!FULL) {
+                        if (lcol) {
+                            T[so - 2] = hl.x;
+                            T[so - 1] = hl.y;
+                        }
+                        if (rcol) {
+                            T[so - s0 + nl] = hr.x;
+                            T[so - s0 + nl + 1] = hr.y;
+                        }
+                    }
+                    // loads for this plane's update and for the next plane
 #pragma unroll
-                for (int k = 0; k < 2 * O; ++k) nb[d][k] = nb_value(src, gi, nbq[d][k]);
-            if (use_l) lx = ldg4(l + gi);
-            if (stage == 2) px = *reinterpret_cast<const float4 *>(prev + gi);
-            if (s + 1 < s_end) {
-                nx = stream_value(src, base, s + 1 + O, ns, per_s, plane);
-                load_halos(s + 1);
-            }
-        }
-        __syncthreads();
-
-        if (active) {
-            if (DYN == DYN_REL6D && s != s_begin) {   // the x drift depends on v_p (the stream axis)
-                idx[sa] = s;
-                drift<DYN, ND>(g, dy, idx, cA, cS);
-            }
-            const float *C = T + so;
-            const float4 c4 = w[O];
-            float2 L01 = make_float2(0.0f, 0.0f), L23 = make_float2(0.0f, 0.0f);
-            // outer axes
+                    for (int d = 0; d < NOUT; ++d)
 #pragma unroll
-            for (int d = 0; d < NOUT; ++d)
-                segment_axis<ORDER>(nb[d][0], nb[d][O - 1], c4, nb[d][O], nb[d][2 * O - 1], cA[d], cS[d], cD[d], L01,
-                                    L23, has_drift<DYN, ND>(d), has_bound<DYN, ND>(d));
-            // stream axis from the register window
-            segment_axis<ORDER>(w[O == 2 ? 0 : O - 1], w[O - 1], c4, w[O + 1], w[O == 2 ? Q - 1 : O + 1], cA[sa],
-                                cS[sa], cD[sa], L01, L23, has_drift<DYN, ND>(sa), has_bound<DYN, ND>(sa));
-            // row axis from the tile
-            {
-                const float4 m1 = *reinterpret_cast<const float4 *>(C - cp);
-                const float4 p1 = *reinterpret_cast<const float4 *>(C + cp);
-                const float4 m2 = (O == 2) ? *reinterpret_cast<const float4 *>(C - 2 * cp) : m1;
-                const float4 p2 = (O == 2) ? *reinterpret_cast<const float4 *>(C + 2 * cp) : p1;
-                segment_axis<ORDER>(m2, m1, c4, p1, p2, cA[ND - 2], cS[ND - 2], cD[ND - 2], L01, L23,
-                                    has_drift<DYN, ND>(ND - 2), has_bound<DYN, ND>(ND - 2));
-            }
-            // last axis: window v[k] = phi(s0 - 2 + k); halo columns are in the tile
-            float L[4] = {L01.x, L01.y, L23.x, L23.y};
-            {
-                const float2 lh = *reinterpret_cast<const float2 *>(C - 2);
-                const float2 rh = *reinterpret_cast<const float2 *>(C + 4);
-                float v[8] = {lh.x, lh.y, c4.x, c4.y, c4.z, c4.w, rh.x, rh.y};
-                if (s0 + 4 > nl) {   // partial last segment: the window continues with the halo columns
-#pragma unroll
-                    for (int k = 2; k < 8; ++k)
-                        if (s0 + k - 2 >= nl) v[k] = C[k - 2];
+                        for (int k = 0; k < 2 * O; ++k)
+                            nb[d][k] = INNER ? ldg4(src + gi + nbq[d][k].delta) : nb_value(src, gi, nbq[d][k]);
+                    if (use_l) lx = ldg4(l + gi);
+                    if (stage == 2) px = *reinterpret_cast<const float4 *>(prev + gi);
+                    if (s + 1 < s_end) {
+                        nx = stream_value(src, base, s + 1 + O, ns, per_s, plane);
+                        load_halos(s + 1);
+                    }
                 }
-                axis_last<ORDER>(v, cA[ND - 1], cS[ND - 1], cD[ND - 1], L, has_drift<DYN, ND>(ND - 1),
-                                 has_bound<DYN, ND>(ND - 1));
-            }
-            float4 out;
-            bad = update_segment(dt, stage, use_l, c4, L, px, lx, nvalid, out) || bad;
-            if (nvalid == 4) {
-                *reinterpret_cast<float4 *>(dst + gi) = out;
-            } else {
-                const float o4[4] = {out.x, out.y, out.z, out.w};
+                __syncthreads();
+
+                if (active) {
+                    if (DYN == DYN_REL6D && s != s_begin) {   // the x drift depends on v_p (the stream axis)
+                        idx[sa] = s;
+                        drift<DYN, ND>(g, dy, idx, cA, cS);
+                    }
+                    const float *C = T + so;
+                    float2 L01 = make_float2(0.0f, 0.0f), L23 = make_float2(0.0f, 0.0f);
+                    // outer axes
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (k < nvalid) dst[gi + k] = o4[k];
+                    for (int d = 0; d < NOUT; ++d)
+                        segment_axis<ORDER>(nb[d][0], nb[d][O - 1], c4, nb[d][O], nb[d][2 * O - 1], cA[d], cS[d],
+                                            cD[d], L01, L23, has_drift<DYN, ND>(d), has_bound<DYN, ND>(d));
+                    // stream axis from the register window
+                    segment_axis<ORDER>(w[u % Q], w[(u + O - 1) % Q], c4, w[(u + O + 1) % Q], w[(u + Q - 1) % Q],
+                                        cA[sa], cS[sa], cD[sa], L01, L23, has_drift<DYN, ND>(sa),
+                                        has_bound<DYN, ND>(sa));
+                    // row axis from the tile; ghost rows from this column
+                    {
+                        float4 m1 = *reinterpret_cast<const float4 *>(C - cp);
+                        float4 p1 = *reinterpret_cast<const float4 *>(C + cp);
+                        float4 m2 = (O == 2) ? *reinterpret_cast<const float4 *>(C - 2 * cp) : m1;
+                        float4 p2 = (O == 2) ? *reinterpret_cast<const float4 *>(C + 2 * cp) : p1;
+                        if (gtop == 1) {
+                            m1 = ghost4(c4, p1, 1.0f);
+                            m2 = (O == 2) ? ghost4(c4, p1, 2.0f) : m1;
+                        } else if (gtop == 2) {
+                            m2 = ghost4(m1, c4, 1.0f);
+                        }
+                        if (gbot == 1) {
+                            p1 = ghost4(c4, m1, 1.0f);
+                            p2 = (O == 2) ? ghost4(c4, m1, 2.0f) : p1;
+                        } else if (gbot == 2) {
+                            p2 = ghost4(p1, c4, 1.0f);
+                        }
+                        segment_axis<ORDER>(m2, m1, c4, p1, p2, cA[ND - 2], cS[ND - 2], cD[ND - 2], L01, L23,
+                                            has_drift<DYN, ND>(ND - 2), has_bound<DYN, ND>(ND - 2));
+                    }
+                    // last axis: window v[k] = phi(s0 - 2 + k)
+                    float L[4] = {L01.x, L01.y, L23.x, L23.y};
+                    {
+                        float2 lh = *reinterpret_cast<const float2 *>(C + lh_off);
+                        float2 rh = *reinterpret_cast<const float2 *>(C + rh_off);
+                        if (FULL) {
+                            if (lghost)
+                                lh = make_float2(keep_sign_ghost(c4.x, c4.y, 2.0f), keep_sign_ghost(c4.x, c4.y, 1.0f));
+                            if (rghost)
+                                rh = make_float2(keep_sign_ghost(c4.w, c4.z, 1.0f), keep_sign_ghost(c4.w, c4.z, 2.0f));
+                        }
+                        float v[8] = {lh.x, lh.y, c4.x, c4.y, c4.z, c4.w, rh.x, rh.y};
+                        if (!FULL && s0 + 4 > nl) {   // partial last segment: the halo columns follow node nl-1
+#pragma unroll
+                            for (int k = 2; k < 8; ++k)
+                                if (s0 + k - 2 >= nl) v[k] = C[k - 2];
+                        }
+                        axis_last<ORDER>(v, cA[ND - 1], cS[ND - 1], cD[ND - 1], L, has_drift<DYN, ND>(ND - 1),
+                                         has_bound<DYN, ND>(ND - 1));
+                    }
+                    float4 out = update_nodes(dt, stage, use_l, c4, L, px, lx, nvalid, fin);
+                    if (FULL || nvalid == 4) {
+                        *reinterpret_cast<float4 *>(dst + gi) = out;
+                    } else {
+                        const float o4[4] = {out.x, out.y, out.z, out.w};
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if (k < nvalid) dst[gi + k] = o4[k];
+                    }
+                }
+                // plane s - O leaves the window, plane s + O + 1 takes its slot
+                w[u % Q] = nx;
             }
         }
-        // advance the stream-axis window
-#pragma unroll
-        for (int k = 0; k < Q - 1; ++k) w[k] = w[k + 1];
-        w[Q - 1] = nx;
-    }
-    if (bad) atomicOr(&st->flags, FLAG_NONFINITE);
+    };
+    if (inner)
+        run(std::true_type{});
+    else
+        run(std::false_type{});
+    if (!(fin.x == 0.0f && fin.y == 0.0f)) atomicOr(&st->flags, FLAG_NONFINITE);
 }
 
 }  // namespace odp
