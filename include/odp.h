@@ -151,6 +151,15 @@ odp_status odp_set_target(odp_grid *g, const float *l, int64_t n_elems, int on_d
  * solve that reaches the limit stops and reports ODP_ETIMEOUT. */
 odp_status odp_set_step_limit(odp_grid *g, int64_t max_steps);
 
+/* Choose how odp_solve_hjb runs the time loop (no paper counterpart):
+ * host_stepped = 0 (default) launches one CUDA graph whose device-side WHILE
+ * node runs every step; host_stepped = 1 launches the same kernels, in the
+ * same order, one step at a time from the host and reads the loop condition
+ * back after each step (one synchronisation per step).  Results are
+ * identical; the host-stepped loop exists for profilers and debuggers that do
+ * not follow kernels inside conditional graph nodes.  Errors: ODP_EINVAL. */
+odp_status odp_set_loop_mode(odp_grid *g, int host_stepped);
+
 /* Solve the HJ PDE (Algorithm 1) from tau[0] = 0 to tau[n_tau-1].
  *  tau          n_tau >= 2 strictly increasing look-back times (host), tau[0] = 0;
  *               each segment is integrated separately, the last CFL step of a

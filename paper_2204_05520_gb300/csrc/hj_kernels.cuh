@@ -444,33 +444,65 @@ __global__ void __launch_bounds__(256) k_alpha_static(GridDesc g, DynDesc dy, So
     }
 }
 
-// Rel6D heading-rate alpha of phi (slot 0: cur) or phi1 (slot 1: nxt), from
-// the p_th interval of every node; four nodes per thread, grid-stride.
+// A segment's value on plane p of an axis with n planes stride floats apart
+// (periodic wrap or sign-keeping ghost outside [0, n), Section 3.1.1); base
+// is the segment's offset on plane 0.
+__device__ __forceinline__ float4 stream_value(const float *__restrict__ src, int base, int p, int n, int periodic,
+                                               int stride)
+{
+    if (p >= 0 && p < n) return ldg4(src + base + p * stride);
+    if (periodic) {
+        while (p < 0) p += n;
+        while (p >= n) p -= n;
+        return ldg4(src + base + p * stride);
+    }
+    const int b = p < 0 ? 0 : n - 1, in = p < 0 ? 1 : n - 2;
+    const float k = p < 0 ? float(-p) : float(p - (n - 1));
+    const float4 pb = ldg4(src + base + b * stride), pi = ldg4(src + base + in * stride);
+    return make_float4(keep_sign_ghost(pb.x, pi.x, k), keep_sign_ghost(pb.y, pi.y, k),
+                       keep_sign_ghost(pb.z, pi.z, k), keep_sign_ghost(pb.w, pi.w, k));
+}
+
+// Rel6D heading-rate alpha of phi (slot 0: cur) or phi1 (slot 1: nxt): the
+// largest bound over the nodes of the heading rate given the interval of p_th
+// (Section 2.1 global alpha).  A thread owns one four-node segment of an
+// (x, y) block and walks the heading axis (axis 2) with the segment's values
+// in a register window, so every value is read once.
 template <int ORDER>
 __global__ void __launch_bounds__(256) k_alpha_rel6d(GridDesc g, DynDesc dy, SolveState *st, int slot)
 {
+    constexpr int O = ORDER, Q = 2 * O + 1;
     __shared__ float red[8];
     const float *__restrict__ src = slot ? st->nxt : st->cur;
+    const int nh = g.n[2], inner = g.stride[2];    // heading planes; floats per plane of an (x, y) block
+    const uint32_t isegs = uint32_t(inner / 4);
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     float amax = 0.0f;
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < uint32_t(g.nthreads);
-         t += gridDim.x * blockDim.x) {
-        int idx[6];
-        const int base = segment_index<6>(g, t, idx);
-        const float4 c4 = ldg4(src + base);
-        const float4 m1 = row_shift4(src, base, idx[2], g.stride[2], g.n[2], g.periodic[2], -1);
-        const float4 p1 = row_shift4(src, base, idx[2], g.stride[2], g.n[2], g.periodic[2], +1);
-        float4 m2 = m1, p2 = p1;
-        if (ORDER == 2) {
-            m2 = row_shift4(src, base, idx[2], g.stride[2], g.n[2], g.periodic[2], -2);
-            p2 = row_shift4(src, base, idx[2], g.stride[2], g.n[2], g.periodic[2], +2);
-        }
-        const float wp = ldgf(g.coord[4] + idx[4]);
-        const int nvalid = min(4, g.n[5] - idx[5]);
+    if (t < uint32_t(g.n[0] * g.n[1]) * isegs) {
+        const uint32_t o = t / isegs;               // (x, y) block
+        const int seg = int(t - o * isegs);
+        const int base = int(o) * nh * inner + seg * 4;
+        const uint32_t row = fast_div(uint32_t(seg), g.div_segs);   // (v_p, w_p) row of the block
+        const int s0 = (seg - int(row) * g.segs) * 4;
+        const int iwp = int(row - fast_div(row, g.div[4]) * uint32_t(g.n[4]));
+        const float wp = ldgf(g.coord[4] + iwp);
+        const int nvalid = min(4, g.n[5] - s0);
+        const int per = g.periodic[2];
+        float4 w[Q];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float dm, dp;
-            diffs<ORDER>(lane(m2, k), lane(m1, k), lane(c4, k), lane(p1, k), lane(p2, k), dm, dp);
-            if (k < nvalid) amax = fmaxf(amax, rel6d_theta_alpha(dy, wp, fminf(dm, dp), fmaxf(dm, dp)));
+        for (int k = 0; k < Q; ++k) w[k] = stream_value(src, base, k - O, nh, per, inner);
+        for (int h = 0; h < nh; ++h) {
+            const float4 nx = (h + 1 < nh) ? stream_value(src, base, h + 1 + O, nh, per, inner) : w[Q - 1];
+            const float4 m2 = w[0], m1 = w[O - 1], c4 = w[O], p1 = w[O + 1], p2 = w[Q - 1];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float dm, dp;
+                diffs<ORDER>(lane(m2, k), lane(m1, k), lane(c4, k), lane(p1, k), lane(p2, k), dm, dp);
+                if (k < nvalid) amax = fmaxf(amax, rel6d_theta_alpha(dy, wp, fminf(dm, dp), fmaxf(dm, dp)));
+            }
+#pragma unroll
+            for (int k = 0; k < Q - 1; ++k) w[k] = w[k + 1];
+            w[Q - 1] = nx;
         }
     }
     amax = warp_max(amax);
@@ -481,6 +513,13 @@ __global__ void __launch_bounds__(256) k_alpha_rel6d(GridDesc g, DynDesc dy, Sol
         for (int w = 0; w < (blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
         atomicMax(&st->alpha_bits[slot][2], __float_as_uint(m));
     }
+}
+
+// Threads of the Rel6D heading-rate alpha pass: one per four-node segment
+// of a heading plane of every (x, y) block.
+inline int64_t alpha_rel6d_threads(const GridDesc &g)
+{
+    return int64_t(g.n[0]) * g.n[1] * (g.stride[2] / 4);
 }
 
 inline int blocks_for(int64_t n, int threads) { return int((n + threads - 1) / threads); }

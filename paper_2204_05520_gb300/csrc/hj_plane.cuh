@@ -42,24 +42,6 @@ __device__ __forceinline__ float4 nb_value(const float *__restrict__ src, int gi
                        keep_sign_ghost(pb.z, pi.z, q.k), keep_sign_ghost(pb.w, pi.w, q.k));
 }
 
-// A segment's value on stream-axis plane p of its pencil (periodic wrap or
-// sign-keeping ghost outside [0, ns)); base is the segment's offset on plane 0.
-__device__ __forceinline__ float4 stream_value(const float *__restrict__ src, int base, int p, int ns, int periodic,
-                                               int plane)
-{
-    if (p >= 0 && p < ns) return ldg4(src + base + p * plane);
-    if (periodic) {
-        while (p < 0) p += ns;
-        while (p >= ns) p -= ns;
-        return ldg4(src + base + p * plane);
-    }
-    const int b = p < 0 ? 0 : ns - 1, in = p < 0 ? 1 : ns - 2;
-    const float k = p < 0 ? float(-p) : float(p - (ns - 1));
-    const float4 pb = ldg4(src + base + b * plane), pi = ldg4(src + base + in * plane);
-    return make_float4(keep_sign_ghost(pb.x, pi.x, k), keep_sign_ghost(pb.y, pi.y, k),
-                       keep_sign_ghost(pb.z, pi.z, k), keep_sign_ghost(pb.w, pi.w, k));
-}
-
 // The k-th ghost row outside boundary row pb with inner row pi, lane by lane
 // (Section 3.1.1).
 __device__ __forceinline__ float4 ghost4(const float4 &pb, const float4 &pi, float k)
@@ -233,115 +215,132 @@ __global__ void __launch_bounds__(512) k_stage_plane(GridDesc g, DynDesc dy, Sol
     }
 
     float2 fin = make_float2(0.f, 0.f);   // sum of x - x over the updated nodes
-    auto run = [&](auto inner_tag) {
+    // One plane: the window slot (u + i) % Q holds plane s - O + i; returns the
+    // segment's value on plane s + O + 1.
+    auto step = [&](int s, int u, auto inner_tag) -> float4 {
         constexpr bool INNER = decltype(inner_tag)::value;
-        for (int s0p = s_begin; s0p < s_end; s0p += Q) {
-#pragma unroll
-            for (int u = 0; u < Q; ++u) {
-                const int s = s0p + u;
-                if (s >= s_end) break;
-                float *T = smem + (((s - s_begin) & 1) ? tile : 0);
-                const int gi = base + s * plane;
-                const float4 c4 = w[(u + O) % Q];
-                float4 nb[NOUT > 0 ? NOUT : 1][2 * O];
-                float4 lx = make_float4(0.f, 0.f, 0.f, 0.f), px = lx, nx = lx;
-                if (active) {
-                    *reinterpret_cast<float4 *>(T + so) = c4;
-                    if (hrow_duty) *reinterpret_cast<float4 *>(T + hso) = hx;
-                    if (!FULL) {
-                        if (lcol) {
-                            T[so - 2] = hl.x;
-                            T[so - 1] = hl.y;
-                        }
-                        if (rcol) {
-                            T[so - s0 + nl] = hr.x;
-                            T[so - s0 + nl + 1] = hr.y;
-                        }
+            float *T = smem + (((s - s_begin) & 1) ? tile : 0);
+            const int gi = base + s * plane;
+            const float4 c4 = w[(u + O) % Q];
+            float4 nb[NOUT > 0 ? NOUT : 1][2 * O];
+            float4 lx = make_float4(0.f, 0.f, 0.f, 0.f), px = lx, nx = lx;
+            if (active) {
+                *reinterpret_cast<float4 *>(T + so) = c4;
+                if (hrow_duty) *reinterpret_cast<float4 *>(T + hso) = hx;
+                if (!FULL) {
+                    if (lcol) {
+                        T[so - 2] = hl.x;
+                        T[so - 1] = hl.y;
                     }
-                    // loads for this plane's update and for the next plane
-#pragma unroll
-                    for (int d = 0; d < NOUT; ++d)
-#pragma unroll
-                        for (int k = 0; k < 2 * O; ++k)
-                            nb[d][k] = INNER ? ldg4(src + gi + nbq[d][k].delta) : nb_value(src, gi, nbq[d][k]);
-                    if (use_l) lx = ldg4(l + gi);
-                    if (stage == 2) px = *reinterpret_cast<const float4 *>(prev + gi);
-                    if (s + 1 < s_end) {
-                        nx = stream_value(src, base, s + 1 + O, ns, per_s, plane);
-                        load_halos(s + 1);
+                    if (rcol) {
+                        T[so - s0 + nl] = hr.x;
+                        T[so - s0 + nl + 1] = hr.y;
                     }
                 }
-                __syncthreads();
+                // loads for this plane's update and for the next plane
+#pragma unroll
+                for (int d = 0; d < NOUT; ++d)
+#pragma unroll
+                    for (int k = 0; k < 2 * O; ++k)
+                        nb[d][k] = INNER ? ldg4(src + gi + nbq[d][k].delta) : nb_value(src, gi, nbq[d][k]);
+                if (use_l) lx = ldg4(l + gi);
+                if (stage == 2) px = *reinterpret_cast<const float4 *>(prev + gi);
+                if (s + 1 < s_end) {
+                    nx = stream_value(src, base, s + 1 + O, ns, per_s, plane);
+                    load_halos(s + 1);
+                }
+            }
+            __syncthreads();
 
-                if (active) {
-                    if (DYN == DYN_REL6D && s != s_begin) {   // the x drift depends on v_p (the stream axis)
-                        idx[sa] = s;
-                        drift<DYN, ND>(g, dy, idx, cA, cS);
-                    }
-                    const float *C = T + so;
-                    float2 L01 = make_float2(0.0f, 0.0f), L23 = make_float2(0.0f, 0.0f);
-                    // outer axes
-#pragma unroll
-                    for (int d = 0; d < NOUT; ++d)
-                        segment_axis<ORDER>(nb[d][0], nb[d][O - 1], c4, nb[d][O], nb[d][2 * O - 1], cA[d], cS[d],
-                                            cD[d], L01, L23, has_drift<DYN, ND>(d), has_bound<DYN, ND>(d));
-                    // stream axis from the register window
-                    segment_axis<ORDER>(w[u % Q], w[(u + O - 1) % Q], c4, w[(u + O + 1) % Q], w[(u + Q - 1) % Q],
-                                        cA[sa], cS[sa], cD[sa], L01, L23, has_drift<DYN, ND>(sa),
-                                        has_bound<DYN, ND>(sa));
-                    // row axis from the tile; ghost rows from this column
-                    {
-                        float4 m1 = *reinterpret_cast<const float4 *>(C - cp);
-                        float4 p1 = *reinterpret_cast<const float4 *>(C + cp);
-                        float4 m2 = (O == 2) ? *reinterpret_cast<const float4 *>(C - 2 * cp) : m1;
-                        float4 p2 = (O == 2) ? *reinterpret_cast<const float4 *>(C + 2 * cp) : p1;
-                        if (gtop == 1) {
-                            m1 = ghost4(c4, p1, 1.0f);
-                            m2 = (O == 2) ? ghost4(c4, p1, 2.0f) : m1;
-                        } else if (gtop == 2) {
-                            m2 = ghost4(m1, c4, 1.0f);
-                        }
-                        if (gbot == 1) {
-                            p1 = ghost4(c4, m1, 1.0f);
-                            p2 = (O == 2) ? ghost4(c4, m1, 2.0f) : p1;
-                        } else if (gbot == 2) {
-                            p2 = ghost4(p1, c4, 1.0f);
-                        }
-                        segment_axis<ORDER>(m2, m1, c4, p1, p2, cA[ND - 2], cS[ND - 2], cD[ND - 2], L01, L23,
-                                            has_drift<DYN, ND>(ND - 2), has_bound<DYN, ND>(ND - 2));
-                    }
-                    // last axis: window v[k] = phi(s0 - 2 + k)
-                    float L[4] = {L01.x, L01.y, L23.x, L23.y};
-                    {
-                        float2 lh = *reinterpret_cast<const float2 *>(C + lh_off);
-                        float2 rh = *reinterpret_cast<const float2 *>(C + rh_off);
-                        if (FULL) {
-                            if (lghost)
-                                lh = make_float2(keep_sign_ghost(c4.x, c4.y, 2.0f), keep_sign_ghost(c4.x, c4.y, 1.0f));
-                            if (rghost)
-                                rh = make_float2(keep_sign_ghost(c4.w, c4.z, 1.0f), keep_sign_ghost(c4.w, c4.z, 2.0f));
-                        }
-                        float v[8] = {lh.x, lh.y, c4.x, c4.y, c4.z, c4.w, rh.x, rh.y};
-                        if (!FULL && s0 + 4 > nl) {   // partial last segment: the halo columns follow node nl-1
-#pragma unroll
-                            for (int k = 2; k < 8; ++k)
-                                if (s0 + k - 2 >= nl) v[k] = C[k - 2];
-                        }
-                        axis_last<ORDER>(v, cA[ND - 1], cS[ND - 1], cD[ND - 1], L, has_drift<DYN, ND>(ND - 1),
-                                         has_bound<DYN, ND>(ND - 1));
-                    }
-                    float4 out = update_nodes(dt, stage, use_l, c4, L, px, lx, nvalid, fin);
-                    if (FULL || nvalid == 4) {
-                        *reinterpret_cast<float4 *>(dst + gi) = out;
-                    } else {
-                        const float o4[4] = {out.x, out.y, out.z, out.w};
-#pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            if (k < nvalid) dst[gi + k] = o4[k];
-                    }
+            if (active) {
+                if (DYN == DYN_REL6D && s != s_begin) {   // the x drift depends on v_p (the stream axis)
+                    idx[sa] = s;
+                    drift<DYN, ND>(g, dy, idx, cA, cS);
                 }
-                // plane s - O leaves the window, plane s + O + 1 takes its slot
-                w[u % Q] = nx;
+                const float *C = T + so;
+                float2 L01 = make_float2(0.0f, 0.0f), L23 = make_float2(0.0f, 0.0f);
+                // outer axes
+#pragma unroll
+                for (int d = 0; d < NOUT; ++d)
+                    segment_axis<ORDER>(nb[d][0], nb[d][O - 1], c4, nb[d][O], nb[d][2 * O - 1], cA[d], cS[d],
+                                        cD[d], L01, L23, has_drift<DYN, ND>(d), has_bound<DYN, ND>(d));
+                // stream axis from the register window
+                segment_axis<ORDER>(w[u % Q], w[(u + O - 1) % Q], c4, w[(u + O + 1) % Q], w[(u + Q - 1) % Q],
+                                    cA[sa], cS[sa], cD[sa], L01, L23, has_drift<DYN, ND>(sa),
+                                    has_bound<DYN, ND>(sa));
+                // row axis from the tile; ghost rows from this column
+                {
+                    float4 m1 = *reinterpret_cast<const float4 *>(C - cp);
+                    float4 p1 = *reinterpret_cast<const float4 *>(C + cp);
+                    float4 m2 = (O == 2) ? *reinterpret_cast<const float4 *>(C - 2 * cp) : m1;
+                    float4 p2 = (O == 2) ? *reinterpret_cast<const float4 *>(C + 2 * cp) : p1;
+                    if (gtop == 1) {
+                        m1 = ghost4(c4, p1, 1.0f);
+                        m2 = (O == 2) ? ghost4(c4, p1, 2.0f) : m1;
+                    } else if (gtop == 2) {
+                        m2 = ghost4(m1, c4, 1.0f);
+                    }
+                    if (gbot == 1) {
+                        p1 = ghost4(c4, m1, 1.0f);
+                        p2 = (O == 2) ? ghost4(c4, m1, 2.0f) : p1;
+                    } else if (gbot == 2) {
+                        p2 = ghost4(p1, c4, 1.0f);
+                    }
+                    segment_axis<ORDER>(m2, m1, c4, p1, p2, cA[ND - 2], cS[ND - 2], cD[ND - 2], L01, L23,
+                                        has_drift<DYN, ND>(ND - 2), has_bound<DYN, ND>(ND - 2));
+                }
+                // last axis: window v[k] = phi(s0 - 2 + k)
+                float L[4] = {L01.x, L01.y, L23.x, L23.y};
+                {
+                    float2 lh = *reinterpret_cast<const float2 *>(C + lh_off);
+                    float2 rh = *reinterpret_cast<const float2 *>(C + rh_off);
+                    if (FULL) {
+                        if (lghost)
+                            lh = make_float2(keep_sign_ghost(c4.x, c4.y, 2.0f), keep_sign_ghost(c4.x, c4.y, 1.0f));
+                        if (rghost)
+                            rh = make_float2(keep_sign_ghost(c4.w, c4.z, 1.0f), keep_sign_ghost(c4.w, c4.z, 2.0f));
+                    }
+                    float v[8] = {lh.x, lh.y, c4.x, c4.y, c4.z, c4.w, rh.x, rh.y};
+                    if (!FULL && s0 + 4 > nl) {   // partial last segment: the halo columns follow node nl-1
+#pragma unroll
+                        for (int k = 2; k < 8; ++k)
+                            if (s0 + k - 2 >= nl) v[k] = C[k - 2];
+                    }
+                    axis_last<ORDER>(v, cA[ND - 1], cS[ND - 1], cD[ND - 1], L, has_drift<DYN, ND>(ND - 1),
+                                     has_bound<DYN, ND>(ND - 1));
+                }
+                float4 out = update_nodes(dt, stage, use_l, c4, L, px, lx, nvalid, fin);
+                if (FULL || nvalid == 4) {
+                    *reinterpret_cast<float4 *>(dst + gi) = out;
+                } else {
+                    const float o4[4] = {out.x, out.y, out.z, out.w};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (k < nvalid) dst[gi + k] = o4[k];
+                }
+            }
+        return nx;
+    };
+    // CTAs with every outer neighbour inside the grid (most of them) run the
+    // loop unrolled by the window length, so the window is never shifted; the
+    // others shift it (smaller code: the two paths share the instruction cache)
+    auto run = [&](auto inner_tag) {
+        constexpr bool UNROLL = decltype(inner_tag)::value;
+        if (UNROLL) {
+            for (int s0p = s_begin; s0p < s_end; s0p += Q) {
+#pragma unroll
+                for (int u = 0; u < Q; ++u) {
+                    const int s = s0p + u;
+                    if (s >= s_end) break;
+                    w[u % Q] = step(s, u, inner_tag);
+                }
+            }
+        } else {
+            for (int s = s_begin; s < s_end; ++s) {
+                const float4 nx = step(s, 0, inner_tag);
+#pragma unroll
+                for (int k = 0; k < Q - 1; ++k) w[k] = w[k + 1];
+                w[Q - 1] = nx;
             }
         }
     };

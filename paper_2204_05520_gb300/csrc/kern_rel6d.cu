@@ -21,7 +21,7 @@ cudaError_t launch_alpha_static_rel6d(const GridDesc &g, const DynDesc &dy, Solv
 cudaError_t launch_alpha_dynamic_rel6d(const GridDesc &g, const DynDesc &dy, SolveState *st,
                                        int order, int slot, cudaStream_t s)
 {
-    const int blocks = reduce_blocks(g.total);
+    const int blocks = blocks_for(alpha_rel6d_threads(g), 256);
     if (order == 1)
         k_alpha_rel6d<1><<<blocks, 256, 0, s>>>(g, dy, st, slot);
     else

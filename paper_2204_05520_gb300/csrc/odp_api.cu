@@ -74,7 +74,7 @@ __global__ void k_dt(SolveState *st, GridDesc g)
 // clear the phi-dependent alpha components, move to the next tau segment
 // when this one is done, and set the loop and snapshot conditions.
 __global__ void k_advance(SolveState *st, int swap, unsigned dyn_mask, cudaGraphConditionalHandle h_loop,
-                          cudaGraphConditionalHandle h_snap, int keep)
+                          cudaGraphConditionalHandle h_snap, int keep, int in_graph)
 {
     for (int d = 0; d < 8; ++d) st->alpha_last[d] = st->alpha_bits[swap ? 0 : 1][d];
     st->t = after_step(st->t, st->dt, st->t_end, st->last);
@@ -104,8 +104,12 @@ __global__ void k_advance(SolveState *st, int swap, unsigned dyn_mask, cudaGraph
         st->flags |= FLAG_TIMEOUT;
         go = 0;
     }
-    cudaGraphSetConditional(h_loop, go);
-    if (keep) cudaGraphSetConditional(h_snap, snap);
+    st->go = go;
+    st->snap_now = snap;
+    if (in_graph) {
+        cudaGraphSetConditional(h_loop, go);
+        if (keep) cudaGraphSetConditional(h_snap, snap);
+    }
 }
 
 __global__ void k_snapshot(SolveState *st, int total)
@@ -453,20 +457,66 @@ extern "C" odp_status odp_set_step_limit(odp_grid *g, int64_t max_steps)
 // ---------------------------------------------------------------------------
 // the time-loop graph
 // ---------------------------------------------------------------------------
-static cudaError_t launch_stage_any(odp_grid *g, int stage)
+static unsigned dynamic_alpha_mask(const odp_grid *g) { return g->dyn.kind == DYN_REL6D ? (1u << 2) : 0u; }
+
+static cudaError_t launch_stage_any(odp_grid *g, int stage, cudaStream_t s)
 {
     const GridDesc &D = g->desc;
     switch (g->dyn.kind) {
     case DYN_SINGLE_INT:
     case DYN_ADVECTION:
-        return launch_stage_si(g->ndim, D, g->dyn, g->state, g->l, g->order, stage, g->brt, g->capture_stream);
+        return launch_stage_si(g->ndim, D, g->dyn, g->state, g->l, g->order, stage, g->brt, s);
     case DYN_DUBINS3D:
     case DYN_DUBINSCAR4D:
-        return launch_stage_dubins(g->ndim, D, g->dyn, g->state, g->l, g->order, stage, g->brt,
-                                   g->capture_stream);
+        return launch_stage_dubins(g->ndim, D, g->dyn, g->state, g->l, g->order, stage, g->brt, s);
     default:
-        return launch_stage_rel6d(D, g->dyn, g->state, g->l, g->order, stage, g->brt, g->capture_stream);
+        return launch_stage_rel6d(D, g->dyn, g->state, g->l, g->order, stage, g->brt, s);
     }
+}
+
+// The kernels of one full time step, in order, on stream s: the Rel6D alpha
+// pass, the CFL step, the stage pass(es) and the closing k_advance.  Used for
+// the captured graph body (in_graph = 1) and for the host-stepped loop.
+static cudaError_t launch_step(odp_grid *g, cudaStream_t s, cudaGraphConditionalHandle h_loop,
+                               cudaGraphConditionalHandle h_snap, int in_graph, int64_t *launches)
+{
+    const bool dyn_alpha = g->dyn.kind == DYN_REL6D;
+    int64_t n = 0;
+    cudaError_t e = cudaSuccess;
+    if (dyn_alpha) {
+        e = launch_alpha_dynamic_rel6d(g->desc, g->dyn, g->state, g->order, 0, s);
+        ++n;
+    }
+    if (e == cudaSuccess) {
+        k_dt<<<1, 1, 0, s>>>(g->state, g->desc);
+        ++n;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        if (g->time_order == 1) {
+            e = launch_stage_any(g, 0, s);
+            ++n;
+        } else {
+            e = launch_stage_any(g, 1, s);
+            ++n;
+            if (e == cudaSuccess && dyn_alpha) {
+                e = launch_alpha_dynamic_rel6d(g->desc, g->dyn, g->state, g->order, 1, s);
+                ++n;
+            }
+            if (e == cudaSuccess) {
+                e = launch_stage_any(g, 2, s);
+                ++n;
+            }
+        }
+    }
+    if (e == cudaSuccess) {
+        k_advance<<<1, 1, 0, s>>>(g->state, g->time_order == 1 ? 1 : 0, dynamic_alpha_mask(g), h_loop, h_snap,
+                                  g->keep, in_graph);
+        ++n;
+        e = cudaGetLastError();
+    }
+    if (launches) *launches = n;
+    return e;
 }
 
 static cudaError_t launch_alpha_static_any(odp_grid *g, cudaStream_t s)
@@ -480,7 +530,6 @@ static cudaError_t launch_alpha_static_any(odp_grid *g, cudaStream_t s)
     }
 }
 
-static unsigned dynamic_alpha_mask(const odp_grid *g) { return g->dyn.kind == DYN_REL6D ? (1u << 2) : 0u; }
 
 // Capture the body of the time loop into `body` and add the snapshot IF node.
 static odp_status build_graph(odp_grid *g)
@@ -509,43 +558,10 @@ static odp_status build_graph(odp_grid *g)
     cudaGraphConditionalHandle h_snap = 0;
     if (g->keep) ODP_CUDA(cudaGraphConditionalHandleCreate(&h_snap, body, 0, 0));
 
-    const bool dyn_alpha = g->dyn.kind == DYN_REL6D;
     cudaStream_t s = g->capture_stream;
     ODP_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     int64_t launches = 0;
-    cudaError_t e = cudaSuccess;
-    if (dyn_alpha) {
-        e = launch_alpha_dynamic_rel6d(g->desc, g->dyn, g->state, g->order, 0, s);
-        ++launches;
-    }
-    if (e == cudaSuccess) {
-        k_dt<<<1, 1, 0, s>>>(g->state, g->desc);
-        ++launches;
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) {
-        if (g->time_order == 1) {
-            e = launch_stage_any(g, 0);
-            ++launches;
-        } else {
-            e = launch_stage_any(g, 1);
-            ++launches;
-            if (e == cudaSuccess && dyn_alpha) {
-                e = launch_alpha_dynamic_rel6d(g->desc, g->dyn, g->state, g->order, 1, s);
-                ++launches;
-            }
-            if (e == cudaSuccess) {
-                e = launch_stage_any(g, 2);
-                ++launches;
-            }
-        }
-    }
-    if (e == cudaSuccess) {
-        k_advance<<<1, 1, 0, s>>>(g->state, g->time_order == 1 ? 1 : 0, dynamic_alpha_mask(g), h_loop,
-                                  h_snap, g->keep);
-        ++launches;
-        e = cudaGetLastError();
-    }
+    cudaError_t e = launch_step(g, s, h_loop, h_snap, 1, &launches);
     cudaStreamCaptureStatus cs;
     const cudaGraphNode_t *deps = nullptr;
     size_t ndeps = 0;
@@ -594,6 +610,42 @@ static odp_status build_graph(odp_grid *g)
         return fail(ODP_ECUDA, "instantiating the time loop: %s", cudaGetErrorString(ei));
     }
     g->launches_per_step = launches;
+    return ODP_OK;
+}
+
+// The time loop stepped from the host: the kernels of the graph body launched
+// one step at a time, the loop and snapshot conditions read back after each
+// step (one synchronisation per step).
+static odp_status run_host_loop(odp_grid *g)
+{
+    cudaStream_t s = g->stream;
+    SolveState *h = nullptr;
+    ODP_CUDA(cudaMallocHost(&h, sizeof(SolveState)));
+    odp_status rc = ODP_OK;
+    for (;;) {
+        cudaError_t e = launch_step(g, s, 0, 0, 0, nullptr);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, g->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && h->snap_now) {
+            const int blocks = int(std::min<int64_t>((g->total_pad + 255) / 256, 152 * 8));
+            k_snapshot<<<blocks, 256, 0, s>>>(g->state, int(g->total_pad));
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {
+            rc = fail(ODP_ECUDA, "host-stepped time loop: %s", cudaGetErrorString(e));
+            break;
+        }
+        if (!h->go) break;
+    }
+    cudaFreeHost(h);
+    return rc;
+}
+
+extern "C" odp_status odp_set_loop_mode(odp_grid *g, int host_stepped)
+{
+    if (!g) return fail(ODP_EINVAL, "grid is NULL");
+    if (host_stepped != 0 && host_stepped != 1) return fail(ODP_EINVAL, "host_stepped must be 0 or 1");
+    g->host_loop = host_stepped;
     return ODP_OK;
 }
 
@@ -670,7 +722,12 @@ extern "C" odp_status odp_solve_hjb(odp_grid *g, const double *tau, int n_tau, o
     ODP_CUDA(launch_alpha_static_any(g, st));
     g->timed = stats != nullptr;
     if (g->timed) ODP_CUDA(cudaEventRecord(g->ev0, st));
-    ODP_CUDA(cudaGraphLaunch(g->exec, st));
+    if (g->host_loop) {
+        odp_status rc = run_host_loop(g);
+        if (rc != ODP_OK) return rc;
+    } else {
+        ODP_CUDA(cudaGraphLaunch(g->exec, st));
+    }
     if (g->timed) ODP_CUDA(cudaEventRecord(g->ev1, st));
     g->solved = true;
     if (stats) return odp_solve_status(g, stats);
@@ -759,7 +816,7 @@ extern "C" odp_status odp_time_stage(odp_grid *g, int stage, int reps, double *m
     ODP_CUDA(cudaStreamSynchronize(g->stream));
     ODP_CUDA(cudaEventRecord(g->ev0, s));
     for (int r = 0; r < reps; ++r) {
-        cudaError_t e = launch_stage_any(g, stage);
+        cudaError_t e = launch_stage_any(g, stage, s);
         if (e != cudaSuccess) return fail(ODP_ECUDA, "stage launch: %s", cudaGetErrorString(e));
     }
     ODP_CUDA(cudaEventRecord(g->ev1, s));

@@ -175,6 +175,8 @@ struct SolveState {
     float *snapshots;            // n_tau * total floats, or nullptr
     unsigned alpha_bits[2][8];   // per stage slot (0: stage 1, 1: stage 2)
     unsigned alpha_last[8];      // alpha of the last stage of the last step
+    int go;                      // the time loop continues (host-stepped loop)
+    int snap_now;                // a snapshot is due after this step (host-stepped loop)
 };
 
 }  // namespace odp

@@ -59,5 +59,6 @@ struct odp_grid {
     GraphKey key;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int64_t launches_per_step = 0;
+    int host_loop = 0;                // 1: the time loop is stepped from the host
 };
 

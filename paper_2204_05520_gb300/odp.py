@@ -108,6 +108,7 @@ def load():
             "odp_set_dynamics": ([P, i32, P, i32, i32, i32], i32),
             "odp_set_target": ([P, P, i64, i32], i32),
             "odp_set_step_limit": ([P, i64], i32),
+            "odp_set_loop_mode": ([P, i32], i32),
             "odp_solve_hjb": ([P, P, i32, i32, i32, i32, f64, i32, P], i32),
             "odp_solve_status": ([P, P], i32),
             "odp_value_readback": ([P, i32, P, i64, i32], i32),
@@ -211,6 +212,12 @@ def set_target(g, l):
 
 def set_step_limit(g, max_steps: int):
     _check(load().odp_set_step_limit(g, int(max_steps)), "odp_set_step_limit")
+
+
+def set_loop_mode(g, host_stepped: bool):
+    """Run the time loop as one CUDA graph (False, default) or stepped from the
+    host with the same kernels (True; for profilers)."""
+    _check(load().odp_set_loop_mode(g, 1 if host_stepped else 0), "odp_set_loop_mode")
 
 
 def solve_hjb(g, tau, set_kind="brt", space_order=1, time_order=1, cfl=0.8, keep_snapshots=False,

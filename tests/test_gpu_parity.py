@@ -270,3 +270,28 @@ def test_rel6d_full_size_solve_properties():
     assert np.isfinite(v).all()
     assert (v <= l).all()
     assert stats["alpha"][0] == pytest.approx(7.0) and stats["alpha"][1] == pytest.approx(5.5)
+
+
+@pytest.mark.parametrize("problem", [
+    inputs.dubins3d(n=(21, 23, 16), horizon=0.5),
+    dataclasses.replace(inputs.dubinscar4d(n=(11, 13, 7, 12), horizon=0.4), tau=np.array([0.0, 0.1, 0.25, 0.4])),
+    inputs.rel6d(n=(6, 6, 8, 4, 4, 4), horizon=0.2),
+], ids=["dubins3d_euler", "dubinscar4d_rk2_eno2_snapshots", "rel6d_rk2"])
+def test_host_stepped_loop_equals_graph_loop(problem):
+    # the same kernels in the same order: bit-identical values, snapshots and steps
+    import torch
+
+    l_dev = torch.from_numpy(problem.target_values()).cuda()
+    keep = len(problem.tau) > 2
+    res = []
+    for host in (False, True):
+        with odp.Grid.for_problem(problem) as g:
+            odp.set_loop_mode(g.handle, host)
+            g.set_target(l_dev)
+            st = g.solve_problem(problem, keep_snapshots=keep, stats=True)
+            vals = [g.readback(torch.empty_like(l_dev), k).cpu().numpy()
+                    for k in (range(len(problem.tau)) if keep else [-1])]
+            res.append((st["steps"], vals))
+    assert res[0][0] == res[1][0] > 0
+    for a, b in zip(res[0][1], res[1][1]):
+        assert np.array_equal(a, b)
