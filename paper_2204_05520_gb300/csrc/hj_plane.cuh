@@ -86,21 +86,27 @@ __global__ void __launch_bounds__(512) k_stage_plane(GridDesc g, DynDesc dy, Sol
     const float dt = float(st->dt);
     const bool use_l = brt && stage != 1;
 
-    // work item: chunk fastest, then band, then outer pencil
+    // work item: chunk fastest, then band, then outer pencil.  Outer pencils
+    // are numbered block by block (blocks of up to 8 indices per outer axis),
+    // so CTAs that run together read each other's neighbour planes from L2.
     const uint32_t item = blockIdx.x;
     const uint32_t q1 = fast_div(item, pg.div_nchunks);
     const int chunk = int(item - q1 * uint32_t(pg.nchunks));
     const uint32_t outer = fast_div(q1, pg.div_nbands);
     const int band = int(q1 - outer * uint32_t(pg.nbands));
     int idx[ND];
-    {
-        uint32_t o = outer;
-        for (int d = ND - 4; d > 0; --d) {
-            const uint32_t q = fast_div(o, g.div[d]);
-            idx[d] = int(o - q * uint32_t(g.n[d]));
-            o = q;
+    int pencil = 0;   // storage offset of the pencil's plane 0
+    if (NOUT > 0) {
+        const uint32_t blk0 = fast_div(outer, pg.div_bvol);
+        uint32_t w = outer - blk0 * uint32_t(pg.bvol), blk = blk0;
+#pragma unroll
+        for (int d = NOUT - 1; d >= 0; --d) {
+            const uint32_t wq = fast_div(w, pg.div_bdim[d]), bq = fast_div(blk, pg.div_nblk[d]);
+            idx[d] = int(blk - bq * uint32_t(pg.nblk[d])) * pg.bdim[d] + int(w - wq * uint32_t(pg.bdim[d]));
+            w = wq;
+            blk = bq;
+            pencil += idx[d] * g.stride[d];
         }
-        if (ND >= 4) idx[0] = int(o);
     }
     constexpr int sa = ND - 3;
     const int ns = pg.ns, plane = pg.plane;
@@ -116,7 +122,7 @@ __global__ void __launch_bounds__(512) k_stage_plane(GridDesc g, DynDesc dy, Sol
     const int s0 = (tid - j * g.segs) * 4;
     const bool active = j < band_rows;
     const int r = band_lo + (active ? j : 0);
-    const int base = int(outer) * ns * plane + r * npad + s0;   // offset on stream plane 0
+    const int base = pencil + r * npad + s0;   // offset on stream plane 0
     const int so = 4 + (O + j) * cp + s0;                       // offset in a tile
     const int nvalid = FULL ? 4 : min(4, nl - s0);
 

@@ -184,6 +184,24 @@ static void plane_geometry(GridDesc &D, int sms)
     pg.items = int(base * pg.nchunks);
     pg.div_nchunks = make_fastdiv(uint32_t(pg.nchunks));
     pg.div_nbands = make_fastdiv(uint32_t(pg.nbands));
+    // blocks of outer pencils: per outer axis the largest divisor of its
+    // length up to 8
+    pg.bvol = 1;
+    for (int d = 0; d < 3; ++d) {
+        int b = 1;
+        if (d < D.ndim - 3)
+            for (int c = 8; c >= 1; --c)
+                if (D.n[d] % c == 0) {
+                    b = c;
+                    break;
+                }
+        pg.bdim[d] = b;
+        pg.nblk[d] = d < D.ndim - 3 ? D.n[d] / b : 1;
+        pg.bvol *= b;
+        pg.div_bdim[d] = make_fastdiv(uint32_t(b));
+        pg.div_nblk[d] = make_fastdiv(uint32_t(pg.nblk[d]));
+    }
+    pg.div_bvol = make_fastdiv(uint32_t(pg.bvol));
     pg.use = 1;
 }
 

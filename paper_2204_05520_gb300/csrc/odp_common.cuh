@@ -111,6 +111,10 @@ struct PlaneGeom {
     int threads;       // CTA size: rb * segs rounded up to a warp
     int smem[2];       // dynamic shared bytes (two tiles) for stencil radius 1, 2
     FastDiv div_nchunks, div_nbands;
+    // outer pencils in blocks: bdim[d] indices of outer axis d per block,
+    // nblk[d] blocks along it, bvol pencils per block
+    int bdim[3], nblk[3], bvol;
+    FastDiv div_bdim[3], div_nblk[3], div_bvol;
 };
 
 // Storage: C order with the last axis padded to n_pad, a multiple of 4 nodes,
