@@ -67,7 +67,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return obj, r.stderr
 
     objs = []
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1))) as ex:
         for obj, log in ex.map(compile_one, sources()):
             objs.append(obj)
             if verbose and log:

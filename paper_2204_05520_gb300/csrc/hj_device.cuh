@@ -74,8 +74,8 @@ ODP_HD float2 f2mul(float2 a, float2 b)
 #endif
 }
 
-// a - b, rounded once (b * -1 is exact)
-ODP_HD float2 f2sub(float2 a, float2 b) { return f2fma(b, make_float2(-1.0f, -1.0f), a); }
+// a - b lane by lane (a + (-b), rounded once)
+ODP_HD float2 f2sub(float2 a, float2 b) { return f2add(a, make_float2(-b.x, -b.y)); }
 
 ODP_HD float2 f2abs(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
 

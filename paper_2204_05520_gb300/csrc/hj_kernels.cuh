@@ -542,18 +542,38 @@ cudaError_t launch_stage_t(const GridDesc &g, const DynDesc &dy, SolveState *st,
 {
     if constexpr (ND >= 3) {
         if (g.pg.use) {
+            // Dubins3D, DubinsCar4D and Rel6D grids whose last axis is a
+            // multiple of 4 get one kernel per RK stage; the other models and
+            // shapes take the stage at run time
             const int blocks = g.pg.items, th = g.pg.threads, sm = g.pg.smem[order - 1];
             const bool full = g.n[ND - 1] % 4 == 0;
-            if (order == 1) {
+            constexpr bool SPEC = DYN == DYN_DUBINS3D || DYN == DYN_DUBINSCAR4D || DYN == DYN_REL6D;
+            if (SPEC && full) {
+                if (order == 1) {
+                    if (stage == 0)
+                        k_stage_plane<ND, 1, DYN, true, 0><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
+                    else if (stage == 1)
+                        k_stage_plane<ND, 1, DYN, true, 1><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
+                    else
+                        k_stage_plane<ND, 1, DYN, true, 2><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
+                } else {
+                    if (stage == 0)
+                        k_stage_plane<ND, 2, DYN, true, 0><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
+                    else if (stage == 1)
+                        k_stage_plane<ND, 2, DYN, true, 1><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
+                    else
+                        k_stage_plane<ND, 2, DYN, true, 2><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
+                }
+            } else if (order == 1) {
                 if (full)
-                    k_stage_plane<ND, 1, DYN, true><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
+                    k_stage_plane<ND, 1, DYN, true, -1><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
                 else
-                    k_stage_plane<ND, 1, DYN, false><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
+                    k_stage_plane<ND, 1, DYN, false, -1><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
             } else {
                 if (full)
-                    k_stage_plane<ND, 2, DYN, true><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
+                    k_stage_plane<ND, 2, DYN, true, -1><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
                 else
-                    k_stage_plane<ND, 2, DYN, false><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
+                    k_stage_plane<ND, 2, DYN, false, -1><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
             }
             return cudaGetLastError();
         }

@@ -61,12 +61,14 @@ __device__ __forceinline__ float4 ghost4(const float4 &pb, const float4 &pi, flo
 // periodic last axis is read at the wrapped columns of the tile row, ghost
 // columns are formed from the segment's own values; otherwise the row's
 // first and last segments write them into the tile one plane ahead.
+// STAGE >= 0 fixes the RK stage at compile time (-1: the stage_rt argument).
 // Non-finite values are detected by accumulating x - x over the updated nodes
 // (0 for finite x, NaN otherwise) and testing the sum once at the end.
-template <int ND, int ORDER, int DYN, bool FULL>
+template <int ND, int ORDER, int DYN, bool FULL, int STAGE>
 __global__ void __launch_bounds__(512) k_stage_plane(GridDesc g, DynDesc dy, SolveState *st,
-                                                     const float *__restrict__ l, int stage, int brt)
+                                                     const float *__restrict__ l, int stage_rt, int brt)
 {
+    const int stage = STAGE >= 0 ? STAGE : stage_rt;
     const PlaneGeom &pg = g.pg;
     constexpr int O = ORDER;
     constexpr int Q = 2 * O + 1;        // stream-axis window
@@ -141,8 +143,10 @@ __global__ void __launch_bounds__(512) k_stage_plane(GridDesc g, DynDesc dy, Sol
         }
     }
     // ghost rows this thread forms: 1 on the boundary row, 2 on the next one
+    // (only bands at a non-periodic grid edge have such rows)
     const int gtop = (!per_r && r < O) ? r + 1 : 0;
     const int gbot = (!per_r && r >= nr - O) ? nr - r : 0;
+    const bool edge_band = !per_r && (band_lo < O || band_lo + band_rows > nr - O);
     // halo columns
     int lh_off = -2, rh_off = 4;   // relative to the segment's first node in the tile
     bool lghost = false, rghost = false, lcol = false, rcol = false;
@@ -280,17 +284,19 @@ __global__ void __launch_bounds__(512) k_stage_plane(GridDesc g, DynDesc dy, Sol
                     float4 p1 = *reinterpret_cast<const float4 *>(C + cp);
                     float4 m2 = (O == 2) ? *reinterpret_cast<const float4 *>(C - 2 * cp) : m1;
                     float4 p2 = (O == 2) ? *reinterpret_cast<const float4 *>(C + 2 * cp) : p1;
-                    if (gtop == 1) {
-                        m1 = ghost4(c4, p1, 1.0f);
-                        m2 = (O == 2) ? ghost4(c4, p1, 2.0f) : m1;
-                    } else if (gtop == 2) {
-                        m2 = ghost4(m1, c4, 1.0f);
-                    }
-                    if (gbot == 1) {
-                        p1 = ghost4(c4, m1, 1.0f);
-                        p2 = (O == 2) ? ghost4(c4, m1, 2.0f) : p1;
-                    } else if (gbot == 2) {
-                        p2 = ghost4(p1, c4, 1.0f);
+                    if (edge_band) {
+                        if (gtop == 1) {
+                            m1 = ghost4(c4, p1, 1.0f);
+                            m2 = (O == 2) ? ghost4(c4, p1, 2.0f) : m1;
+                        } else if (gtop == 2) {
+                            m2 = ghost4(m1, c4, 1.0f);
+                        }
+                        if (gbot == 1) {
+                            p1 = ghost4(c4, m1, 1.0f);
+                            p2 = (O == 2) ? ghost4(c4, m1, 2.0f) : p1;
+                        } else if (gbot == 2) {
+                            p2 = ghost4(p1, c4, 1.0f);
+                        }
                     }
                     segment_axis<ORDER>(m2, m1, c4, p1, p2, cA[ND - 2], cS[ND - 2], cD[ND - 2], L01, L23,
                                         has_drift<DYN, ND>(ND - 2), has_bound<DYN, ND>(ND - 2));

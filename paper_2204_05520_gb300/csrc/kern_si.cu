@@ -1,8 +1,17 @@
 // kern_si.cu -- kernel instantiations for the single integrator and the
-// constant-velocity advection model, 1 to 6 dimensions.
-#include "hj_kernels.cuh"
+// constant-velocity advection model: 1 to 3 dimensions here, 4, 5 and 6 in
+// kern_si4.cu, kern_si5.cu and kern_si6.cu; the launchers dispatch on the
+// dimension count.
+#include "kern_si_nd.cuh"
 
 namespace odp {
+
+ODP_SI_INSTANTIATE(1)
+ODP_SI_INSTANTIATE(2)
+ODP_SI_INSTANTIATE(3)
+ODP_SI_EXTERN(4)
+ODP_SI_EXTERN(5)
+ODP_SI_EXTERN(6)
 
 #define ODP_ND_SWITCH(nd, CALL)                                                  \
     switch (nd) {                                                                \
@@ -18,27 +27,18 @@ namespace odp {
 cudaError_t launch_stage_si(int nd, const GridDesc &g, const DynDesc &dy, SolveState *st,
                             const float *l, int order, int stage, int brt, cudaStream_t s)
 {
-    if (dy.kind == DYN_SINGLE_INT) {
-        ODP_ND_SWITCH(nd, (launch_stage_t<ND, DYN_SINGLE_INT>(g, dy, st, l, order, stage, brt, s)))
-    }
-    ODP_ND_SWITCH(nd, (launch_stage_t<ND, DYN_ADVECTION>(g, dy, st, l, order, stage, brt, s)))
+    ODP_ND_SWITCH(nd, (launch_stage_si_nd<ND>(g, dy, st, l, order, stage, brt, s)))
 }
 
 cudaError_t configure_stage_si(int nd, int kind)
 {
-    if (kind == DYN_SINGLE_INT) {
-        ODP_ND_SWITCH(nd, (configure_stage_t<ND, DYN_SINGLE_INT>()))
-    }
-    ODP_ND_SWITCH(nd, (configure_stage_t<ND, DYN_ADVECTION>()))
+    ODP_ND_SWITCH(nd, (configure_stage_si_nd<ND>(kind)))
 }
 
 cudaError_t launch_alpha_static_si(int nd, const GridDesc &g, const DynDesc &dy, SolveState *st,
                                    cudaStream_t s)
 {
-    if (dy.kind == DYN_SINGLE_INT) {
-        ODP_ND_SWITCH(nd, (launch_alpha_static_t<ND, DYN_SINGLE_INT>(g, dy, st, s)))
-    }
-    ODP_ND_SWITCH(nd, (launch_alpha_static_t<ND, DYN_ADVECTION>(g, dy, st, s)))
+    ODP_ND_SWITCH(nd, (launch_alpha_static_si_nd<ND>(g, dy, st, s)))
 }
 
 }  // namespace odp
