@@ -64,8 +64,26 @@ __device__ __forceinline__ float4 ghost4(const float4 &pb, const float4 &pi, flo
 // STAGE >= 0 fixes the RK stage at compile time (-1: the stage_rt argument).
 // Non-finite values are detected by accumulating x - x over the updated nodes
 // (0 for finite x, NaN otherwise) and testing the sum once at the end.
+// Register budget per model and order, chosen so that whole CTAs fill the
+// register file of each SM sub-partition (16384 registers for its warps):
+// the DubinsCar4D ENO2 pass (7-warp CTAs) runs 3 CTAs per SM at 80
+// registers, the Rel6D upwind pass (5-warp CTAs) 4 CTAs at 96.  The
+// DubinsCar4D pass loads its outer-axis neighbours after the plane barrier
+// instead of before it, which keeps it within 80 registers.
+template <int ND, int ORDER, int DYN>
+constexpr int plane_max_regs()
+{
+    return (DYN == DYN_DUBINSCAR4D && ORDER == 2) ? 80 : (DYN == DYN_REL6D && ORDER == 1) ? 96 : 128;
+}
+
+template <int ND, int ORDER, int DYN>
+constexpr bool plane_late_outer_loads()
+{
+    return DYN == DYN_DUBINSCAR4D && ORDER == 2;
+}
+
 template <int ND, int ORDER, int DYN, bool FULL, int STAGE>
-__global__ void __launch_bounds__(512) k_stage_plane(GridDesc g, DynDesc dy, SolveState *st,
+__global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DYN>())) k_stage_plane(GridDesc g, DynDesc dy, SolveState *st,
                                                      const float *__restrict__ l, int stage_rt, int brt)
 {
     const int stage = STAGE >= 0 ? STAGE : stage_rt;
@@ -73,6 +91,7 @@ __global__ void __launch_bounds__(512) k_stage_plane(GridDesc g, DynDesc dy, Sol
     constexpr int O = ORDER;
     constexpr int Q = 2 * O + 1;        // stream-axis window
     constexpr int NOUT = ND - 3;        // outer axes
+    constexpr bool LATE = plane_late_outer_loads<ND, ORDER, DYN>();
     extern __shared__ __align__(16) float smem[];
     const int cp = pg.cp;               // tile row pitch: n_pad + 4
     const int tile = 4 + (pg.rb + 2 * O) * cp;
@@ -248,11 +267,13 @@ __global__ void __launch_bounds__(512) k_stage_plane(GridDesc g, DynDesc dy, Sol
                     }
                 }
                 // loads for this plane's update and for the next plane
+                if (!LATE) {
 #pragma unroll
-                for (int d = 0; d < NOUT; ++d)
+                    for (int d = 0; d < NOUT; ++d)
 #pragma unroll
-                    for (int k = 0; k < 2 * O; ++k)
-                        nb[d][k] = INNER ? ldg4(src + gi + nbq[d][k].delta) : nb_value(src, gi, nbq[d][k]);
+                        for (int k = 0; k < 2 * O; ++k)
+                            nb[d][k] = INNER ? ldg4(src + gi + nbq[d][k].delta) : nb_value(src, gi, nbq[d][k]);
+                }
                 if (use_l) lx = ldg4(l + gi);
                 if (stage == 2) px = *reinterpret_cast<const float4 *>(prev + gi);
                 if (s + 1 < s_end) {
@@ -266,6 +287,13 @@ __global__ void __launch_bounds__(512) k_stage_plane(GridDesc g, DynDesc dy, Sol
                 if (DYN == DYN_REL6D && s != s_begin) {   // the x drift depends on v_p (the stream axis)
                     idx[sa] = s;
                     drift<DYN, ND>(g, dy, idx, cA, cS);
+                }
+                if (LATE) {
+#pragma unroll
+                    for (int d = 0; d < NOUT; ++d)
+#pragma unroll
+                        for (int k = 0; k < 2 * O; ++k)
+                            nb[d][k] = INNER ? ldg4(src + gi + nbq[d][k].delta) : nb_value(src, gi, nbq[d][k]);
                 }
                 const float *C = T + so;
                 float2 L01 = make_float2(0.0f, 0.0f), L23 = make_float2(0.0f, 0.0f);
