@@ -61,6 +61,13 @@ ODP_HD float last_axis_value(const float *__restrict__ row, int j, int n, int pe
     return keep_sign_ghost(ldgf(row + b), ldgf(row + in), k);
 }
 
+// Rel6D x drift of the four nodes of a segment, -v_p + v_e cos th + w_p y
+// (unscaled; reading R12 of the model).
+ODP_HD void rel6d_x_drift(float vp, const float4 &ve, float c, float wp, float y, float *a)
+{
+    for (int k = 0; k < 4; ++k) a[k] = -vp + lane(ve, k) * c + wp * y;
+}
+
 // Half-scaled drift coefficients of the four nodes of a segment,
 // cA_d = a_d(z) / (2 h_d), and of the signed input bounds, cS_d = S_d / (2 h_d)
 // (Appendix dynamics; Section 4.2 modes).  idx holds the node's axis indices
@@ -104,8 +111,8 @@ ODP_HD void drift(const GridDesc &g, const DynDesc &dy, const int *idx, float cA
         const float vp = ldgf(g.coord[3] + idx[3]);
         const float wp = ldgf(g.coord[4] + idx[4]);
         const float4 ve = ldg4(g.coord[5] + s0);
+        rel6d_x_drift(vp, ve, c, wp, y, cA[0]);
         for (int k = 0; k < 4; ++k) {
-            cA[0][k] = -vp + lane(ve, k) * c + wp * y;
             cA[1][k] = lane(ve, k) * s - wp * x;
             cA[2][k] = -wp;
         }

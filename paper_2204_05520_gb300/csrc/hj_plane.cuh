@@ -206,18 +206,28 @@ __global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DY
                 q.k = jd < 0 ? float(-jd) : float(jd - (g.n[d] - 1));
                 q.db = (b - idx[d]) * sd;
                 q.di = (in - idx[d]) * sd;
-                inner = false;
             }
+            // the interior path takes every neighbour at o strides, unwrapped
+            if (jd != idx[d] + o || q.ghost) inner = false;
             nbq[d][k++] = q;
         }
     }
 
-    // drift coefficients of the segment
+    // drift coefficients of the segment; for Rel6D also the factors of its x
+    // drift that do not depend on v_p, the stream axis
     float cA[ND][4], cS[ND];
     idx[sa] = s_begin;
     idx[ND - 2] = r;
     idx[ND - 1] = s0;
     drift<DYN, ND>(g, dy, idx, cA, cS);
+    float4 rx_ve = make_float4(0.f, 0.f, 0.f, 0.f);
+    float rx_c = 0.f, rx_wp = 0.f, rx_y = 0.f;
+    if (DYN == DYN_REL6D) {
+        rx_ve = ldg4(g.coord[ND - 1] + s0);
+        rx_c = ldgf(g.cos_tab + idx[2]);
+        rx_wp = ldgf(g.coord[4] + idx[4]);
+        rx_y = ldgf(g.coord[1] + idx[1]);
+    }
 
     // halo values of plane p for this thread's duties (loaded one plane ahead)
     float4 hx = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -272,7 +282,7 @@ __global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DY
                     for (int d = 0; d < NOUT; ++d)
 #pragma unroll
                         for (int k = 0; k < 2 * O; ++k)
-                            nb[d][k] = INNER ? ldg4(src + gi + nbq[d][k].delta) : nb_value(src, gi, nbq[d][k]);
+                            nb[d][k] = INNER ? ldg4(src + gi + (k < O ? k - O : k - O + 1) * g.stride[d]) : nb_value(src, gi, nbq[d][k]);
                 }
                 if (use_l) lx = ldg4(l + gi);
                 if (stage == 2) px = *reinterpret_cast<const float4 *>(prev + gi);
@@ -285,15 +295,16 @@ __global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DY
 
             if (active) {
                 if (DYN == DYN_REL6D && s != s_begin) {   // the x drift depends on v_p (the stream axis)
-                    idx[sa] = s;
-                    drift<DYN, ND>(g, dy, idx, cA, cS);
+                    rel6d_x_drift(ldgf(g.coord[3] + s), rx_ve, rx_c, rx_wp, rx_y, cA[0]);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) cA[0][k] *= 0.5f * g.inv_dz[0];
                 }
                 if (LATE) {
 #pragma unroll
                     for (int d = 0; d < NOUT; ++d)
 #pragma unroll
                         for (int k = 0; k < 2 * O; ++k)
-                            nb[d][k] = INNER ? ldg4(src + gi + nbq[d][k].delta) : nb_value(src, gi, nbq[d][k]);
+                            nb[d][k] = INNER ? ldg4(src + gi + (k < O ? k - O : k - O + 1) * g.stride[d]) : nb_value(src, gi, nbq[d][k]);
                 }
                 const float *C = T + so;
                 float2 L01 = make_float2(0.0f, 0.0f), L23 = make_float2(0.0f, 0.0f);
@@ -361,7 +372,8 @@ __global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DY
             }
         return nx;
     };
-    // CTAs with every outer neighbour inside the grid (most of them) run the
+    // CTAs whose outer neighbours all lie at plain stride offsets inside the
+    // grid (most of them) run the
     // loop unrolled by the window length, so the window is never shifted; the
     // others shift it (smaller code: the two paths share the instruction cache)
     auto run = [&](auto inner_tag) {
