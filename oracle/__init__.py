@@ -68,9 +68,9 @@ def _load():
             lib.og_eval_dynamics_batch.restype = i32
             lib.og_terms.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, i32, P, P,
                                      P, P, P, P, P, P, P, P]
-            lib.og_solve.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, P, P, i32, i32,
+            lib.og_solve.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, P, P, P, i32, i32,
                                      i32, i32, f64, i64, P, P, P, P, P]
-            lib.og_step.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, P, f64, i32, i32,
+            lib.og_step.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, P, P, f64, i32, i32,
                                     i32, P, P]
             for f in (lib.og_spacing, lib.og_eval_dynamics, lib.og_terms, lib.og_solve,
                       lib.og_step):
@@ -183,7 +183,15 @@ def terms(problem_or_grid, phi, order=None, alpha=None, dynamics=None, params=No
     return out
 
 
-def step(problem, phi, dt, l=None) -> dict:
+def _obstacle(problem, g):
+    """float64 obstacle array: ``g`` if given, else the problem's own
+    obstacle (float32 values promoted), else None."""
+    if g is None and getattr(problem, "obstacle", None) is not None:
+        g = problem.obstacle_values()
+    return None if g is None else np.ascontiguousarray(g, dtype=np.float64).reshape(-1)
+
+
+def step(problem, phi, dt, l=None, g=None) -> dict:
     """One full time step of size ``dt`` from ``phi`` (float64 copy taken),
     as ``solve`` takes it.  Returns dict(out, alpha) with alpha of stage 1."""
     lib = _load()
@@ -192,13 +200,15 @@ def step(problem, phi, dt, l=None) -> dict:
     if l is None:
         l = p.target_values()
     l64 = np.ascontiguousarray(l, dtype=np.float64).reshape(-1)
+    g64 = _obstacle(p, g)
     phi64 = np.ascontiguousarray(phi, dtype=np.float64).reshape(-1)
     prm = np.ascontiguousarray(p.params, dtype=np.float64)
     out = np.zeros_like(phi64)
     alpha = np.zeros(len(n_a))
     rc = lib.og_step(len(n_a), _ptr(n_a), _ptr(lo_a), _ptr(hi_a), _ptr(per_a),
                      DYN_IDS[p.dynamics], _ptr(prm), len(prm), MODE_IDS[p.u_mode],
-                     MODE_IDS[p.d_mode], _ptr(l64), _ptr(phi64), float(dt), SET_IDS[p.set_kind],
+                     MODE_IDS[p.d_mode], _ptr(l64), _ptr(g64), _ptr(phi64), float(dt),
+                     SET_IDS[p.set_kind],
                      p.space_order, p.time_order, _ptr(out), _ptr(alpha))
     if rc:
         raise OracleError(rc, "step")
@@ -206,10 +216,12 @@ def step(problem, phi, dt, l=None) -> dict:
 
 
 def solve(problem, l=None, snapshots: bool = False, max_steps: int = 10_000_000,
-          raise_on_error: bool = True, phi0=None) -> dict:
+          raise_on_error: bool = True, phi0=None, g=None) -> dict:
     """Run the full solve of ``problem`` (an ``inputs.Problem``).
 
     ``l`` defaults to ``problem.target_values()`` (float32) promoted to float64.
+    ``g`` (optional) is an obstacle (reach-avoid); it defaults to the
+    problem's own obstacle, if it has one.
     ``phi0`` (optional) is the value to start from instead of ``l``.
     Returns dict(final, snapshots (or None), steps (per segment), alpha,
     last_dt, rc).
@@ -220,6 +232,7 @@ def solve(problem, l=None, snapshots: bool = False, max_steps: int = 10_000_000,
     if l is None:
         l = p.target_values()
     l64 = np.ascontiguousarray(l, dtype=np.float64).reshape(-1)
+    g64 = _obstacle(p, g)
     p0 = None if phi0 is None else np.ascontiguousarray(phi0, dtype=np.float64).reshape(-1)
     tau = np.ascontiguousarray(p.tau, dtype=np.float64)
     prm = np.ascontiguousarray(p.params, dtype=np.float64)
@@ -231,7 +244,7 @@ def solve(problem, l=None, snapshots: bool = False, max_steps: int = 10_000_000,
     last_dt = ctypes.c_double(0.0)
     rc = lib.og_solve(len(n_a), _ptr(n_a), _ptr(lo_a), _ptr(hi_a), _ptr(per_a),
                       DYN_IDS[p.dynamics], _ptr(prm), len(prm), MODE_IDS[p.u_mode],
-                      MODE_IDS[p.d_mode], _ptr(l64), _ptr(p0), _ptr(tau), len(tau),
+                      MODE_IDS[p.d_mode], _ptr(l64), _ptr(g64), _ptr(p0), _ptr(tau), len(tau),
                       SET_IDS[p.set_kind],
                       p.space_order, p.time_order, float(p.cfl), int(max_steps), _ptr(snaps),
                       _ptr(final), _ptr(steps), _ptr(alpha), ctypes.byref(last_dt))

@@ -33,6 +33,11 @@
  *     the stage-1 alpha, stage 2 uses its own alpha.  BRT min once per step.
  *  R9 ghost cells on non-periodic axes: k cells outside the boundary point b,
  *     g_k = phi_b + k*sign(phi_b)*|phi_b - phi_inner|, sign(0) = +1.
+ *  R17 reach-avoid (Section 4.3, the target and obstacle computation
+ *     methods): with an obstacle function g, after each full step
+ *     phi <- max(phi, g), taken after the BRT min with l (target first, then
+ *     obstacle, in the order the solver options list them); g is
+ *     time-invariant here.
  *  R10 ENO2: p- = D-phi + (h/2) c, p+ = D+phi - (h/2) c', c (c') the second
  *     difference of smaller magnitude among those at i-1 and i (i and i+1);
  *     on equal magnitude the centred one (at i).  The comparison is taken in
@@ -579,13 +584,13 @@ int og_terms(int ndim, const int64_t *n, const double *lo, const double *hi,
 }
 
 /* One full time step of size dt from phi (Algorithm 1 update with the
- * Euler or TVD-RK2 integrator of Section 3.1.3 and the BRS / BRT post-step),
- * as taken inside og_solve.  out may not alias phi.  alpha_out (ndim) gets the
+ * Euler or TVD-RK2 integrator of Section 3.1.3, the BRS / BRT post-step and
+ * the obstacle max when obst is not NULL), as taken inside og_solve.  out may not alias phi.  alpha_out (ndim) gets the
  * stage-1 alpha (the one the CFL step is computed from). */
 int og_step(int ndim, const int64_t *n, const double *lo, const double *hi, const int *periodic,
             int kind, const double *prm, int n_prm, int umode, int dmode, const double *l,
-            const double *phi, double dt, int set_kind, int space_order, int time_order,
-            double *out, double *alpha_out)
+            const double *obst, const double *phi, double dt, int set_kind, int space_order,
+            int time_order, double *out, double *alpha_out)
 {
     og_grid g;
     og_dyn dy;
@@ -613,6 +618,9 @@ int og_step(int ndim, const int64_t *n, const double *lo, const double *hi, cons
     if (set_kind == OG_BRT)
         for (int64_t i = 0; i < N; ++i)
             if (l[i] < out[i]) out[i] = l[i];
+    if (obst)
+        for (int64_t i = 0; i < N; ++i)
+            if (obst[i] > out[i]) out[i] = obst[i];
     free(L);
     free(phi1);
     return OG_OK;
@@ -625,6 +633,8 @@ int og_step(int ndim, const int64_t *n, const double *lo, const double *hi, cons
  *  tau         n_tau look-back times, tau[0] = 0, strictly increasing
  *  set_kind    OG_BRS (plain PDE) or OG_BRT (phi <- min(phi, l) after each step,
  *              the HJ variational inequality)
+ *  obst        NULL, or the obstacle g(z): phi <- max(phi, g) after each step,
+ *              after the BRT min (reach-avoid, reading R17)
  *  snapshots   NULL, or n_tau * total doubles: phi at every tau
  *  final_out   total doubles: phi at tau[n_tau-1]
  *  steps_out   NULL or n_tau-1 step counts, one per segment
@@ -633,7 +643,8 @@ int og_step(int ndim, const int64_t *n, const double *lo, const double *hi, cons
  */
 int og_solve(int ndim, const int64_t *n, const double *lo, const double *hi,
              const int *periodic, int kind, const double *prm, int n_prm, int umode,
-             int dmode, const double *l, const double *phi0, const double *tau, int n_tau,
+             int dmode, const double *l, const double *obst, const double *phi0,
+             const double *tau, int n_tau,
              int set_kind, int space_order, int time_order, double cfl, int64_t max_steps,
              double *snapshots, double *final_out, int64_t *steps_out,
              double *alpha_out, double *last_dt)
@@ -685,6 +696,7 @@ int og_solve(int ndim, const int64_t *n, const double *lo, const double *hi,
             for (int64_t i = 0; i < N; ++i) {
                 double v = phi1[i];
                 if (set_kind == OG_BRT && l[i] < v) v = l[i];
+                if (obst && obst[i] > v) v = obst[i];
                 if (!isfinite(v)) bad = 1;
                 phi[i] = v;
             }

@@ -26,7 +26,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import Callable, Sequence
+from typing import Callable, Optional, Sequence
 
 import numpy as np
 
@@ -53,6 +53,9 @@ class Problem:
     space_order: int = 1
     time_order: int = 1
     cfl: float = 0.8
+    # reach-avoid: obstacle g(z), positive inside the obstacle; after each step
+    # phi <- max(phi, g) (after the BRT min with l)
+    obstacle: Optional[Callable[[Sequence[np.ndarray]], np.ndarray]] = None
 
     @property
     def ndim(self) -> int:
@@ -69,6 +72,14 @@ class Problem:
         """l(z) at every node, C order, rounded to float32."""
         mesh = np.meshgrid(*self.nodes(), indexing="ij")
         return np.ascontiguousarray(self.target(mesh), dtype=np.float64).astype(np.float32)
+
+    def obstacle_values(self) -> np.ndarray:
+        """g(z) at every node, C order, rounded to float32 (None without an
+        obstacle)."""
+        if self.obstacle is None:
+            return None
+        mesh = np.meshgrid(*self.nodes(), indexing="ij")
+        return np.ascontiguousarray(self.obstacle(mesh), dtype=np.float64).astype(np.float32)
 
 
 def node_coords(n, lo, hi, periodic) -> list:
@@ -105,6 +116,27 @@ def ball(radius: float) -> Callable:
         for m in mesh:
             acc = acc + m * m
         return np.sqrt(acc) - radius
+
+    return f
+
+
+def cylinder_obstacle(radius: float, center, dims=(0, 1)) -> Callable:
+    """Obstacle function of a cylinder: radius minus the distance to its axis
+    (positive inside)."""
+    inside = cylinder(radius, dims=dims, center=center)
+    return lambda mesh: -inside(mesh)
+
+
+def box_obstacle(lo: Sequence[float], hi: Sequence[float], dims: Sequence[int]) -> Callable:
+    """Obstacle function of an axis-aligned box over the given dimensions:
+    the smallest distance from a face, positive inside, negative outside."""
+
+    def f(mesh):
+        acc = None
+        for a, b, d in zip(lo, hi, dims):
+            v = np.minimum(mesh[d] - a, b - mesh[d])
+            acc = v if acc is None else np.minimum(acc, v)
+        return acc
 
     return f
 
@@ -198,14 +230,27 @@ def advection(n, velocity, freqs=None, horizon=1.0, cfl=1.0, space_order=1,
         space_order=space_order, time_order=time_order, cfl=cfl)
 
 
+def reach_avoid(problem: Problem, obstacle: Callable) -> Problem:
+    """The same solve as a reach-avoid problem with obstacle function g."""
+    return dataclasses.replace(problem, name=problem.name + "_reach_avoid", obstacle=obstacle)
+
+
+def dubins_obstacle() -> Callable:
+    """Cylinder obstacle of radius 0.75 centred at (x, y) = (2, 0.5), beside
+    the target of the Dubins workloads."""
+    return cylinder_obstacle(0.75, center=(2.0, 0.5))
+
+
 def workload(name: str) -> Problem:
-    """The three named single-solve workloads at full size."""
+    """The named single-solve workloads at full size."""
     if name == "dubins3d":
         return dubins3d()
     if name == "dubinscar4d":
         return dubinscar4d()
     if name == "rel6d":
         return rel6d()
+    if name == "dubinscar4d_reach_avoid":
+        return reach_avoid(dubinscar4d(), dubins_obstacle())
     raise KeyError(name)
 
 

@@ -497,3 +497,88 @@ def test_resuming_from_a_kept_value_continues_the_schedule():
     res = oracle.solve(seg, phi0=full["snapshots"][1])
     np.testing.assert_allclose(res["final"], full["final"], atol=1e-12)
     assert res["steps"][0] == full["steps"][1]
+
+
+# ---------------------------------------------------------------------------
+# reach-avoid: phi <- max(min(phi, l), g) after each step (Section 4.3, the
+# target and obstacle computation methods; reading R17)
+# ---------------------------------------------------------------------------
+
+def test_reach_avoid_with_an_obstacle_below_the_value_is_the_brt():
+    # an obstacle that never exceeds the value changes nothing, bit for bit
+    p = inputs.dubins3d(n=(21, 19, 16), horizon=0.7)
+    l = p.target_values()
+    low = np.full(p.n, float(l.min()) - 1.0, dtype=np.float32)
+    ref = oracle.solve(p)
+    ra = oracle.solve(p, g=low)
+    assert np.array_equal(ref["final"], ra["final"])
+    assert np.array_equal(ref["steps"], ra["steps"])
+
+
+@pytest.mark.parametrize("order", [(1, 1), (2, 2)])
+def test_reach_avoid_value_stays_above_the_obstacle(order):
+    # after every step phi >= g; where target and obstacle overlap the obstacle
+    # wins (min with l first, then max with g)
+    p = inputs.reach_avoid(
+        inputs.dubins3d(n=(25, 25, 16), space_order=order[0], time_order=order[1],
+                        tau=tuple(np.linspace(0.0, 1.0, 6))),
+        inputs.cylinder_obstacle(0.8, center=(0.5, 0.0)))
+    g = p.obstacle_values().astype(np.float64)
+    l = p.target_values().astype(np.float64)
+    r = oracle.solve(p, snapshots=True)
+    for snap in r["snapshots"][1:]:
+        assert np.all(snap >= g)
+    both = (g > 0) & (l < 0)
+    assert both.any()
+    assert np.all(r["final"][both] > 0)
+    # the plain tube marks those nodes reachable
+    plain = oracle.solve(inputs.dubins3d(n=(25, 25, 16), space_order=order[0], time_order=order[1],
+                                         tau=tuple(np.linspace(0.0, 1.0, 6))))
+    assert np.all(plain["final"][both] < 0)
+
+
+def test_reach_avoid_obstacle_acts_only_within_its_domain_of_dependence():
+    # the upwind Euler update couples a node to its axis neighbours only and
+    # the single integrator's alpha does not depend on phi, so after s steps
+    # the obstacle can only have changed nodes within L1 distance s (in cells)
+    # of the nodes where it binds
+    n = (31, 29)
+    base = inputs.single_integrator(n, horizon=2.0)
+    obst = inputs.box_obstacle((0.6, -0.4), (1.0, 0.4), dims=(0, 1))
+    ra = inputs.reach_avoid(base, obst)
+    g = ra.obstacle_values().astype(np.float64)
+    l = base.target_values().astype(np.float64)
+    steps = 6
+    plain = oracle.solve(base, max_steps=steps, raise_on_error=False)
+    with_g = oracle.solve(ra, max_steps=steps, raise_on_error=False)
+    assert plain["rc"] == with_g["rc"] == -5   # stopped by the step limit
+    # nodes where the obstacle can bind at some step: g above the smallest value
+    # the plain solve can take there (it only decreases from l)
+    bind = g > plain["final"] - 1e-12
+    bind |= g > l
+    ii, jj = np.nonzero(bind)
+    I, J = np.meshgrid(np.arange(n[0]), np.arange(n[1]), indexing="ij")
+    dist = np.full(n, 10 ** 6)
+    for a, b in zip(ii, jj):
+        dist = np.minimum(dist, np.abs(I - a) + np.abs(J - b))
+    far = dist > steps
+    assert far.sum() > 0.5 * far.size
+    assert np.array_equal(plain["final"][far], with_g["final"][far])
+    near = dist <= steps
+    assert np.abs(plain["final"][near] - with_g["final"][near]).max() > 0
+
+
+def test_reach_avoid_1d_obstacle_blocks_the_far_side():
+    # x' = u, |u| <= 1 on [-4, 4]; target |x| <= 0.5; obstacle [1.5, 2.5].
+    # Without the obstacle x = 3 is reached after t = 2.5; with it every node
+    # at or beyond the obstacle's far face stays out of the reach-avoid set,
+    # while the near side fills in as for the plain tube
+    base = inputs.single_integrator((161,), half_width=4.0, horizon=3.0)
+    ra = inputs.reach_avoid(base, inputs.box_obstacle((1.5,), (2.5,), dims=(0,)))
+    x = base.nodes()[0]
+    plain = oracle.solve(base)["final"]
+    with_g = oracle.solve(ra)["final"]
+    assert plain[np.argmin(np.abs(x - 3.0))] < 0
+    assert np.all(with_g[x >= 2.5 - 1e-9] >= 0)
+    near = (x > -1.3) & (x < 1.3)
+    assert np.all(with_g[near] < 0) and np.all(plain[near] < 0)
