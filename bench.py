@@ -44,7 +44,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("dubinscar4d", "dubins3d", "rel6d", "batch512", "served"),
+    ap.add_argument("--workload", choices=("dubinscar4d", "dubins3d", "rel6d", "dubinscar4d_reach_avoid",
+                                           "batch512", "served"),
                     default="dubinscar4d")
     ap.add_argument("--rates", default="10,30,100,300,1000,2000",
                     help="served workload: Poisson arrival rates (req/s)")
@@ -337,7 +338,9 @@ def run_ours(args):
                        "scheme": "ENO%d + %s" % (problem.space_order,
                                                   "TVD-RK2" if problem.time_order == 2 else "Euler"),
                        "set": problem.set_kind, "cfl": problem.cfl, "horizon": problem.tau[-1],
-                       "l2": "working set (%.0f MB) larger than L2 (129 MB)" % (12.0 * N / 1e6),
+                       "l2": "working set (%.0f MB) larger than L2 (129 MB)" % (
+                           (16.0 if problem.obstacle is not None else 12.0) * N / 1e6),
+                       "reach_avoid": problem.obstacle is not None,
                        "parallelism": "independent solve per GPU",
                        "time_loop": "host-stepped" if args.host_loop else "one CUDA graph"},
             "gpu_launches": launches_per_solve * args.steps,

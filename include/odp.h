@@ -147,6 +147,14 @@ odp_status odp_set_dynamics(odp_grid *g, odp_dyn kind, const double *params, int
  * (asynchronously for device and pinned host memory).  Errors: ODP_EINVAL. */
 odp_status odp_set_target(odp_grid *g, const float *l, int64_t n_elems, int on_device);
 
+/* Reach-avoid obstacle (Section 4.3, the target and obstacle computation
+ * methods): g(z) at every node in C order, positive inside the obstacle.
+ * After each full time step of later solves phi <- max(phi, g), taken after
+ * the tube's min with l.  g is copied like the target (on_device as there);
+ * g == NULL removes the obstacle.  Grids with an obstacle are refused by
+ * odp_batch_solve.  Errors: ODP_EINVAL, ODP_ENOMEM. */
+odp_status odp_set_obstacle(odp_grid *g, const float *gv, int64_t n_elems, int on_device);
+
 /* Limit the number of full time steps of one solve (default 10,000,000).  A
  * solve that reaches the limit stops and reports ODP_ETIMEOUT. */
 odp_status odp_set_step_limit(odp_grid *g, int64_t max_steps);

@@ -171,6 +171,7 @@ __device__ bool batch_item(const BatchGrid &B, int blk, int round, int phase)
         A.dst = B.a;
     }
     A.l = B.l;
+    A.gob = nullptr;
     A.brt = B.brt;
     A.dt = float(round == B.n_steps - 1 ? B.dt_last : B.dt_cfl);
     for (int d = 0; d < ODP_MAXD; ++d) A.cD[d] = B.cD[d];
@@ -331,6 +332,7 @@ extern "C" odp_status odp_batch_solve(odp_grid *const *grids, int n, const doubl
         const odp_grid *g = grids[i];
         if (!g) return fail(ODP_EINVAL, "grid %d is NULL", i);
         if (!g->has_dyn || !g->has_target) return fail(ODP_ESTATE, "grid %d lacks dynamics or target", i);
+        if (g->has_obst) return fail(ODP_EINVAL, "grid %d has an obstacle: the batched solve has no reach-avoid", i);
         if (g->device != device) return fail(ODP_EINVAL, "grid %d is on another device", i);
         if (!(T[i] > 0.0) || !std::isfinite(T[i])) return fail(ODP_EINVAL, "horizon %d must be finite and > 0", i);
         const int k = g->dyn.kind;

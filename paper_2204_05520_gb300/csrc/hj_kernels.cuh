@@ -162,6 +162,7 @@ struct StageArgs {
     const float *src;     // phi the derivatives are taken of
     const float *prev;    // phi^n for the Heun average (stage 2), else unused
     const float *l;       // target, for the BRT min
+    const float *gob;     // obstacle g for the reach-avoid max, or nullptr
     float *dst;
     float cD[ODP_MAXD];   // alpha_d / (2 h_d)
     float dt;
@@ -189,7 +190,7 @@ ODP_HD void segment_axis(const float4 &m2, const float4 &m1, const float4 &c, co
 // (the last stage of a step of a tube).  Returns true if a valid node is not
 // finite.
 ODP_HD bool update_segment(float dt_, int stage, bool use_l, const float4 &c4, const float *L, const float4 &b4,
-                           const float4 &l4, int nvalid, float4 &out)
+                           const float4 &l4, bool use_g, const float4 &g4, int nvalid, float4 &out)
 {
     const float2 dt = f2splat(dt_);
     float2 v01 = f2fma(dt, make_float2(L[0], L[1]), make_float2(c4.x, c4.y));
@@ -210,13 +211,19 @@ ODP_HD bool update_segment(float dt_, int stage, bool use_l, const float4 &c4, c
         out.z = fminf(out.z, l4.z);
         out.w = fminf(out.w, l4.w);
     }
+    if (use_g) {
+        out.x = fmaxf(out.x, g4.x);
+        out.y = fmaxf(out.y, g4.y);
+        out.z = fmaxf(out.z, g4.z);
+        out.w = fmaxf(out.w, g4.w);
+    }
     return bad;
 }
 
 // The same update without a per-node finite test: x - x of every valid
 // updated node (0 when finite, NaN otherwise) is added to fin instead.
 ODP_HD float4 update_nodes(float dt_, int stage, bool use_l, const float4 &c4, const float *L, const float4 &b4,
-                           const float4 &l4, int nvalid, float2 &fin)
+                           const float4 &l4, bool use_g, const float4 &g4, int nvalid, float2 &fin)
 {
     const float2 dt = f2splat(dt_);
     float2 v01 = f2fma(dt, make_float2(L[0], L[1]), make_float2(c4.x, c4.y));
@@ -239,17 +246,25 @@ ODP_HD float4 update_nodes(float dt_, int stage, bool use_l, const float4 &c4, c
         out.z = fminf(out.z, l4.z);
         out.w = fminf(out.w, l4.w);
     }
+    if (use_g) {
+        out.x = fmaxf(out.x, g4.x);
+        out.y = fmaxf(out.y, g4.y);
+        out.z = fmaxf(out.z, g4.z);
+        out.w = fmaxf(out.w, g4.w);
+    }
     return out;
 }
 
-// update_segment with phi^n and l read at storage offset base.
+// update_segment with phi^n, l and the obstacle read at storage offset base.
 ODP_HD bool stage_epilogue(const StageArgs &A, int base, const float4 &c4, const float *L, int nvalid, float4 &out)
 {
-    float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f), l4 = b4;
+    float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f), l4 = b4, g4 = b4;
     if (A.stage == 2) b4 = *reinterpret_cast<const float4 *>(A.prev + base);
     const bool use_l = A.brt && A.stage != 1;
     if (use_l) l4 = ldg4(A.l + base);
-    return update_segment(A.dt, A.stage, use_l, c4, L, b4, l4, nvalid, out);
+    const bool use_g = A.gob != nullptr && A.stage != 1;
+    if (use_g) g4 = ldg4(A.gob + base);
+    return update_segment(A.dt, A.stage, use_l, c4, L, b4, l4, use_g, g4, nvalid, out);
 }
 
 // Row j (possibly outside [0, n)) of axis `axis` relative to row i0 of the
@@ -401,13 +416,15 @@ ODP_HD bool stage_tile(const GridDesc &g, const DynDesc &dy, const StageArgs &A,
 // solve state.
 template <int ND, int ORDER, int DYN, int R>
 __global__ void __launch_bounds__(256) k_stage(GridDesc g, DynDesc dy, SolveState *st,
-                                               const float *__restrict__ l, int stage, int brt)
+                                               const float *__restrict__ l, const float *__restrict__ gob,
+                                               int stage, int brt)
 {
     StageArgs A;
     A.src = (stage == 2) ? st->nxt : st->cur;
     A.prev = st->cur;
     A.dst = (stage == 2) ? st->cur : st->nxt;
     A.l = l;
+    A.gob = gob;
     const unsigned *ab = st->alpha_bits[stage == 2 ? 1 : 0];
 #pragma unroll
     for (int d = 0; d < ND; ++d) A.cD[d] = 0.5f * bits_to_float(ab[d]) * g.inv_dz[d];
@@ -545,42 +562,57 @@ namespace odp {
 
 template <int ND, int DYN>
 cudaError_t launch_stage_t(const GridDesc &g, const DynDesc &dy, SolveState *st, const float *l,
-                           int order, int stage, int brt, cudaStream_t s)
+                           const float *gob, int order, int stage, int brt, cudaStream_t s)
 {
     if constexpr (ND >= 3) {
         if (g.pg.use) {
             // Dubins3D, DubinsCar4D and Rel6D grids whose last axis is a
-            // multiple of 4 get one kernel per RK stage; the other models and
-            // shapes take the stage at run time
+            // multiple of 4 get one kernel per RK stage and obstacle use; the
+            // other models and shapes take both at run time
             const int blocks = g.pg.items, th = g.pg.threads, sm = g.pg.smem[order - 1];
             const bool full = g.n[ND - 1] % 4 == 0;
             constexpr bool SPEC = DYN == DYN_DUBINS3D || DYN == DYN_DUBINSCAR4D || DYN == DYN_REL6D;
             if (SPEC && full) {
+                const bool ob = gob != nullptr;
                 if (order == 1) {
-                    if (stage == 0)
-                        k_stage_plane<ND, 1, DYN, true, 0><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
-                    else if (stage == 1)
-                        k_stage_plane<ND, 1, DYN, true, 1><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
-                    else
-                        k_stage_plane<ND, 1, DYN, true, 2><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
+                    if (stage == 0) {
+                        if (ob)
+                            k_stage_plane<ND, 1, DYN, true, 0, 1><<<blocks, th, sm, s>>>(g, dy, st, l, gob, stage, brt);
+                        else
+                            k_stage_plane<ND, 1, DYN, true, 0, 0><<<blocks, th, sm, s>>>(g, dy, st, l, gob, stage, brt);
+                    } else if (stage == 1) {
+                        k_stage_plane<ND, 1, DYN, true, 1, 0><<<blocks, th, sm, s>>>(g, dy, st, l, gob, stage, brt);
+                    } else {
+                        if (ob)
+                            k_stage_plane<ND, 1, DYN, true, 2, 1><<<blocks, th, sm, s>>>(g, dy, st, l, gob, stage, brt);
+                        else
+                            k_stage_plane<ND, 1, DYN, true, 2, 0><<<blocks, th, sm, s>>>(g, dy, st, l, gob, stage, brt);
+                    }
                 } else {
-                    if (stage == 0)
-                        k_stage_plane<ND, 2, DYN, true, 0><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
-                    else if (stage == 1)
-                        k_stage_plane<ND, 2, DYN, true, 1><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
-                    else
-                        k_stage_plane<ND, 2, DYN, true, 2><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
+                    if (stage == 0) {
+                        if (ob)
+                            k_stage_plane<ND, 2, DYN, true, 0, 1><<<blocks, th, sm, s>>>(g, dy, st, l, gob, stage, brt);
+                        else
+                            k_stage_plane<ND, 2, DYN, true, 0, 0><<<blocks, th, sm, s>>>(g, dy, st, l, gob, stage, brt);
+                    } else if (stage == 1) {
+                        k_stage_plane<ND, 2, DYN, true, 1, 0><<<blocks, th, sm, s>>>(g, dy, st, l, gob, stage, brt);
+                    } else {
+                        if (ob)
+                            k_stage_plane<ND, 2, DYN, true, 2, 1><<<blocks, th, sm, s>>>(g, dy, st, l, gob, stage, brt);
+                        else
+                            k_stage_plane<ND, 2, DYN, true, 2, 0><<<blocks, th, sm, s>>>(g, dy, st, l, gob, stage, brt);
+                    }
                 }
             } else if (order == 1) {
                 if (full)
-                    k_stage_plane<ND, 1, DYN, true, -1><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
+                    k_stage_plane<ND, 1, DYN, true, -1, -1><<<blocks, th, sm, s>>>(g, dy, st, l, gob, stage, brt);
                 else
-                    k_stage_plane<ND, 1, DYN, false, -1><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
+                    k_stage_plane<ND, 1, DYN, false, -1, -1><<<blocks, th, sm, s>>>(g, dy, st, l, gob, stage, brt);
             } else {
                 if (full)
-                    k_stage_plane<ND, 2, DYN, true, -1><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
+                    k_stage_plane<ND, 2, DYN, true, -1, -1><<<blocks, th, sm, s>>>(g, dy, st, l, gob, stage, brt);
                 else
-                    k_stage_plane<ND, 2, DYN, false, -1><<<blocks, th, sm, s>>>(g, dy, st, l, stage, brt);
+                    k_stage_plane<ND, 2, DYN, false, -1, -1><<<blocks, th, sm, s>>>(g, dy, st, l, gob, stage, brt);
             }
             return cudaGetLastError();
         }
@@ -588,14 +620,14 @@ cudaError_t launch_stage_t(const GridDesc &g, const DynDesc &dy, SolveState *st,
     const int grid = blocks_for(g.nthreads_rb, 256), block = 256;
     if (g.R == 4) {
         if (order == 1)
-            k_stage<ND, 1, DYN, 4><<<grid, block, 0, s>>>(g, dy, st, l, stage, brt);
+            k_stage<ND, 1, DYN, 4><<<grid, block, 0, s>>>(g, dy, st, l, gob, stage, brt);
         else
-            k_stage<ND, 2, DYN, 4><<<grid, block, 0, s>>>(g, dy, st, l, stage, brt);
+            k_stage<ND, 2, DYN, 4><<<grid, block, 0, s>>>(g, dy, st, l, gob, stage, brt);
     } else {
         if (order == 1)
-            k_stage<ND, 1, DYN, 1><<<grid, block, 0, s>>>(g, dy, st, l, stage, brt);
+            k_stage<ND, 1, DYN, 1><<<grid, block, 0, s>>>(g, dy, st, l, gob, stage, brt);
         else
-            k_stage<ND, 2, DYN, 1><<<grid, block, 0, s>>>(g, dy, st, l, stage, brt);
+            k_stage<ND, 2, DYN, 1><<<grid, block, 0, s>>>(g, dy, st, l, gob, stage, brt);
     }
     return cudaGetLastError();
 }

@@ -61,7 +61,8 @@ __device__ __forceinline__ float4 ghost4(const float4 &pb, const float4 &pi, flo
 // periodic last axis is read at the wrapped columns of the tile row, ghost
 // columns are formed from the segment's own values; otherwise the row's
 // first and last segments write them into the tile one plane ahead.
-// STAGE >= 0 fixes the RK stage at compile time (-1: the stage_rt argument).
+// STAGE >= 0 fixes the RK stage at compile time (-1: the stage_rt argument);
+// GOB = 0 / 1 fixes whether an obstacle is applied (-1: gob != nullptr).
 // Non-finite values are detected by accumulating x - x over the updated nodes
 // (0 for finite x, NaN otherwise) and testing the sum once at the end.
 // Register budget per model and order, chosen so that whole CTAs fill the
@@ -82,9 +83,10 @@ constexpr bool plane_late_outer_loads()
     return DYN == DYN_DUBINSCAR4D && ORDER == 2;
 }
 
-template <int ND, int ORDER, int DYN, bool FULL, int STAGE>
+template <int ND, int ORDER, int DYN, bool FULL, int STAGE, int GOB>
 __global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DYN>())) k_stage_plane(GridDesc g, DynDesc dy, SolveState *st,
-                                                     const float *__restrict__ l, int stage_rt, int brt)
+                                                     const float *__restrict__ l,
+                                                     const float *__restrict__ gob, int stage_rt, int brt)
 {
     const int stage = STAGE >= 0 ? STAGE : stage_rt;
     const PlaneGeom &pg = g.pg;
@@ -106,6 +108,7 @@ __global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DY
     for (int d = 0; d < ND; ++d) cD[d] = 0.5f * bits_to_float(ab[d]) * g.inv_dz[d];
     const float dt = float(st->dt);
     const bool use_l = brt && stage != 1;
+    const bool use_g = (GOB >= 0 ? GOB == 1 : gob != nullptr) && stage != 1;   // reach-avoid obstacle
 
     // work item: chunk fastest, then band, then outer pencil.  Outer pencils
     // are numbered block by block (blocks of up to 8 indices per outer axis),
@@ -262,7 +265,7 @@ __global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DY
             const int gi = base + s * plane;
             const float4 c4 = w[(u + O) % Q];
             float4 nb[NOUT > 0 ? NOUT : 1][2 * O];
-            float4 lx = make_float4(0.f, 0.f, 0.f, 0.f), px = lx, nx = lx;
+            float4 lx = make_float4(0.f, 0.f, 0.f, 0.f), px = lx, nx = lx, gx = lx;
             if (active) {
                 *reinterpret_cast<float4 *>(T + so) = c4;
                 if (hrow_duty) *reinterpret_cast<float4 *>(T + hso) = hx;
@@ -282,9 +285,11 @@ __global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DY
                     for (int d = 0; d < NOUT; ++d)
 #pragma unroll
                         for (int k = 0; k < 2 * O; ++k)
-                            nb[d][k] = INNER ? ldg4(src + gi + (k < O ? k - O : k - O + 1) * g.stride[d]) : nb_value(src, gi, nbq[d][k]);
+                            nb[d][k] = INNER ? ldg4(src + gi + (k < O ? k - O : k - O + 1) * g.stride[d])
+                                             : nb_value(src, gi, nbq[d][k]);
                 }
                 if (use_l) lx = ldg4(l + gi);
+                if (use_g) gx = ldg4(gob + gi);
                 if (stage == 2) px = *reinterpret_cast<const float4 *>(prev + gi);
                 if (s + 1 < s_end) {
                     nx = stream_value(src, base, s + 1 + O, ns, per_s, plane);
@@ -304,7 +309,8 @@ __global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DY
                     for (int d = 0; d < NOUT; ++d)
 #pragma unroll
                         for (int k = 0; k < 2 * O; ++k)
-                            nb[d][k] = INNER ? ldg4(src + gi + (k < O ? k - O : k - O + 1) * g.stride[d]) : nb_value(src, gi, nbq[d][k]);
+                            nb[d][k] = INNER ? ldg4(src + gi + (k < O ? k - O : k - O + 1) * g.stride[d])
+                                             : nb_value(src, gi, nbq[d][k]);
                 }
                 const float *C = T + so;
                 float2 L01 = make_float2(0.0f, 0.0f), L23 = make_float2(0.0f, 0.0f);
@@ -360,7 +366,7 @@ __global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DY
                     axis_last<ORDER>(v, cA[ND - 1], cS[ND - 1], cD[ND - 1], L, has_drift<DYN, ND>(ND - 1),
                                      has_bound<DYN, ND>(ND - 1));
                 }
-                float4 out = update_nodes(dt, stage, use_l, c4, L, px, lx, nvalid, fin);
+                float4 out = update_nodes(dt, stage, use_l, c4, L, px, lx, use_g, gx, nvalid, fin);
                 if (FULL || nvalid == 4) {
                     *reinterpret_cast<float4 *>(dst + gi) = out;
                 } else {

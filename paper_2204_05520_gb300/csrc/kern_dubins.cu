@@ -5,10 +5,10 @@
 namespace odp {
 
 cudaError_t launch_stage_dubins(int nd, const GridDesc &g, const DynDesc &dy, SolveState *st,
-                                const float *l, int order, int stage, int brt, cudaStream_t s)
+                                const float *l, const float *gob, int order, int stage, int brt, cudaStream_t s)
 {
-    if (nd == 3) return launch_stage_t<3, DYN_DUBINS3D>(g, dy, st, l, order, stage, brt, s);
-    return launch_stage_t<4, DYN_DUBINSCAR4D>(g, dy, st, l, order, stage, brt, s);
+    if (nd == 3) return launch_stage_t<3, DYN_DUBINS3D>(g, dy, st, l, gob, order, stage, brt, s);
+    return launch_stage_t<4, DYN_DUBINSCAR4D>(g, dy, st, l, gob, order, stage, brt, s);
 }
 
 cudaError_t configure_stage_dubins(int nd)

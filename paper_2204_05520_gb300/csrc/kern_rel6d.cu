@@ -5,9 +5,9 @@
 namespace odp {
 
 cudaError_t launch_stage_rel6d(const GridDesc &g, const DynDesc &dy, SolveState *st,
-                               const float *l, int order, int stage, int brt, cudaStream_t s)
+                               const float *l, const float *gob, int order, int stage, int brt, cudaStream_t s)
 {
-    return launch_stage_t<6, DYN_REL6D>(g, dy, st, l, order, stage, brt, s);
+    return launch_stage_t<6, DYN_REL6D>(g, dy, st, l, gob, order, stage, brt, s);
 }
 
 cudaError_t configure_stage_rel6d() { return configure_stage_t<6, DYN_REL6D>(); }

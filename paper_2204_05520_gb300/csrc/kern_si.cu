@@ -25,9 +25,9 @@ ODP_SI_EXTERN(6)
     }
 
 cudaError_t launch_stage_si(int nd, const GridDesc &g, const DynDesc &dy, SolveState *st,
-                            const float *l, int order, int stage, int brt, cudaStream_t s)
+                            const float *l, const float *gob, int order, int stage, int brt, cudaStream_t s)
 {
-    ODP_ND_SWITCH(nd, (launch_stage_si_nd<ND>(g, dy, st, l, order, stage, brt, s)))
+    ODP_ND_SWITCH(nd, (launch_stage_si_nd<ND>(g, dy, st, l, gob, order, stage, brt, s)))
 }
 
 cudaError_t configure_stage_si(int nd, int kind)

@@ -9,11 +9,11 @@
 namespace odp {
 
 template <int ND>
-cudaError_t launch_stage_si_nd(const GridDesc &g, const DynDesc &dy, SolveState *st, const float *l, int order,
-                               int stage, int brt, cudaStream_t s)
+cudaError_t launch_stage_si_nd(const GridDesc &g, const DynDesc &dy, SolveState *st, const float *l,
+                               const float *gob, int order, int stage, int brt, cudaStream_t s)
 {
-    if (dy.kind == DYN_SINGLE_INT) return launch_stage_t<ND, DYN_SINGLE_INT>(g, dy, st, l, order, stage, brt, s);
-    return launch_stage_t<ND, DYN_ADVECTION>(g, dy, st, l, order, stage, brt, s);
+    if (dy.kind == DYN_SINGLE_INT) return launch_stage_t<ND, DYN_SINGLE_INT>(g, dy, st, l, gob, order, stage, brt, s);
+    return launch_stage_t<ND, DYN_ADVECTION>(g, dy, st, l, gob, order, stage, brt, s);
 }
 
 template <int ND>
@@ -32,14 +32,15 @@ cudaError_t launch_alpha_static_si_nd(const GridDesc &g, const DynDesc &dy, Solv
 
 #define ODP_SI_INSTANTIATE(ND)                                                                               \
     template cudaError_t launch_stage_si_nd<ND>(const GridDesc &, const DynDesc &, SolveState *, const float *, \
-                                                int, int, int, cudaStream_t);                                 \
+                                                const float *, int, int, int, cudaStream_t);                  \
     template cudaError_t configure_stage_si_nd<ND>(int);                                                      \
     template cudaError_t launch_alpha_static_si_nd<ND>(const GridDesc &, const DynDesc &, SolveState *,       \
                                                        cudaStream_t);
 
 #define ODP_SI_EXTERN(ND)                                                                                     \
     extern template cudaError_t launch_stage_si_nd<ND>(const GridDesc &, const DynDesc &, SolveState *,       \
-                                                       const float *, int, int, int, cudaStream_t);           \
+                                                       const float *, const float *, int, int, int,           \
+                                                       cudaStream_t);                                         \
     extern template cudaError_t configure_stage_si_nd<ND>(int);                                               \
     extern template cudaError_t launch_alpha_static_si_nd<ND>(const GridDesc &, const DynDesc &, SolveState *, \
                                                               cudaStream_t);

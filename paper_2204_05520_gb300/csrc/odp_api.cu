@@ -218,6 +218,7 @@ static void release(odp_grid *g)
     cudaFree(g->phi_a);
     cudaFree(g->phi_b);
     cudaFree(g->l);
+    cudaFree(g->obst);
     cudaFree(g->tables);
     cudaFree(g->state);
     cudaFree(g->tau);
@@ -465,6 +466,32 @@ extern "C" odp_status odp_set_target(odp_grid *g, const float *l, int64_t n_elem
     return ODP_OK;
 }
 
+extern "C" odp_status odp_set_obstacle(odp_grid *g, const float *gv, int64_t n_elems, int on_device)
+{
+    if (!g) return fail(ODP_EINVAL, "grid is NULL");
+    if (!gv) {
+        g->has_obst = false;
+        return ODP_OK;
+    }
+    ODP_BIND(g);
+    if (n_elems != g->total) return fail(ODP_EINVAL, "obstacle has %lld values, grid has %lld",
+                                         (long long)n_elems, (long long)g->total);
+    if (!g->obst) {
+        const size_t bytes = size_t(g->total_pad) * sizeof(float);
+        if (cudaMalloc(&g->obst, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            g->obst = nullptr;
+            return fail(ODP_ENOMEM, "obstacle array of %zu bytes", bytes);
+        }
+        ODP_CUDA(cudaMemsetAsync(g->obst, 0, bytes, g->stream));
+    }
+    ODP_CUDA(cudaMemcpy2DAsync(g->obst, size_t(g->n_pad) * sizeof(float), gv, size_t(g->n_last) * sizeof(float),
+                               size_t(g->n_last) * sizeof(float), size_t(g->rows),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));
+    g->has_obst = true;
+    return ODP_OK;
+}
+
 extern "C" odp_status odp_set_step_limit(odp_grid *g, int64_t max_steps)
 {
     if (!g || max_steps < 1) return fail(ODP_EINVAL, "need a grid and max_steps >= 1");
@@ -480,15 +507,16 @@ static unsigned dynamic_alpha_mask(const odp_grid *g) { return g->dyn.kind == DY
 static cudaError_t launch_stage_any(odp_grid *g, int stage, cudaStream_t s)
 {
     const GridDesc &D = g->desc;
+    const float *gob = g->has_obst ? g->obst : nullptr;
     switch (g->dyn.kind) {
     case DYN_SINGLE_INT:
     case DYN_ADVECTION:
-        return launch_stage_si(g->ndim, D, g->dyn, g->state, g->l, g->order, stage, g->brt, s);
+        return launch_stage_si(g->ndim, D, g->dyn, g->state, g->l, gob, g->order, stage, g->brt, s);
     case DYN_DUBINS3D:
     case DYN_DUBINSCAR4D:
-        return launch_stage_dubins(g->ndim, D, g->dyn, g->state, g->l, g->order, stage, g->brt, s);
+        return launch_stage_dubins(g->ndim, D, g->dyn, g->state, g->l, gob, g->order, stage, g->brt, s);
     default:
-        return launch_stage_rel6d(D, g->dyn, g->state, g->l, g->order, stage, g->brt, s);
+        return launch_stage_rel6d(D, g->dyn, g->state, g->l, gob, g->order, stage, g->brt, s);
     }
 }
 
@@ -710,6 +738,7 @@ extern "C" odp_status odp_solve_hjb(odp_grid *g, const double *tau, int n_tau, o
     key.time_order = time_order;
     key.brt = g->brt;
     key.keep = g->keep;
+    key.obstacle = g->has_obst ? 1 : 0;
     key.dyn_version = g->dyn_version;
     if (!g->exec || !(key == g->key)) {
         odp_status rc = build_graph(g);
@@ -789,10 +818,12 @@ extern "C" odp_status odp_solve_status(odp_grid *g, odp_solve_stats *stats)
         }
         // algorithmic HBM bytes per node per step: every stage reads phi once
         // and writes its result; stage 2 also reads phi^n; the last stage of a
-        // tube reads l; Rel6D adds one read of phi per stage for its alpha.
+        // tube reads l (and the obstacle of a reach-avoid solve); Rel6D adds
+        // one read of phi per stage for its alpha.
         const double per_stage_rw = 8.0;
         double b = (g->time_order == 1) ? per_stage_rw : (2 * per_stage_rw + 4.0);
         if (g->brt) b += 4.0;
+        if (g->has_obst) b += 4.0;
         if (g->dyn.kind == DYN_REL6D) b += 4.0 * g->time_order;
         stats->bytes = b * double(g->total) * double(h.steps);
         stats->launches = g->launches_per_step * h.steps;

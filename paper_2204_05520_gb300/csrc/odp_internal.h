@@ -16,12 +16,12 @@ odp_status fail(odp_status code, const char *fmt, ...);
 // Kernel arguments (grid and dynamics descriptors) are frozen into the graph
 // when it is captured, so any change of scheme or dynamics rebuilds it.
 struct GraphKey {
-    int order = 0, time_order = 0, brt = 0, keep = 0;
+    int order = 0, time_order = 0, brt = 0, keep = 0, obstacle = 0;
     long long dyn_version = -1;
     bool operator==(const GraphKey &o) const
     {
         return order == o.order && time_order == o.time_order && brt == o.brt && keep == o.keep &&
-               dyn_version == o.dyn_version;
+               obstacle == o.obstacle && dyn_version == o.dyn_version;
     }
 };
 
@@ -38,6 +38,8 @@ struct odp_grid {
     int device = 0;
 
     float *phi_a = nullptr, *phi_b = nullptr, *l = nullptr;
+    float *obst = nullptr;            // reach-avoid obstacle g (allocated on first use)
+    bool has_obst = false;
     float *tables = nullptr;          // all node-coordinate and trig tables
     odp::SolveState *state = nullptr;
     double *tau = nullptr;

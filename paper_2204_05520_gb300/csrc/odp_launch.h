@@ -7,13 +7,14 @@
 
 namespace odp {
 
-// One fused stage pass (K2) over the whole grid.
+// One fused stage pass (K2) over the whole grid; gob is the reach-avoid
+// obstacle (nullptr: none).
 cudaError_t launch_stage_si(int nd, const GridDesc &g, const DynDesc &dy, SolveState *st,
-                            const float *l, int order, int stage, int brt, cudaStream_t s);
+                            const float *l, const float *gob, int order, int stage, int brt, cudaStream_t s);
 cudaError_t launch_stage_dubins(int nd, const GridDesc &g, const DynDesc &dy, SolveState *st,
-                                const float *l, int order, int stage, int brt, cudaStream_t s);
+                                const float *l, const float *gob, int order, int stage, int brt, cudaStream_t s);
 cudaError_t launch_stage_rel6d(const GridDesc &g, const DynDesc &dy, SolveState *st,
-                               const float *l, int order, int stage, int brt, cudaStream_t s);
+                               const float *l, const float *gob, int order, int stage, int brt, cudaStream_t s);
 
 // Shared-memory limits of the plane-streaming kernels of a model (call before
 // launching or capturing them on the current device).

@@ -175,6 +175,7 @@ __device__ bool serve_item(const ServeGrid &B, int blk, int step, int phase)
         A.dst = B.a;
     }
     A.l = B.l;
+    A.gob = nullptr;
     A.brt = B.brt;
     A.dt = float(step == B.n_steps - 1 ? B.dt_last : B.dt_cfl);
     for (int d = 0; d < ODP_MAXD; ++d) A.cD[d] = B.cD[d];

@@ -107,6 +107,7 @@ def load():
             "odp_grid_points": ([P], i64),
             "odp_set_dynamics": ([P, i32, P, i32, i32, i32], i32),
             "odp_set_target": ([P, P, i64, i32], i32),
+            "odp_set_obstacle": ([P, P, i64, i32], i32),
             "odp_set_step_limit": ([P, i64], i32),
             "odp_set_loop_mode": ([P, i32], i32),
             "odp_solve_hjb": ([P, P, i32, i32, i32, i32, f64, i32, P], i32),
@@ -208,6 +209,17 @@ def set_target(g, l):
     n = grid_points(g)
     ptr, dev = _buffer(l, n, writable=False)
     _check(load().odp_set_target(g, ptr, n, dev), "odp_set_target")
+
+
+def set_obstacle(g, gv):
+    """Reach-avoid obstacle g(z) (float32 array or tensor of the grid's
+    shape), or None to remove it."""
+    if gv is None:
+        _check(load().odp_set_obstacle(g, None, 0, 0), "odp_set_obstacle")
+        return
+    n = grid_points(g)
+    ptr, dev = _buffer(gv, n, writable=False)
+    _check(load().odp_set_obstacle(g, ptr, n, dev), "odp_set_obstacle")
 
 
 def set_step_limit(g, max_steps: int):
@@ -386,6 +398,8 @@ class Grid:
     def for_problem(cls, problem, stream=None) -> "Grid":
         g = cls(problem.n, problem.lo, problem.hi, problem.periodic, stream)
         set_dynamics(g.handle, problem.dynamics, problem.params, problem.u_mode, problem.d_mode)
+        if getattr(problem, "obstacle", None) is not None:
+            set_obstacle(g.handle, problem.obstacle_values())
         return g
 
     def close(self):
@@ -407,6 +421,9 @@ class Grid:
 
     def set_target(self, l):
         set_target(self.handle, l)
+
+    def set_obstacle(self, gv):
+        set_obstacle(self.handle, gv)
 
     def solve(self, tau, set_kind="brt", space_order=1, time_order=1, cfl=0.8,
               keep_snapshots=False, stats=False):

@@ -295,3 +295,63 @@ def test_host_stepped_loop_equals_graph_loop(problem):
     assert res[0][0] == res[1][0] > 0
     for a, b in zip(res[0][1], res[1][1]):
         assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------------------
+# reach-avoid: phi <- max(min(phi, l), g) after each step
+# ---------------------------------------------------------------------------
+
+RA_CASES = [
+    inputs.reach_avoid(inputs.dubins3d(n=(41, 41, 36)), inputs.dubins_obstacle()),
+    inputs.reach_avoid(inputs.dubins3d(n=(25, 27, 20), tau=(0.0, 0.4, 1.0, 1.6)),
+                       inputs.cylinder_obstacle(0.8, center=(0.5, 0.0))),
+    inputs.reach_avoid(inputs.single_integrator((37, 29), horizon=1.5),
+                       inputs.box_obstacle((0.6, -0.4), (1.0, 0.4), dims=(0, 1))),
+    inputs.reach_avoid(inputs.dubinscar4d(n=(21, 19, 11, 16), horizon=1.0), inputs.dubins_obstacle()),
+    inputs.reach_avoid(inputs.rel6d(n=(9, 8, 10, 5, 4, 3), horizon=0.3),
+                       inputs.box_obstacle((0.0, -1.5), (2.0, 1.5), dims=(0, 1))),
+]
+
+
+@pytest.mark.parametrize("problem", RA_CASES, ids=lambda p: "%s_o%d%d" % (p.name, p.space_order, p.time_order))
+def test_reach_avoid_matches_oracle(problem):
+    check(problem)
+
+
+def test_reach_avoid_full_size_step_matches_oracle():
+    p = inputs.workload("dubinscar4d_reach_avoid")   # 80x80x40x64, ENO2 + RK2, obstacle
+    rel, phi_b, _ = one_step_at_full_size(p, t_a=1.0)
+    assert rel <= REL_TOL
+    assert (phi_b >= p.obstacle_values()).all()
+
+
+def test_removing_the_obstacle_restores_the_plain_tube():
+    import torch
+
+    p = inputs.dubins3d(n=(21, 23, 16), horizon=0.8)
+    l = torch.from_numpy(p.target_values()).cuda()
+    g_vals = inputs.reach_avoid(p, inputs.dubins_obstacle()).obstacle_values()
+    out = []
+    for obst in (None, g_vals, None):
+        with odp.Grid.for_problem(p) as g:
+            g.set_target(l)
+            g.set_obstacle(g_vals)
+            g.set_obstacle(obst)
+            g.solve_problem(p)
+            out.append(g.readback(torch.empty_like(l)).cpu().numpy())
+    assert np.array_equal(out[0], out[2])
+    assert not np.array_equal(out[0], out[1])
+
+
+def test_obstacle_arguments_are_checked():
+    p = inputs.dubins3d(n=(9, 9, 8))
+    with odp.Grid.for_problem(p) as g:
+        with pytest.raises(ValueError):   # the binding checks the size first
+            g.set_obstacle(np.zeros((9, 9, 7), np.float32))
+        arr = np.zeros(p.n, np.float32)
+        assert odp.load().odp_set_obstacle(g.handle, arr.ctypes.data, arr.size - 1, 0) == odp.EINVAL
+        g.set_target(p.target_values())
+        g.set_obstacle(np.zeros(p.n, np.float32))
+        with pytest.raises(odp.OdpError) as e:
+            odp.batch_solve([g], [0.5])
+        assert e.value.code == odp.EINVAL
