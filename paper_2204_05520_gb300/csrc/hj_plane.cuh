@@ -223,6 +223,13 @@ __global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DY
     idx[ND - 2] = r;
     idx[ND - 1] = s0;
     drift<DYN, ND>(g, dy, idx, cA, cS);
+    // the budget-capped passes keep the two drift rows in shared memory
+    // (after the two tiles, 32 bytes per thread) and reload them each plane
+    float4 *cA_sm = reinterpret_cast<float4 *>(smem + 2 * tile) + 2 * tid;
+    if (LATE) {
+        cA_sm[0] = make_float4(cA[0][0], cA[0][1], cA[0][2], cA[0][3]);
+        cA_sm[1] = make_float4(cA[1][0], cA[1][1], cA[1][2], cA[1][3]);
+    }
     float4 rx_ve = make_float4(0.f, 0.f, 0.f, 0.f);
     float rx_c = 0.f, rx_wp = 0.f, rx_y = 0.f;
     if (DYN == DYN_REL6D) {
@@ -315,6 +322,17 @@ __global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DY
                 const float *C = T + so;
                 float2 L01 = make_float2(0.0f, 0.0f), L23 = make_float2(0.0f, 0.0f);
                 // outer axes
+                if (LATE) {
+                    const float4 a0 = cA_sm[0], a1 = cA_sm[1];
+                    cA[0][0] = a0.x;
+                    cA[0][1] = a0.y;
+                    cA[0][2] = a0.z;
+                    cA[0][3] = a0.w;
+                    cA[1][0] = a1.x;
+                    cA[1][1] = a1.y;
+                    cA[1][2] = a1.z;
+                    cA[1][3] = a1.w;
+                }
 #pragma unroll
                 for (int d = 0; d < NOUT; ++d)
                     segment_axis<ORDER>(nb[d][0], nb[d][O - 1], c4, nb[d][O], nb[d][2 * O - 1], cA[d], cS[d],

@@ -168,7 +168,13 @@ static void plane_geometry(GridDesc &D, int sms)
     pg.threads = threads;
     pg.plane = nr * D.n_pad;
     pg.cp = D.n_pad + 4;
-    for (int o = 1; o <= 2; ++o) pg.smem[o - 1] = 2 * (4 + (rb + 2 * o) * pg.cp) * 4;
+    // two tiles, then 32 bytes per thread for the drift rows of the
+    // register-capped passes
+    for (int o = 1; o <= 2; ++o) pg.smem[o - 1] = 2 * (4 + (rb + 2 * o) * pg.cp) * 4 + threads * 32;
+    if (pg.smem[1] > 48 * 1024) {   // beyond the default dynamic shared memory of a CTA
+        pg = PlaneGeom{};
+        return;
+    }
     pg.ns = D.n[D.ndim - 3];
     long long pencils = 1;
     for (int d = 0; d < D.ndim - 3; ++d) pencils *= D.n[d];
