@@ -69,9 +69,9 @@ def _load():
             lib.og_terms.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, i32, P, P,
                                      P, P, P, P, P, P, P, P]
             lib.og_solve.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, P, P, P, i32, i32,
-                                     i32, i32, f64, i64, P, P, P, P, P]
+                                     i32, i32, i32, f64, i64, P, P, P, P, P]
             lib.og_step.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, P, P, f64, i32, i32,
-                                    i32, P, P]
+                                    i32, i32, P, P]
             for f in (lib.og_spacing, lib.og_eval_dynamics, lib.og_terms, lib.og_solve,
                       lib.og_step):
                 f.restype = i32
@@ -191,6 +191,11 @@ def _obstacle(problem, g):
     return None if g is None else np.ascontiguousarray(g, dtype=np.float64).reshape(-1)
 
 
+def _local(problem) -> int:
+    """1 when the problem asks for per-node dissipation (reading R18)."""
+    return 1 if getattr(problem, "dissipation", "global") == "local" else 0
+
+
 def step(problem, phi, dt, l=None, g=None) -> dict:
     """One full time step of size ``dt`` from ``phi`` (float64 copy taken),
     as ``solve`` takes it.  Returns dict(out, alpha) with alpha of stage 1."""
@@ -209,7 +214,7 @@ def step(problem, phi, dt, l=None, g=None) -> dict:
                      DYN_IDS[p.dynamics], _ptr(prm), len(prm), MODE_IDS[p.u_mode],
                      MODE_IDS[p.d_mode], _ptr(l64), _ptr(g64), _ptr(phi64), float(dt),
                      SET_IDS[p.set_kind],
-                     p.space_order, p.time_order, _ptr(out), _ptr(alpha))
+                     p.space_order, p.time_order, _local(p), _ptr(out), _ptr(alpha))
     if rc:
         raise OracleError(rc, "step")
     return {"out": out.reshape(tuple(p.n)), "alpha": alpha}
@@ -246,7 +251,7 @@ def solve(problem, l=None, snapshots: bool = False, max_steps: int = 10_000_000,
                       DYN_IDS[p.dynamics], _ptr(prm), len(prm), MODE_IDS[p.u_mode],
                       MODE_IDS[p.d_mode], _ptr(l64), _ptr(g64), _ptr(p0), _ptr(tau), len(tau),
                       SET_IDS[p.set_kind],
-                      p.space_order, p.time_order, float(p.cfl), int(max_steps), _ptr(snaps),
+                      p.space_order, p.time_order, _local(p), float(p.cfl), int(max_steps), _ptr(snaps),
                       _ptr(final), _ptr(steps), _ptr(alpha), ctypes.byref(last_dt))
     if rc and raise_on_error:
         raise OracleError(rc, "solve")

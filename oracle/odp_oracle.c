@@ -33,6 +33,10 @@
  *     the stage-1 alpha, stage 2 uses its own alpha.  BRT min once per step.
  *  R9 ghost cells on non-periodic axes: k cells outside the boundary point b,
  *     g_k = phi_b + k*sign(phi_b)*|phi_b - phi_inner|, sign(0) = +1.
+ *  R18 per-node alpha (Algorithm 1's second loop, kept as an option): the
+ *     dissipation of node i uses alpha_i, the local bound of R5 at that node
+ *     (its own derivative box), instead of the grid maximum; the CFL step
+ *     still uses the grid maximum.
  *  R17 reach-avoid (Section 4.3, the target and obstacle computation
  *     methods): with an obstacle function g, after each full step
  *     phi <- max(phi, g), taken after the BRT min with l (target first, then
@@ -410,9 +414,11 @@ static void og_alpha(const og_grid *g, const og_dyn *dy, const double *phi, int 
 }
 
 /* Second pass: the Lax-Friedrichs right-hand side at every node,
- * L = H(pbar) + 1/2 sum_d alpha_d (p+_d - p-_d)  (Algorithm 1, reading R2). */
+ * L = H(pbar) + 1/2 sum_d alpha_d (p+_d - p-_d)  (Algorithm 1, reading R2),
+ * with the grid alpha, or with the node's own alpha_i when local is set
+ * (reading R18). */
 static void og_rhs(const og_grid *g, const og_dyn *dy, const double *phi, int order,
-                   const double *alpha, double *L)
+                   const double *alpha, int local, double *L)
 {
     int nd = g->ndim;
 #pragma omp parallel for schedule(static)
@@ -426,8 +432,17 @@ static void og_rhs(const og_grid *g, const og_dyn *dy, const double *phi, int or
             pbar[d] = 0.5 * (pp[d] + pm[d]);
         }
         double h = og_hamiltonian(dy, z, pbar);
+        double a_loc[OG_MAXD];
+        if (local) {
+            double lo[OG_MAXD], hi[OG_MAXD];
+            for (int d = 0; d < nd; ++d) {
+                lo[d] = fmin(pm[d], pp[d]);
+                hi[d] = fmax(pm[d], pp[d]);
+            }
+            og_local_alpha(dy, z, lo, hi, a_loc);
+        }
         double diss = 0.0;
-        for (int d = 0; d < nd; ++d) diss += 0.5 * alpha[d] * (pp[d] - pm[d]);
+        for (int d = 0; d < nd; ++d) diss += 0.5 * (local ? a_loc[d] : alpha[d]) * (pp[d] - pm[d]);
         L[i] = h + diss;
     }
 }
@@ -590,7 +605,7 @@ int og_terms(int ndim, const int64_t *n, const double *lo, const double *hi,
 int og_step(int ndim, const int64_t *n, const double *lo, const double *hi, const int *periodic,
             int kind, const double *prm, int n_prm, int umode, int dmode, const double *l,
             const double *obst, const double *phi, double dt, int set_kind, int space_order,
-            int time_order, double *out, double *alpha_out)
+            int time_order, int local_alpha, double *out, double *alpha_out)
 {
     og_grid g;
     og_dyn dy;
@@ -606,13 +621,13 @@ int og_step(int ndim, const int64_t *n, const double *lo, const double *hi, cons
     og_alpha(&g, &dy, phi, space_order, alpha);
     if (alpha_out)
         for (int d = 0; d < ndim; ++d) alpha_out[d] = alpha[d];
-    og_rhs(&g, &dy, phi, space_order, alpha, L);
+    og_rhs(&g, &dy, phi, space_order, alpha, local_alpha, L);
     if (time_order == 1) {
         for (int64_t i = 0; i < N; ++i) out[i] = phi[i] + dt * L[i];
     } else {
         for (int64_t i = 0; i < N; ++i) phi1[i] = phi[i] + dt * L[i];
         og_alpha(&g, &dy, phi1, space_order, alpha);
-        og_rhs(&g, &dy, phi1, space_order, alpha, L);
+        og_rhs(&g, &dy, phi1, space_order, alpha, local_alpha, L);
         for (int64_t i = 0; i < N; ++i) out[i] = 0.5 * (phi[i] + (phi1[i] + dt * L[i]));
     }
     if (set_kind == OG_BRT)
@@ -635,6 +650,8 @@ int og_step(int ndim, const int64_t *n, const double *lo, const double *hi, cons
  *              the HJ variational inequality)
  *  obst        NULL, or the obstacle g(z): phi <- max(phi, g) after each step,
  *              after the BRT min (reach-avoid, reading R17)
+ *  local_alpha 0: dissipation with the grid alpha (Section 2.1); 1: with each
+ *              node's own alpha_i (Algorithm 1's second loop, reading R18)
  *  snapshots   NULL, or n_tau * total doubles: phi at every tau
  *  final_out   total doubles: phi at tau[n_tau-1]
  *  steps_out   NULL or n_tau-1 step counts, one per segment
@@ -645,7 +662,7 @@ int og_solve(int ndim, const int64_t *n, const double *lo, const double *hi,
              const int *periodic, int kind, const double *prm, int n_prm, int umode,
              int dmode, const double *l, const double *obst, const double *phi0,
              const double *tau, int n_tau,
-             int set_kind, int space_order, int time_order, double cfl, int64_t max_steps,
+             int set_kind, int space_order, int time_order, int local_alpha, double cfl, int64_t max_steps,
              double *snapshots, double *final_out, int64_t *steps_out,
              double *alpha_out, double *last_dt)
 {
@@ -683,12 +700,12 @@ int og_solve(int ndim, const int64_t *n, const double *lo, const double *hi,
             double dt_cfl = og_cfl_dt(&g, alpha, cfl);
             int last = !(dt_cfl < t_end - t);
             dt = last ? (t_end - t) : dt_cfl;
-            og_rhs(&g, &dy, phi, space_order, alpha, L);
+            og_rhs(&g, &dy, phi, space_order, alpha, local_alpha, L);
             for (int64_t i = 0; i < N; ++i) phi1[i] = phi[i] + dt * L[i];
             if (time_order == 2) {
                 /* stage 2 with its own alpha; Heun average */
                 og_alpha(&g, &dy, phi1, space_order, alpha2);
-                og_rhs(&g, &dy, phi1, space_order, alpha2, L);
+                og_rhs(&g, &dy, phi1, space_order, alpha2, local_alpha, L);
                 for (int64_t i = 0; i < N; ++i)
                     phi1[i] = 0.5 * (phi[i] + (phi1[i] + dt * L[i]));
             }

@@ -56,6 +56,9 @@ class Problem:
     # reach-avoid: obstacle g(z), positive inside the obstacle; after each step
     # phi <- max(phi, g) (after the BRT min with l)
     obstacle: Optional[Callable[[Sequence[np.ndarray]], np.ndarray]] = None
+    # Lax-Friedrichs dissipation: "global" (grid alpha, Section 2.1) or
+    # "local" (each node's own alpha, Algorithm 1's second loop)
+    dissipation: str = "global"
 
     @property
     def ndim(self) -> int:

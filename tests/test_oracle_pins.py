@@ -9,6 +9,7 @@ step of Algorithm 1 (a dropped term, a wrong sign, a swapped ENO choice, a
 wrong ghost rule, a reversed input mode, a wrong RK2 average) fails one of
 them.
 """
+import dataclasses
 import math
 import os
 
@@ -582,3 +583,79 @@ def test_reach_avoid_1d_obstacle_blocks_the_far_side():
     assert np.all(with_g[x >= 2.5 - 1e-9] >= 0)
     near = (x > -1.3) & (x < 1.3)
     assert np.all(with_g[near] < 0) and np.all(plain[near] < 0)
+
+
+# ---------------------------------------------------------------------------
+# per-node dissipation: alpha_i of each node instead of the grid maximum
+# (Algorithm 1's second loop; reading R18)
+# ---------------------------------------------------------------------------
+
+def local(problem):
+    return dataclasses.replace(problem, dissipation="local")
+
+
+@pytest.mark.parametrize("problem", [
+    inputs.single_integrator((19, 17), horizon=0.6),
+    inputs.single_integrator((9, 8, 7), space_order=2, time_order=2, horizon=0.4),
+    inputs.advection((24, 20), (1.0, -0.5), horizon=0.5, cfl=0.8),
+], ids=lambda p: p.name)
+def test_local_dissipation_equals_global_when_alpha_is_uniform(problem):
+    # the single integrator's bound and a constant velocity give every node
+    # the grid alpha, so the two dissipations are the same numbers
+    a = oracle.solve(problem)
+    b = oracle.solve(local(problem))
+    assert np.array_equal(a["final"], b["final"])
+    assert np.array_equal(a["steps"], b["steps"])
+
+
+def test_local_dissipation_is_the_upwind_scheme_for_transport():
+    # Dubins car with no turning: phi_tau = v cos(th) phi_x + v sin(th) phi_y.
+    # With alpha_i = |a_d(z_i)| the Lax-Friedrichs term a pbar + |a|/2 (p+ - p-)
+    # is the upwind difference a p+ (a >= 0) or a p- (a < 0), the textbook
+    # first-order upwind scheme, written out here independently
+    p = local(inputs.dubins3d(n=(23, 21, 16), v=1.3, w_max=0.0, set_kind="brs"))
+    rng = np.random.Generator(np.random.PCG64(11))
+    phi = rng.uniform(-1.0, 1.0, size=p.n)
+    dt = 0.03
+    out = oracle.step(p, phi, dt, l=np.zeros(p.n))["out"]
+    x, y, th = p.nodes()
+    hx, hy = x[1] - x[0], y[1] - y[0]
+    ax = (1.3 * np.cos(th))[None, None, :]
+    ay = (1.3 * np.sin(th))[None, None, :]
+    fx = (phi[2:, 1:-1] - phi[1:-1, 1:-1]) / hx        # D+ along x
+    bx = (phi[1:-1, 1:-1] - phi[:-2, 1:-1]) / hx       # D- along x
+    fy = (phi[1:-1, 2:] - phi[1:-1, 1:-1]) / hy
+    by = (phi[1:-1, 1:-1] - phi[1:-1, :-2]) / hy
+    upwind = np.where(ax >= 0, ax * fx, ax * bx) + np.where(ay >= 0, ay * fy, ay * by)
+    expect = phi[1:-1, 1:-1] + dt * upwind
+    np.testing.assert_allclose(out[1:-1, 1:-1], expect, rtol=0, atol=1e-13)
+    # the grid alpha adds dissipation wherever |cos th| or |sin th| < 1
+    glob = oracle.step(dataclasses.replace(p, dissipation="global"), phi, dt, l=np.zeros(p.n))["out"]
+    assert np.abs(glob[1:-1, 1:-1] - expect).max() > 1e-3
+
+
+def test_local_dissipation_is_closer_to_the_exact_transport():
+    # same transport from a smooth field: the exact solution is the field
+    # shifted along (v cos th, v sin th); away from the non-periodic x, y
+    # faces the per-node dissipation stays closer to it than the grid one
+    v, T = 1.0, 0.6
+    target = lambda m: np.sin(1.3 * m[0]) * np.cos(0.9 * m[1])
+    base = inputs.dubins3d(n=(61, 61, 16), v=v, w_max=0.0, set_kind="brs", horizon=T)
+    base = dataclasses.replace(base, target=target)
+    x, y, th = base.nodes()
+    X, Y, TH = np.meshgrid(x, y, th, indexing="ij")
+    exact = np.sin(1.3 * (X + v * np.cos(TH) * T)) * np.cos(0.9 * (Y + v * np.sin(TH) * T))
+    inner = (np.abs(X) < 2.5) & (np.abs(Y) < 2.5)
+    err_g = np.abs(oracle.solve(base)["final"] - exact)[inner].max()
+    err_l = np.abs(oracle.solve(local(base))["final"] - exact)[inner].max()
+    assert err_l < 0.8 * err_g
+    assert err_l < 0.05
+
+
+def test_local_dissipation_keeps_the_brt_monotone():
+    p = local(inputs.dubins3d(tau=(0.0, 0.5, 1.0, 1.5, 2.0)))
+    s = oracle.solve(p, snapshots=True)["snapshots"]
+    l = p.target_values().astype(np.float64)
+    assert (s <= l[None]).all()
+    for k in range(1, len(s)):
+        assert (s[k] <= s[k - 1] + 1e-12).all()
