@@ -17,6 +17,7 @@ solves, weak scaling); rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import glob
 import json
@@ -54,6 +55,8 @@ def parse_args():
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dissipation", choices=("global", "local"), default="global",
+                    help="Lax-Friedrichs dissipation: grid alpha or each node's own alpha")
     ap.add_argument("--host-loop", action="store_true",
                     help="step the time loop from the host (same kernels; for profilers)")
     return ap.parse_args()
@@ -247,6 +250,8 @@ def run_ours(args):
     odp.load()
     device = torch.device("cuda", local)
     problem = inputs.workload(args.workload)
+    if args.dissipation == "local":
+        problem = dataclasses.replace(problem, dissipation="local")
     N = problem.points
     l_host = problem.target_values()
     stream = torch.cuda.Stream()
@@ -341,6 +346,7 @@ def run_ours(args):
                        "l2": "working set (%.0f MB) larger than L2 (129 MB)" % (
                            (16.0 if problem.obstacle is not None else 12.0) * N / 1e6),
                        "reach_avoid": problem.obstacle is not None,
+                       "dissipation": problem.dissipation,
                        "parallelism": "independent solve per GPU",
                        "time_loop": "host-stepped" if args.host_loop else "one CUDA graph"},
             "gpu_launches": launches_per_solve * args.steps,

@@ -155,6 +155,14 @@ odp_status odp_set_target(odp_grid *g, const float *l, int64_t n_elems, int on_d
  * odp_batch_solve.  Errors: ODP_EINVAL, ODP_ENOMEM. */
 odp_status odp_set_obstacle(odp_grid *g, const float *gv, int64_t n_elems, int on_device);
 
+/* Lax-Friedrichs dissipation of later solves (no change to the CFL step):
+ * per_node = 0 (default) uses the grid alpha, the largest rate over the grid
+ * per component (Section 2.1); per_node = 1 uses each node's own alpha_i, the
+ * largest rate over the input extremes its derivative box admits (Algorithm
+ * 1's second loop).  Per-node solves run the generic stage kernels; grids
+ * with per_node = 1 are refused by odp_batch_solve.  Errors: ODP_EINVAL. */
+odp_status odp_set_dissipation(odp_grid *g, int per_node);
+
 /* Limit the number of full time steps of one solve (default 10,000,000).  A
  * solve that reaches the limit stops and reports ODP_ETIMEOUT. */
 odp_status odp_set_step_limit(odp_grid *g, int64_t max_steps);

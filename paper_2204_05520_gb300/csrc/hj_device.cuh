@@ -92,13 +92,14 @@ ODP_HD float2 f2pick(float2 x, float2 c)
 // L += cA P + cS |P| + cD M with P = dp + dm, M = dp - dm (unscaled one-sided
 // differences, see diffs()); has_a / has_s (compile-time constants at every
 // call) drop the terms a model does not have on this axis.  Same operation
-// order as diffs() for the ENO2 choice.
+// order as diffs() for the ENO2 choice.  pair_diffs / pair_terms are its two
+// halves.
 template <int ORDER>
-ODP_HD void axis_pair(float2 fm2, float2 fm1, float2 f0, float2 fp1, float2 fp2, float2 cA, float cS, float cD,
-                      float2 &L, bool has_a, bool has_s)
+ODP_HD void pair_diffs(float2 fm2, float2 fm1, float2 f0, float2 fp1, float2 fp2, float2 &dm, float2 &dp)
 {
     const float2 a = f2sub(f0, fm1), b = f2sub(fp1, f0);
-    float2 dm = a, dp = b;
+    dm = a;
+    dp = b;
     if (ORDER == 2) {
         const float2 d2l = f2sub(a, f2sub(fm1, fm2));
         const float2 d2m = f2sub(b, a);
@@ -107,10 +108,26 @@ ODP_HD void axis_pair(float2 fm2, float2 fm1, float2 f0, float2 fp1, float2 fp2,
         dm = f2fma(cm, f2splat(0.5f), a);
         dp = f2fma(cp, f2splat(-0.5f), b);
     }
+}
+
+// The axis's terms from the unscaled one-sided differences of two nodes:
+// L += cA P + cS |P| + cD M, cD per lane (the dissipation coefficient
+// alpha / (2 h) of each node).
+ODP_HD void pair_terms(float2 dm, float2 dp, float2 cA, float cS, float2 cD, float2 &L, bool has_a, bool has_s)
+{
     const float2 P = f2add(dp, dm), M = f2sub(dp, dm);
     if (has_a) L = f2fma(cA, P, L);
     if (has_s) L = f2fma(f2splat(cS), f2abs(P), L);
-    L = f2fma(f2splat(cD), M, L);
+    L = f2fma(cD, M, L);
+}
+
+template <int ORDER>
+ODP_HD void axis_pair(float2 fm2, float2 fm1, float2 f0, float2 fp1, float2 fp2, float2 cA, float cS, float2 cD,
+                      float2 &L, bool has_a, bool has_s)
+{
+    float2 dm, dp;
+    pair_diffs<ORDER>(fm2, fm1, f0, fp1, fp2, dm, dp);
+    pair_terms(dm, dp, cA, cS, cD, L, has_a, has_s);
 }
 
 // The last axis of four consecutive nodes from their eight-node window

@@ -174,14 +174,40 @@ struct StageArgs {
 // pairs of nodes).
 template <int ORDER>
 ODP_HD void segment_axis(const float4 &m2, const float4 &m1, const float4 &c, const float4 &p1, const float4 &p2,
-                         const float *cA, float cS, float cD, float2 &L01, float2 &L23, bool has_a, bool has_s)
+                         const float *cA, float cS, float cD, float2 &L01, float2 &L23, bool has_a, bool has_s,
+                         bool abs_cA = false)
 {
+    // abs_cA: per-node dissipation of an axis whose rate is the drift alone,
+    // alpha_i / (2 h) = |a(z_i)| / (2 h) = |cA| (Algorithm 1's second loop)
+    const float2 a01 = make_float2(cA[0], cA[1]), a23 = make_float2(cA[2], cA[3]);
     axis_pair<ORDER>(make_float2(m2.x, m2.y), make_float2(m1.x, m1.y), make_float2(c.x, c.y),
-                                   make_float2(p1.x, p1.y), make_float2(p2.x, p2.y), make_float2(cA[0], cA[1]),
-                                   cS, cD, L01, has_a, has_s);
+                     make_float2(p1.x, p1.y), make_float2(p2.x, p2.y), a01, cS,
+                     abs_cA ? f2abs(a01) : f2splat(cD), L01, has_a, has_s);
     axis_pair<ORDER>(make_float2(m2.z, m2.w), make_float2(m1.z, m1.w), make_float2(c.z, c.w),
-                                   make_float2(p1.z, p1.w), make_float2(p2.z, p2.w), make_float2(cA[2], cA[3]),
-                                   cS, cD, L23, has_a, has_s);
+                     make_float2(p1.z, p1.w), make_float2(p2.z, p2.w), a23, cS,
+                     abs_cA ? f2abs(a23) : f2splat(cD), L23, has_a, has_s);
+}
+
+// The Rel6D heading axis with per-node dissipation: each node's heading-rate
+// bound from the interval of its own one-sided differences (the same rule as
+// the grid alpha, rel6d_theta_alpha), scaled by 1 / (2 h).
+template <int ORDER>
+ODP_HD void segment_axis_rel6d_theta(const float4 &m2, const float4 &m1, const float4 &c, const float4 &p1,
+                                     const float4 &p2, const float *cA, float cS, const DynDesc &dy, float wp,
+                                     float hh, float2 &L01, float2 &L23)
+{
+    const float2 a01 = make_float2(cA[0], cA[1]), a23 = make_float2(cA[2], cA[3]);
+    float2 dm, dp;
+    pair_diffs<ORDER>(make_float2(m2.x, m2.y), make_float2(m1.x, m1.y), make_float2(c.x, c.y),
+                      make_float2(p1.x, p1.y), make_float2(p2.x, p2.y), dm, dp);
+    float2 cD = make_float2(hh * rel6d_theta_alpha(dy, wp, fminf(dm.x, dp.x), fmaxf(dm.x, dp.x)),
+                            hh * rel6d_theta_alpha(dy, wp, fminf(dm.y, dp.y), fmaxf(dm.y, dp.y)));
+    pair_terms(dm, dp, a01, cS, cD, L01, true, true);
+    pair_diffs<ORDER>(make_float2(m2.z, m2.w), make_float2(m1.z, m1.w), make_float2(c.z, c.w),
+                      make_float2(p1.z, p1.w), make_float2(p2.z, p2.w), dm, dp);
+    cD = make_float2(hh * rel6d_theta_alpha(dy, wp, fminf(dm.x, dp.x), fmaxf(dm.x, dp.x)),
+                     hh * rel6d_theta_alpha(dy, wp, fminf(dm.y, dp.y), fmaxf(dm.y, dp.y)));
+    pair_terms(dm, dp, a23, cS, cD, L23, true, true);
 }
 
 // Update of a four-node segment from its right-hand side L: phi + dt L
@@ -363,7 +389,13 @@ ODP_HD bool stage_tile(const GridDesc &g, const DynDesc &dy, const StageArgs &A,
                 m2 = axis_row(src, base, id, id - 2, stride, n, per);
                 p2 = axis_row(src, base, id, id + 2, stride, n, per);
             }
-            segment_axis<ORDER>(m2, m1, c4, p1, p2, cA[d], cS[d], A.cD[d], L01, L23, has_drift<DYN, ND>(d), has_bound<DYN, ND>(d));
+            if (DYN == DYN_REL6D && d == 2 && dy.local_diss)
+                segment_axis_rel6d_theta<ORDER>(m2, m1, c4, p1, p2, cA[d], cS[d], dy, ldgf(g.coord[4] + idx[4]),
+                                                0.5f * g.inv_dz[2], L01, L23);
+            else
+                segment_axis<ORDER>(m2, m1, c4, p1, p2, cA[d], cS[d], A.cD[d], L01, L23, has_drift<DYN, ND>(d),
+                                    has_bound<DYN, ND>(d),
+                                    dy.local_diss && has_drift<DYN, ND>(d) && !has_bound<DYN, ND>(d));
         }
 
         // axis ND-2 from the column
@@ -371,7 +403,8 @@ ODP_HD bool stage_tile(const GridDesc &g, const DynDesc &dy, const StageArgs &A,
             constexpr int d = ND - 2 < 0 ? 0 : ND - 2;
             const float4 m2 = col[i + O - 2 < 0 ? 0 : i + O - 2], m1 = col[i + O - 1];
             const float4 p1 = col[i + O + 1], p2 = col[i + O + 2 < NC ? i + O + 2 : NC - 1];
-            segment_axis<ORDER>(m2, m1, c4, p1, p2, cA[d], cS[d], A.cD[d], L01, L23, has_drift<DYN, ND>(d), has_bound<DYN, ND>(d));
+            segment_axis<ORDER>(m2, m1, c4, p1, p2, cA[d], cS[d], A.cD[d], L01, L23, has_drift<DYN, ND>(d),
+                                has_bound<DYN, ND>(d), dy.local_diss && has_drift<DYN, ND>(d) && !has_bound<DYN, ND>(d));
         }
 
         // last axis: an eight-node window w[j] = phi(first node - 2 + j)
@@ -572,7 +605,7 @@ cudaError_t launch_stage_t(const GridDesc &g, const DynDesc &dy, SolveState *st,
             const int blocks = g.pg.items, th = g.pg.threads, sm = g.pg.smem[order - 1];
             const bool full = g.n[ND - 1] % 4 == 0;
             constexpr bool SPEC = DYN == DYN_DUBINS3D || DYN == DYN_DUBINSCAR4D || DYN == DYN_REL6D;
-            if (SPEC && full) {
+            if (SPEC && full && !dy.local_diss) {
                 const bool ob = gob != nullptr;
                 if (order == 1) {
                     if (stage == 0) {

@@ -89,6 +89,9 @@ __global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DY
                                                      const float *__restrict__ gob, int stage_rt, int brt)
 {
     const int stage = STAGE >= 0 ? STAGE : stage_rt;
+    // per-node dissipation (Algorithm 1's second loop) runs in the generic
+    // instantiation only
+    const bool local = STAGE < 0 && dy.local_diss != 0;
     const PlaneGeom &pg = g.pg;
     constexpr int O = ORDER;
     constexpr int Q = 2 * O + 1;        // stream-axis window
@@ -334,13 +337,20 @@ __global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DY
                     cA[1][3] = a1.w;
                 }
 #pragma unroll
-                for (int d = 0; d < NOUT; ++d)
-                    segment_axis<ORDER>(nb[d][0], nb[d][O - 1], c4, nb[d][O], nb[d][2 * O - 1], cA[d], cS[d],
-                                        cD[d], L01, L23, has_drift<DYN, ND>(d), has_bound<DYN, ND>(d));
+                for (int d = 0; d < NOUT; ++d) {
+                    if (DYN == DYN_REL6D && d == 2 && local)
+                        segment_axis_rel6d_theta<ORDER>(nb[d][0], nb[d][O - 1], c4, nb[d][O], nb[d][2 * O - 1],
+                                                        cA[d], cS[d], dy, rx_wp, 0.5f * g.inv_dz[2], L01, L23);
+                    else
+                        segment_axis<ORDER>(nb[d][0], nb[d][O - 1], c4, nb[d][O], nb[d][2 * O - 1], cA[d], cS[d],
+                                            cD[d], L01, L23, has_drift<DYN, ND>(d), has_bound<DYN, ND>(d),
+                                            local && has_drift<DYN, ND>(d) && !has_bound<DYN, ND>(d));
+                }
                 // stream axis from the register window
                 segment_axis<ORDER>(w[u % Q], w[(u + O - 1) % Q], c4, w[(u + O + 1) % Q], w[(u + Q - 1) % Q],
                                     cA[sa], cS[sa], cD[sa], L01, L23, has_drift<DYN, ND>(sa),
-                                    has_bound<DYN, ND>(sa));
+                                    has_bound<DYN, ND>(sa),
+                                    local && has_drift<DYN, ND>(sa) && !has_bound<DYN, ND>(sa));
                 // row axis from the tile; ghost rows from this column
                 {
                     float4 m1 = *reinterpret_cast<const float4 *>(C - cp);
@@ -362,7 +372,8 @@ __global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DY
                         }
                     }
                     segment_axis<ORDER>(m2, m1, c4, p1, p2, cA[ND - 2], cS[ND - 2], cD[ND - 2], L01, L23,
-                                        has_drift<DYN, ND>(ND - 2), has_bound<DYN, ND>(ND - 2));
+                                        has_drift<DYN, ND>(ND - 2), has_bound<DYN, ND>(ND - 2),
+                                        local && has_drift<DYN, ND>(ND - 2) && !has_bound<DYN, ND>(ND - 2));
                 }
                 // last axis: window v[k] = phi(s0 - 2 + k)
                 float L[4] = {L01.x, L01.y, L23.x, L23.y};

@@ -437,6 +437,7 @@ extern "C" odp_status odp_set_dynamics(odp_grid *g, odp_dyn kind, const double *
     dy.umode = int(u_mode);
     dy.dmode = int(d_mode);
     dy.angle_axis = angle;
+    dy.local_diss = g->local_diss;
     for (int k = 0; k < n_params; ++k) dy.prm[k] = float(params[k]);
     g->dyn = dy;
     g->dyn_version += 1;
@@ -495,6 +496,18 @@ extern "C" odp_status odp_set_obstacle(odp_grid *g, const float *gv, int64_t n_e
                                size_t(g->n_last) * sizeof(float), size_t(g->rows),
                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));
     g->has_obst = true;
+    return ODP_OK;
+}
+
+extern "C" odp_status odp_set_dissipation(odp_grid *g, int per_node)
+{
+    if (!g) return fail(ODP_EINVAL, "grid is NULL");
+    if (per_node != 0 && per_node != 1) return fail(ODP_EINVAL, "per_node must be 0 or 1");
+    if (g->local_diss != per_node) {
+        g->local_diss = per_node;
+        g->dyn.local_diss = per_node;
+        g->dyn_version += 1;   // the captured loop holds the old flag
+    }
     return ODP_OK;
 }
 

@@ -155,6 +155,7 @@ struct DynDesc {
     int kind;
     int umode, dmode;
     int angle_axis;              // axis holding the heading angle, -1 if none
+    int local_diss;              // 1: per-node dissipation alpha_i (Algorithm 1's second loop)
     float prm[8];
 };
 

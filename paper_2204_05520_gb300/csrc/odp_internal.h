@@ -40,6 +40,7 @@ struct odp_grid {
     float *phi_a = nullptr, *phi_b = nullptr, *l = nullptr;
     float *obst = nullptr;            // reach-avoid obstacle g (allocated on first use)
     bool has_obst = false;
+    int local_diss = 0;               // per-node dissipation (odp_set_dissipation)
     float *tables = nullptr;          // all node-coordinate and trig tables
     odp::SolveState *state = nullptr;
     double *tau = nullptr;

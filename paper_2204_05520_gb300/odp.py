@@ -108,6 +108,7 @@ def load():
             "odp_set_dynamics": ([P, i32, P, i32, i32, i32], i32),
             "odp_set_target": ([P, P, i64, i32], i32),
             "odp_set_obstacle": ([P, P, i64, i32], i32),
+            "odp_set_dissipation": ([P, i32], i32),
             "odp_set_step_limit": ([P, i64], i32),
             "odp_set_loop_mode": ([P, i32], i32),
             "odp_solve_hjb": ([P, P, i32, i32, i32, i32, f64, i32, P], i32),
@@ -220,6 +221,12 @@ def set_obstacle(g, gv):
     n = grid_points(g)
     ptr, dev = _buffer(gv, n, writable=False)
     _check(load().odp_set_obstacle(g, ptr, n, dev), "odp_set_obstacle")
+
+
+def set_dissipation(g, per_node: bool):
+    """Lax-Friedrichs dissipation with the grid alpha (False) or each node's
+    own alpha (True)."""
+    _check(load().odp_set_dissipation(g, 1 if per_node else 0), "odp_set_dissipation")
 
 
 def set_step_limit(g, max_steps: int):
@@ -400,6 +407,8 @@ class Grid:
         set_dynamics(g.handle, problem.dynamics, problem.params, problem.u_mode, problem.d_mode)
         if getattr(problem, "obstacle", None) is not None:
             set_obstacle(g.handle, problem.obstacle_values())
+        if getattr(problem, "dissipation", "global") == "local":
+            set_dissipation(g.handle, True)
         return g
 
     def close(self):

@@ -355,3 +355,66 @@ def test_obstacle_arguments_are_checked():
         with pytest.raises(odp.OdpError) as e:
             odp.batch_solve([g], [0.5])
         assert e.value.code == odp.EINVAL
+
+
+# ---------------------------------------------------------------------------
+# per-node dissipation (Algorithm 1's second loop) against the oracle
+# ---------------------------------------------------------------------------
+
+def per_node(problem):
+    return dataclasses.replace(problem, dissipation="local")
+
+
+LOCAL_CASES = [
+    per_node(inputs.dubins3d()),                                          # 41x41x36, Euler, upwind
+    per_node(inputs.dubins3d(n=(23, 19, 13), space_order=2, time_order=2)),
+    per_node(inputs.dubinscar4d(n=(21, 19, 11, 16))),                    # ENO2 + RK2
+    per_node(inputs.dubinscar4d(n=(17, 15, 9, 13), space_order=1, time_order=1)),  # partial segments
+    per_node(inputs.rel6d(n=(9, 8, 10, 5, 4, 3), horizon=0.3)),           # upwind + RK2
+    per_node(inputs.rel6d(n=(7, 7, 8, 3, 4, 3), space_order=2, horizon=0.2)),
+]
+
+
+@pytest.mark.parametrize("problem", LOCAL_CASES, ids=lambda p: "%s_o%d%d_local" % (
+    p.name, p.space_order, p.time_order))
+def test_per_node_dissipation_matches_oracle(problem):
+    if problem.dynamics == "rel6d":
+        # the per-node heading-rate alpha switches with the sign of p_theta, so
+        # the whole solve is as sensitive to rounding as ENO2 (1e-7 relative
+        # input noise moves the FP64 oracle by 5e-4 of the value range):
+        # compared segment by segment at the same bar
+        steps = int(oracle.solve(problem)["steps"].sum())
+        check_parity_resync(problem, segments=max(2, steps // 2))
+    else:
+        check(problem)
+
+
+def test_per_node_dissipation_changes_dubins_but_not_the_single_integrator():
+    import torch
+
+    def run(p):
+        l = torch.from_numpy(p.target_values()).cuda()
+        with odp.Grid.for_problem(p) as g:
+            g.set_target(l)
+            g.solve_problem(p)
+            return g.readback(torch.empty_like(l)).cpu().numpy()
+
+    si = inputs.single_integrator((29, 27, 13), horizon=0.6)
+    assert np.array_equal(run(si), run(per_node(si)))
+    d3 = inputs.dubins3d(n=(25, 23, 20), horizon=0.8)
+    assert np.abs(run(d3) - run(per_node(d3))).max() > 1e-4
+
+
+def test_per_node_dissipation_full_size_step_matches_oracle():
+    p = per_node(inputs.dubinscar4d())
+    rel, _, _ = one_step_at_full_size(p, t_a=0.5)
+    assert rel <= REL_TOL
+
+
+def test_batch_refuses_per_node_dissipation():
+    p = inputs.dubins3d(n=(9, 9, 8))
+    with odp.Grid.for_problem(per_node(p)) as g:
+        g.set_target(p.target_values())
+        with pytest.raises(odp.OdpError) as e:
+            odp.batch_solve([g], [0.5])
+        assert e.value.code == odp.EINVAL
