@@ -24,7 +24,8 @@ _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-DYN_IDS = {"single_integrator": 0, "dubins3d": 1, "dubinscar4d": 2, "rel6d": 3, "advection": 4}
+DYN_IDS = {"single_integrator": 0, "dubins3d": 1, "dubinscar4d": 2, "rel6d": 3, "advection": 4,
+           "dubins_capture": 5}
 MODE_IDS = {"min": 0, "max": 1}
 SET_IDS = {"brs": 0, "brt": 1}
 MAX_INPUTS = 8

@@ -37,6 +37,11 @@
  *     dissipation of node i uses alpha_i, the local bound of R5 at that node
  *     (its own derivative box), instead of the grid maximum; the CFL step
  *     still uses the grid maximum.
+ *  R20 alpha with coupled inputs: each input's selectable extremes come from
+ *     the range of its own switching function over the derivative box, and
+ *     alpha_d is the largest |f_d| over every combination of them (a product
+ *     set).  For the capture model, whose two inputs share p_th, this bounds
+ *     Algorithm 1's max over the box from above.
  *  R17 reach-avoid (Section 4.3, the target and obstacle computation
  *     methods): with an obstacle function g, after each full step
  *     phi <- max(phi, g), taken after the BRT min with l (target first, then
@@ -58,7 +63,8 @@
 #define OG_MAXD 8
 
 /* dynamics ids (this library's own numbering) */
-enum { OG_SINGLE_INT = 0, OG_DUBINS3D = 1, OG_DUBINSCAR4D = 2, OG_REL6D = 3, OG_ADVECTION = 4 };
+enum { OG_SINGLE_INT = 0, OG_DUBINS3D = 1, OG_DUBINSCAR4D = 2, OG_REL6D = 3, OG_ADVECTION = 4,
+       OG_CAPTURE = 5 };
 enum { OG_MIN = 0, OG_MAX = 1 };
 enum { OG_BRS = 0, OG_BRT = 1 };
 
@@ -219,13 +225,14 @@ static int og_n_ctrl(const og_dyn *dy)
     case OG_DUBINS3D: return 1;
     case OG_DUBINSCAR4D: return 2;
     case OG_REL6D: return 2;
+    case OG_CAPTURE: return 1;
     default: return 0;
     }
 }
 
 static int og_n_dstb(const og_dyn *dy)
 {
-    return dy->kind == OG_REL6D ? 2 : 0;
+    return dy->kind == OG_REL6D ? 2 : (dy->kind == OG_CAPTURE ? 1 : 0);
 }
 
 static double og_ctrl_bound(const og_dyn *dy, int k)
@@ -235,13 +242,16 @@ static double og_ctrl_bound(const og_dyn *dy, int k)
     case OG_DUBINS3D: return dy->prm[1];            /* |w| <= w_max              */
     case OG_DUBINSCAR4D: return dy->prm[k];         /* |a| <= a_max, |w| <= w_max */
     case OG_REL6D: return dy->prm[k];               /* |a_p|, |alpha_p|          */
+    case OG_CAPTURE: return dy->prm[1];             /* |a| <= A (evader turn)    */
     default: return 0.0;
     }
 }
 
 static double og_dstb_bound(const og_dyn *dy, int k)
 {
-    return dy->kind == OG_REL6D ? dy->prm[2 + k] : 0.0;   /* |a_e|, |w_e| */
+    if (dy->kind == OG_REL6D) return dy->prm[2 + k];   /* |a_e|, |w_e|              */
+    if (dy->kind == OG_CAPTURE) return dy->prm[2];     /* |b| <= B (pursuer turn)   */
+    return 0.0;
 }
 
 /* f(z, u, d) of each model (Appendix; Rel6D is the repository's 6-D
@@ -278,6 +288,13 @@ static void og_dynamics(const og_dyn *dy, const double *z, const double *u,
         f[3] = u[0];              /* pursuer acceleration a_p               */
         f[4] = u[1];              /* pursuer angular acceleration alpha_p   */
         f[5] = dd[0];             /* evader acceleration a_e                */
+        break;
+    }
+    case OG_CAPTURE: {            /* Section 4.2 pursuit-evasion, (x, y, th) relative */
+        double v = dy->prm[0], x = z[0], y = z[1], th = z[2];
+        f[0] = -v + v * cos(th) + u[0] * y;
+        f[1] = v * sin(th) - u[0] * x;
+        f[2] = dd[0] - u[0];      /* pursuer turn b minus evader turn a */
         break;
     }
     default:
@@ -473,6 +490,7 @@ static int og_setup(og_grid *g, og_dyn *dy, int ndim, const int64_t *n, const do
     case OG_DUBINS3D: need = 2; if (ndim != 3) return OG_EINVAL; break;
     case OG_DUBINSCAR4D: need = 2; if (ndim != 4) return OG_EINVAL; break;
     case OG_REL6D: need = 4; if (ndim != 6) return OG_EINVAL; break;
+    case OG_CAPTURE: need = 3; if (ndim != 3) return OG_EINVAL; break;
     case OG_ADVECTION: need = ndim; break;
     default: return OG_EINVAL;
     }

@@ -31,7 +31,7 @@ from typing import Callable, Optional, Sequence
 import numpy as np
 
 # Dynamics names understood by both sides (each maps them to its own enum).
-DYNAMICS = ("single_integrator", "dubins3d", "dubinscar4d", "rel6d", "advection")
+DYNAMICS = ("single_integrator", "dubins3d", "dubinscar4d", "rel6d", "advection", "dubins_capture")
 
 
 @dataclasses.dataclass
@@ -206,6 +206,20 @@ def rel6d(n=(24,) * 6, bounds=(1.0, 1.0, 1.0, 1.0), radius=0.5, horizon=1.5,
         params=tuple(bounds), u_mode="min", d_mode="max", target=cylinder(radius),
         tau=tau or (0.0, horizon), set_kind=set_kind, space_order=space_order,
         time_order=time_order)
+
+
+def dubins_capture(n=(40, 40, 40), v=1.0, a_max=1.0, b_max=1.0, radius=0.5, horizon=1.5,
+                   u_mode="max", d_mode="min", set_kind="brt", space_order=1, time_order=1,
+                   tau=None) -> Problem:
+    """Pursuit-evasion of two Dubins cars in relative coordinates (Section 4.2):
+    x' = -v + v cos th + a y, y' = v sin th - a x, th' = b - a; evader turn a
+    (|a| <= a_max, maximising), pursuer turn b (|b| <= b_max, minimising);
+    capture target sqrt(x^2 + y^2) - radius on [-4, 4]^2 x [-pi, pi)."""
+    return Problem(
+        name="dubins_capture_%dx%dx%d" % tuple(n), n=tuple(n), lo=(-4.0, -4.0, -PI), hi=(4.0, 4.0, PI),
+        periodic=(False, False, True), dynamics="dubins_capture", params=(v, a_max, b_max),
+        u_mode=u_mode, d_mode=d_mode, target=cylinder(radius), tau=tau or (0.0, horizon),
+        set_kind=set_kind, space_order=space_order, time_order=time_order)
 
 
 def single_integrator(n, half_width=2.0, u_max=1.0, radius=0.5, horizon=0.5,

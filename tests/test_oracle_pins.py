@@ -118,6 +118,8 @@ def input_bounds(problem):
         return [prm[0], prm[1]], []
     if dyn == "rel6d":
         return [prm[0], prm[1]], [prm[2], prm[3]]
+    if dyn == "dubins_capture":
+        return [prm[1]], [prm[2]]
     return [], []
 
 
@@ -155,6 +157,8 @@ TINY = [
     inputs.dubinscar4d(n=(5, 5, 4, 6), u_mode="min"),
     inputs.dubinscar4d(n=(5, 5, 4, 6), u_mode="max"),
     inputs.rel6d(n=(4, 4, 4, 3, 3, 3)),
+    inputs.dubins_capture(n=(9, 9, 8)),
+    inputs.dubins_capture(n=(9, 9, 8), u_mode="min", d_mode="max"),
     inputs.single_integrator((6, 5), u_mode="min"),
     inputs.single_integrator((6, 5), u_mode="max"),
 ]
@@ -659,3 +663,101 @@ def test_local_dissipation_keeps_the_brt_monotone():
     assert (s <= l[None]).all()
     for k in range(1, len(s)):
         assert (s[k] <= s[k - 1] + 1e-12).all()
+
+
+# ---------------------------------------------------------------------------
+# the pursuit-evasion capture model of Section 4.2: its evader input enters
+# all three components, so its switching function y p_x - x p_y - p_th mixes
+# them and the dissipation bound needs interval bounds of it
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("problem", [
+    inputs.dubins_capture(n=(9, 9, 8)),
+    inputs.dubins_capture(n=(9, 9, 8), u_mode="min", d_mode="max"),
+    inputs.rel6d(n=(4, 4, 4, 3, 3, 3)),
+], ids=lambda p: p.name + "_" + p.u_mode)
+@pytest.mark.parametrize("order", [1, 2])
+def test_local_alpha_matches_the_corners_of_the_derivative_box(problem, order):
+    # the switching functions are linear in p, so over a node's derivative box
+    # their ranges are spanned by its corners: an input's selectable extremes
+    # are its bang-bang choices at the corners.  alpha_d is the largest |f_d|
+    # over every combination of each input's selectable extremes (reading
+    # R20); the choices the inputs make together at one corner never exceed it
+    phi = inputs.random_field(problem.n, seed=5 + order)
+    t = oracle.terms(problem, phi, order=order)
+    nd = problem.ndim
+    lo = np.minimum(t["pm"], t["pp"]).reshape(-1, nd)
+    hi = np.maximum(t["pm"], t["pp"]).reshape(-1, nd)
+    z = np.stack(np.meshgrid(*problem.nodes(), indexing="ij"), axis=-1).reshape(-1, nd)
+    ub, db = input_bounds(problem)
+    rng = np.random.Generator(np.random.PCG64(4))
+    pick = rng.choice(len(z), size=min(len(z), 60), replace=False)
+    corners = np.array(np.meshgrid(*[[0, 1]] * nd, indexing="ij")).reshape(nd, -1).T
+    a_oracle = t["a"].reshape(-1, nd)[pick]
+    dyn, prm = problem.dynamics, problem.params
+
+    def column(zi, k, is_d):
+        e = np.zeros(8)
+        e[k] = 1.0
+        f0 = oracle.eval_dynamics(dyn, prm, zi)
+        f1 = oracle.eval_dynamics(dyn, prm, zi, d=e) if is_d else oracle.eval_dynamics(dyn, prm, zi, u=e)
+        return f1 - f0
+
+    def choice(s, b, mode):
+        up = s >= 0 if mode == "max" else s < 0
+        return b if up else -b
+
+    for row, i in enumerate(pick):
+        pcs = [np.where(c == 1, hi[i], lo[i]) for c in corners]
+        sel, joint = [], [dict() for _ in pcs]
+        for k, (b, is_d) in enumerate([(b, False) for b in ub] + [(b, True) for b in db]):
+            g = column(z[i], k - (len(ub) if is_d else 0), is_d)
+            mode = problem.d_mode if is_d else problem.u_mode
+            picks = [choice(float(pc @ g), b, mode) for pc in pcs]
+            sel.append(sorted(set(picks)))
+            for c, v in enumerate(picks):
+                joint[c][k] = v
+        best = np.zeros(nd)
+        for combo in np.array(np.meshgrid(*sel, indexing="ij")).reshape(len(sel), -1).T:
+            u = np.zeros(8)
+            d = np.zeros(8)
+            u[:len(ub)] = combo[:len(ub)]
+            d[:len(db)] = combo[len(ub):]
+            best = np.maximum(best, np.abs(oracle.eval_dynamics(dyn, prm, z[i], u=u, d=d)))
+        np.testing.assert_allclose(a_oracle[row], best, rtol=0, atol=1e-12)
+        for jc in joint:
+            u = np.zeros(8)
+            d = np.zeros(8)
+            u[:len(ub)] = [jc[k] for k in range(len(ub))]
+            d[:len(db)] = [jc[len(ub) + k] for k in range(len(db))]
+            f = np.abs(oracle.eval_dynamics(dyn, prm, z[i], u=u, d=d))
+            assert (f <= a_oracle[row] + 1e-12).all()
+
+
+def capture_transport_error(n_xy, n_th, T=0.5, v=1.0):
+    """Without turning (A = B = 0) the capture dynamics drift with
+    (-v + v cos th, v sin th): V(z, t) = l(x + t (v cos th - v), y + t v sin th)."""
+    p = inputs.dubins_capture(n=(n_xy, n_xy, n_th), v=v, a_max=0.0, b_max=0.0, radius=1.0,
+                              horizon=T, set_kind="brs")
+    res = oracle.solve(p)
+    x, y, th = np.meshgrid(*p.nodes(), indexing="ij")
+    xs, ys = x + T * (v * np.cos(th) - v), y + T * v * np.sin(th)
+    rho = np.sqrt(xs ** 2 + ys ** 2)
+    inner = (np.abs(x) < 4 - 2 * v * T - 0.5) & (np.abs(y) < 4 - v * T - 0.5) & (rho > 0.5)
+    return np.abs(res["final"] - (rho - 1.0))[inner].max()
+
+
+def test_capture_transport_characteristics():
+    e1 = capture_transport_error(41, 24)
+    e2 = capture_transport_error(81, 24)
+    assert e2 < 0.1
+    assert e1 / e2 > 1.6
+
+
+def test_capture_mirror_symmetry():
+    # (x, y, th) -> (x, -y, -th) with a -> -a, b -> -b maps the game onto
+    # itself; the symmetric bounds and target make the value symmetric
+    p = inputs.dubins_capture(n=(21, 21, 16), horizon=0.6)
+    v = oracle.solve(p)["final"]
+    mirrored = v[:, ::-1, :][:, :, (-np.arange(16)) % 16]
+    np.testing.assert_allclose(v, mirrored, rtol=0, atol=1e-12)
