@@ -74,13 +74,20 @@ typedef struct odp_grid odp_grid;
  *                      (the 3D pursuit-evasion model of Section 4.2 extended
  *                      with speed and turn-rate states as in the 5D Dubins car)
  *  ODP_DYN_ADVECTION   any ndim: z' = c, params c_0 .. c_{ndim-1} (no inputs)
+ *  ODP_DYN_DUBINS_CAPTURE z = (x, y, th): pursuit-evasion of two Dubins cars in
+ *                      relative coordinates (Section 4.2): x' = -v + v cos th + a y,
+ *                      y' = v sin th - a x, th' = b - a; control a (evader turn,
+ *                      |a| <= A), disturbance b (pursuer turn, |b| <= B);
+ *                      params (v, A, B); every alpha component is reduced per
+ *                      stage; no per-node dissipation
  * Angles (th) must lie on a periodic axis. */
 typedef enum {
     ODP_DYN_SINGLE_INT = 0,
     ODP_DYN_DUBINS3D = 1,
     ODP_DYN_DUBINSCAR4D = 2,
     ODP_DYN_REL6D = 3,
-    ODP_DYN_ADVECTION = 4
+    ODP_DYN_ADVECTION = 4,
+    ODP_DYN_DUBINS_CAPTURE = 5
 } odp_dyn;
 
 /* Role of an input in the Hamiltonian (Algorithm 1, optimal control and

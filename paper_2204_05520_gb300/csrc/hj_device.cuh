@@ -113,9 +113,11 @@ ODP_HD void pair_diffs(float2 fm2, float2 fm1, float2 f0, float2 fp1, float2 fp2
 // The axis's terms from the unscaled one-sided differences of two nodes:
 // L += cA P + cS |P| + cD M, cD per lane (the dissipation coefficient
 // alpha / (2 h) of each node).
-ODP_HD void pair_terms(float2 dm, float2 dp, float2 cA, float cS, float2 cD, float2 &L, bool has_a, bool has_s)
+ODP_HD void pair_terms(float2 dm, float2 dp, float2 cA, float cS, float2 cD, float2 &L, bool has_a, bool has_s,
+                       float2 *Pout = nullptr)
 {
     const float2 P = f2add(dp, dm), M = f2sub(dp, dm);
+    if (Pout) *Pout = P;
     if (has_a) L = f2fma(cA, P, L);
     if (has_s) L = f2fma(f2splat(cS), f2abs(P), L);
     L = f2fma(cD, M, L);
@@ -134,7 +136,8 @@ ODP_HD void axis_pair(float2 fm2, float2 fm1, float2 f0, float2 fp1, float2 fp2,
 // w[j] = phi(first - 2 + j), sharing the first and second differences of the
 // window between the four nodes (the same float32 operations as diffs()).
 template <int ORDER>
-ODP_HD void axis_last(const float *w, const float *cA, float cS, float cD, float *L, bool has_a, bool has_s)
+ODP_HD void axis_last(const float *w, const float *cA, float cS, float cD, float *L, bool has_a, bool has_s,
+                      float *Pout = nullptr)
 {
     float e[7];
 #pragma unroll
@@ -153,6 +156,7 @@ ODP_HD void axis_last(const float *w, const float *cA, float cS, float cD, float
             dp = fmaf(cp, -0.5f, b);
         }
         const float P = dp + dm, M = dp - dm;
+        if (Pout) Pout[k] = P;
         float acc = L[k];
         if (has_a) acc = fmaf(cA[k], P, acc);
         if (has_s) acc = fmaf(cS, fabsf(P), acc);
@@ -161,7 +165,9 @@ ODP_HD void axis_last(const float *w, const float *cA, float cS, float cD, float
 }
 
 // Which axes carry a drift term (a_d(z) depends on the state) and which a
-// bounded input (S_d != 0), per model (Appendix dynamics).
+// bounded input (S_d != 0), per model (Appendix dynamics).  The capture
+// model's evader turn enters all three axes; its term S_a |y pbar_x -
+// x pbar_y - pbar_th| is added separately (capture_term).
 template <int DYN, int ND>
 constexpr bool has_drift(int d)
 {
@@ -169,6 +175,7 @@ constexpr bool has_drift(int d)
          : DYN == DYN_SINGLE_INT ? false
          : DYN == DYN_DUBINS3D ? d < 2
          : DYN == DYN_DUBINSCAR4D ? d < 2
+         : DYN == DYN_CAPTURE ? d < 2
          : d < 3;   // Rel6D
 }
 
@@ -179,6 +186,7 @@ constexpr bool has_bound(int d)
          : DYN == DYN_SINGLE_INT ? true
          : DYN == DYN_DUBINS3D ? d == 2
          : DYN == DYN_DUBINSCAR4D ? d >= 2
+         : DYN == DYN_CAPTURE ? d == 2
          : d >= 2;  // Rel6D
 }
 
@@ -198,6 +206,8 @@ ODP_HD void static_alpha(const GridDesc &g, const DynDesc &dy, const int *idx, f
         a[0] = fabsf(dy.prm[0] * ldgf(g.cos_tab + idx[2]));
         a[1] = fabsf(dy.prm[0] * ldgf(g.sin_tab + idx[2]));
         a[2] = dy.prm[1];
+    } else if (DYN == DYN_CAPTURE) {
+        for (int d = 0; d < ND; ++d) a[d] = 0.0f;   // every component depends on phi
     } else if (DYN == DYN_DUBINSCAR4D) {
         const float v = ldgf(g.coord[2] + idx[2]);
         a[0] = fabsf(v * ldgf(g.cos_tab + idx[3]));

@@ -94,6 +94,14 @@ ODP_HD void drift(const GridDesc &g, const DynDesc &dy, const int *idx, float cA
             cA[1][k] = v * lane(s, k);
         }
         cS[2] = su * dy.prm[1];
+    } else if (DYN == DYN_CAPTURE) {           // (x, y, th), th last (Section 4.2)
+        const float4 c = ldg4(g.cos_tab + s0), s = ldg4(g.sin_tab + s0);
+        const float v = dy.prm[0];
+        for (int k = 0; k < 4; ++k) {
+            cA[0][k] = -v + v * lane(c, k);
+            cA[1][k] = v * lane(s, k);
+        }
+        cS[2] = sd * dy.prm[2];                // pursuer turn b: S_b |pbar_th|
     } else if (DYN == DYN_DUBINSCAR4D) {       // (x, y, v, th), th last
         const float4 c = ldg4(g.cos_tab + s0), s = ldg4(g.sin_tab + s0);
         const float v = ldgf(g.coord[2] + idx[2]);
@@ -169,6 +177,39 @@ struct StageArgs {
     int stage;            // 0 Euler, 1 RK2 stage 1, 2 RK2 stage 2
     int brt;
 };
+
+// One non-last axis of a four-node segment that also returns the unscaled
+// sums P = dp + dm of its two node pairs (for the capture model's coupled
+// term).
+template <int ORDER>
+ODP_HD void segment_axis_P(const float4 &m2, const float4 &m1, const float4 &c, const float4 &p1, const float4 &p2,
+                           const float *cA, float cS, float cD, float2 &L01, float2 &L23, bool has_a, bool has_s,
+                           float2 &P01, float2 &P23)
+{
+    float2 dm, dp;
+    pair_diffs<ORDER>(make_float2(m2.x, m2.y), make_float2(m1.x, m1.y), make_float2(c.x, c.y),
+                      make_float2(p1.x, p1.y), make_float2(p2.x, p2.y), dm, dp);
+    pair_terms(dm, dp, make_float2(cA[0], cA[1]), cS, f2splat(cD), L01, has_a, has_s, &P01);
+    pair_diffs<ORDER>(make_float2(m2.z, m2.w), make_float2(m1.z, m1.w), make_float2(c.z, c.w),
+                      make_float2(p1.z, p1.w), make_float2(p2.z, p2.w), dm, dp);
+    pair_terms(dm, dp, make_float2(cA[2], cA[3]), cS, f2splat(cD), L23, has_a, has_s, &P23);
+}
+
+// The capture model's evader term (Section 4.2): the evader turn a enters
+// every axis, x' += a y, y' -= a x, th' -= a, so it contributes
+// S_a |s| with s = y pbar_x - x pbar_y - pbar_th, S_a = +-A by its mode;
+// pbar_d = P_d / (2 h_d) from the unscaled sums of each axis.
+ODP_HD void capture_term(const GridDesc &g, const DynDesc &dy, float x, float y, const float *Px, const float *Py,
+                         const float *Pth, float *L)
+{
+    const float cx = y * (0.5f * g.inv_dz[0]), cy = -x * (0.5f * g.inv_dz[1]), ct = -0.5f * g.inv_dz[2];
+    const float Sa = mode_sign(dy.umode) * dy.prm[1];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float s = fmaf(cx, Px[k], fmaf(cy, Py[k], ct * Pth[k]));
+        L[k] = fmaf(Sa, fabsf(s), L[k]);
+    }
+}
 
 // One non-last axis of a four-node segment from its neighbour rows (as two
 // pairs of nodes).
@@ -378,6 +419,7 @@ ODP_HD bool stage_tile(const GridDesc &g, const DynDesc &dy, const StageArgs &A,
         const float f[4] = {c4.x, c4.y, c4.z, c4.w};
         float2 L01 = make_float2(0.0f, 0.0f), L23 = make_float2(0.0f, 0.0f);
 
+        float2 Pc[2][2];   // capture model: unscaled sums of axes x, y (two node pairs)
         // outer axes: neighbour rows one by one
 #pragma unroll
         for (int d = 0; d < ND - 2; ++d) {
@@ -389,7 +431,10 @@ ODP_HD bool stage_tile(const GridDesc &g, const DynDesc &dy, const StageArgs &A,
                 m2 = axis_row(src, base, id, id - 2, stride, n, per);
                 p2 = axis_row(src, base, id, id + 2, stride, n, per);
             }
-            if (DYN == DYN_REL6D && d == 2 && dy.local_diss)
+            if (DYN == DYN_CAPTURE)
+                segment_axis_P<ORDER>(m2, m1, c4, p1, p2, cA[d], cS[d], A.cD[d], L01, L23, has_drift<DYN, ND>(d),
+                                      has_bound<DYN, ND>(d), Pc[0][0], Pc[0][1]);
+            else if (DYN == DYN_REL6D && d == 2 && dy.local_diss)
                 segment_axis_rel6d_theta<ORDER>(m2, m1, c4, p1, p2, cA[d], cS[d], dy, ldgf(g.coord[4] + idx[4]),
                                                 0.5f * g.inv_dz[2], L01, L23);
             else
@@ -403,8 +448,13 @@ ODP_HD bool stage_tile(const GridDesc &g, const DynDesc &dy, const StageArgs &A,
             constexpr int d = ND - 2 < 0 ? 0 : ND - 2;
             const float4 m2 = col[i + O - 2 < 0 ? 0 : i + O - 2], m1 = col[i + O - 1];
             const float4 p1 = col[i + O + 1], p2 = col[i + O + 2 < NC ? i + O + 2 : NC - 1];
-            segment_axis<ORDER>(m2, m1, c4, p1, p2, cA[d], cS[d], A.cD[d], L01, L23, has_drift<DYN, ND>(d),
-                                has_bound<DYN, ND>(d), dy.local_diss && has_drift<DYN, ND>(d) && !has_bound<DYN, ND>(d));
+            if (DYN == DYN_CAPTURE)
+                segment_axis_P<ORDER>(m2, m1, c4, p1, p2, cA[d], cS[d], A.cD[d], L01, L23, has_drift<DYN, ND>(d),
+                                      has_bound<DYN, ND>(d), Pc[1][0], Pc[1][1]);
+            else
+                segment_axis<ORDER>(m2, m1, c4, p1, p2, cA[d], cS[d], A.cD[d], L01, L23, has_drift<DYN, ND>(d),
+                                    has_bound<DYN, ND>(d),
+                                    dy.local_diss && has_drift<DYN, ND>(d) && !has_bound<DYN, ND>(d));
         }
 
         // last axis: an eight-node window w[j] = phi(first node - 2 + j)
@@ -428,7 +478,14 @@ ODP_HD bool stage_tile(const GridDesc &g, const DynDesc &dy, const StageArgs &A,
                 if (j < 2 || j >= 6 || s0 + j - 2 >= nl) w[j] = last_axis_value(rowp, s0 + j - 2, nl, per);
         }
         float L[4] = {L01.x, L01.y, L23.x, L23.y};
-        axis_last<ORDER>(w, cA[ND - 1], cS[ND - 1], A.cD[ND - 1], L, has_drift<DYN, ND>(ND - 1), has_bound<DYN, ND>(ND - 1));
+        float Pth[4];
+        axis_last<ORDER>(w, cA[ND - 1], cS[ND - 1], A.cD[ND - 1], L, has_drift<DYN, ND>(ND - 1), has_bound<DYN, ND>(ND - 1),
+                         DYN == DYN_CAPTURE ? Pth : nullptr);
+        if (DYN == DYN_CAPTURE) {
+            const float Px[4] = {Pc[0][0].x, Pc[0][0].y, Pc[0][1].x, Pc[0][1].y};
+            const float Py[4] = {Pc[1][0].x, Pc[1][0].y, Pc[1][1].x, Pc[1][1].y};
+            capture_term(g, dy, ldgf(g.coord[0] + idx[0]), ldgf(g.coord[1] + idx[1]), Px, Py, Pth, L);
+        }
 
         float4 out;
         const bool bad_here = stage_epilogue(A, base, c4, L, nvalid, out);
@@ -569,6 +626,97 @@ __global__ void __launch_bounds__(256) k_alpha_rel6d(GridDesc g, DynDesc dy, Sol
         float m = 0.0f;
         for (int w = 0; w < (blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
         atomicMax(&st->alpha_bits[slot][2], __float_as_uint(m));
+    }
+}
+
+// Capture-model alpha of phi (slot 0: cur) or phi1 (slot 1: nxt), every
+// component per stage (Section 2.1 global alpha, readings R5 and R20): at
+// each node the inputs selectable over its derivative box -- the evader turn
+// a from the interval of its switching function y p_x - x p_y - p_th, the
+// pursuer turn b from the interval of p_th -- and the largest |f_d| over
+// every combination of them.  One thread per four-node segment.
+template <int ORDER>
+__global__ void __launch_bounds__(256) k_alpha_capture(GridDesc g, DynDesc dy, SolveState *st, int slot)
+{
+    __shared__ float red[8][3];
+    const float *__restrict__ src = slot ? st->nxt : st->cur;
+    float amax[3] = {0.0f, 0.0f, 0.0f};
+    const float v = dy.prm[0], A = dy.prm[1], B = dy.prm[2];
+    const float a_up = dy.umode == MODE_MAX ? A : -A, b_up = dy.dmode == MODE_MAX ? B : -B;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < uint32_t(g.nthreads)) {
+        int idx[3];
+        const int base = segment_index<3>(g, t, idx);
+        const float4 c4 = ldg4(src + base);
+        float4 m[2][2], p[2][2];   // axis, offset 1 / 2
+        for (int d = 0; d < 2; ++d) {
+            m[d][0] = row_shift4(src, base, idx[d], g.stride[d], g.n[d], g.periodic[d], -1);
+            p[d][0] = row_shift4(src, base, idx[d], g.stride[d], g.n[d], g.periodic[d], +1);
+            m[d][1] = m[d][0];
+            p[d][1] = p[d][0];
+            if (ORDER == 2) {
+                m[d][1] = row_shift4(src, base, idx[d], g.stride[d], g.n[d], g.periodic[d], -2);
+                p[d][1] = row_shift4(src, base, idx[d], g.stride[d], g.n[d], g.periodic[d], +2);
+            }
+        }
+        const int s0 = idx[2], nl = g.n[2];
+        const float *rowp = src + (base - s0);
+        float w[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) w[j] = last_axis_value(rowp, s0 + j - 2, nl, g.periodic[2]);
+        const float x = ldgf(g.coord[0] + idx[0]), y = ldgf(g.coord[1] + idx[1]);
+        const int nvalid = min(4, nl - s0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (k >= nvalid) break;
+            float lo[3], hi[3];
+            for (int d = 0; d < 2; ++d) {
+                float dm, dp;
+                diffs<ORDER>(lane(m[d][1], k), lane(m[d][0], k), lane(c4, k), lane(p[d][0], k), lane(p[d][1], k), dm,
+                             dp);
+                lo[d] = fminf(dm, dp) * g.inv_dz[d];
+                hi[d] = fmaxf(dm, dp) * g.inv_dz[d];
+            }
+            {
+                float dm, dp;
+                diffs<ORDER>(w[k], w[k + 1], w[k + 2], w[k + 3], w[k + 4], dm, dp);
+                lo[2] = fminf(dm, dp) * g.inv_dz[2];
+                hi[2] = fmaxf(dm, dp) * g.inv_dz[2];
+            }
+            // interval of s_a = y p_x - x p_y - p_th over the box
+            const float gc[3] = {y, -x, -1.0f};
+            float slo = 0.0f, shi = 0.0f;
+            for (int d = 0; d < 3; ++d) {
+                slo += gc[d] >= 0.0f ? gc[d] * lo[d] : gc[d] * hi[d];
+                shi += gc[d] >= 0.0f ? gc[d] * hi[d] : gc[d] * lo[d];
+            }
+            float as[2], bs[2];
+            int na = 1, nb = 1;
+            if (slo > 0.0f) as[0] = a_up;
+            else if (shi < 0.0f) as[0] = -a_up;
+            else { as[0] = -A; as[1] = A; na = 2; }
+            if (lo[2] > 0.0f) bs[0] = b_up;
+            else if (hi[2] < 0.0f) bs[0] = -b_up;
+            else { bs[0] = -B; bs[1] = B; nb = 2; }
+            const float cth = ldgf(g.cos_tab + s0 + k), sth = ldgf(g.sin_tab + s0 + k);
+            for (int ia = 0; ia < na; ++ia) {
+                amax[0] = fmaxf(amax[0], fabsf(-v + v * cth + as[ia] * y));
+                amax[1] = fmaxf(amax[1], fabsf(v * sth - as[ia] * x));
+                for (int ib = 0; ib < nb; ++ib) amax[2] = fmaxf(amax[2], fabsf(bs[ib] - as[ia]));
+            }
+        }
+    }
+    const int lane_id = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        amax[d] = warp_max(amax[d]);
+        if (lane_id == 0) red[warp][d] = amax[d];
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        float mx = 0.0f;
+        for (int w2 = 0; w2 < (blockDim.x >> 5); ++w2) mx = fmaxf(mx, red[w2][threadIdx.x]);
+        atomicMax(&st->alpha_bits[slot][threadIdx.x], __float_as_uint(mx));
     }
 }
 

@@ -347,10 +347,16 @@ __global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DY
                                             local && has_drift<DYN, ND>(d) && !has_bound<DYN, ND>(d));
                 }
                 // stream axis from the register window
-                segment_axis<ORDER>(w[u % Q], w[(u + O - 1) % Q], c4, w[(u + O + 1) % Q], w[(u + Q - 1) % Q],
-                                    cA[sa], cS[sa], cD[sa], L01, L23, has_drift<DYN, ND>(sa),
-                                    has_bound<DYN, ND>(sa),
-                                    local && has_drift<DYN, ND>(sa) && !has_bound<DYN, ND>(sa));
+                float2 Pc[2][2];   // capture model: unscaled sums of axes x (stream), y (row)
+                if (DYN == DYN_CAPTURE)
+                    segment_axis_P<ORDER>(w[u % Q], w[(u + O - 1) % Q], c4, w[(u + O + 1) % Q], w[(u + Q - 1) % Q],
+                                          cA[sa], cS[sa], cD[sa], L01, L23, has_drift<DYN, ND>(sa),
+                                          has_bound<DYN, ND>(sa), Pc[0][0], Pc[0][1]);
+                else
+                    segment_axis<ORDER>(w[u % Q], w[(u + O - 1) % Q], c4, w[(u + O + 1) % Q], w[(u + Q - 1) % Q],
+                                        cA[sa], cS[sa], cD[sa], L01, L23, has_drift<DYN, ND>(sa),
+                                        has_bound<DYN, ND>(sa),
+                                        local && has_drift<DYN, ND>(sa) && !has_bound<DYN, ND>(sa));
                 // row axis from the tile; ghost rows from this column
                 {
                     float4 m1 = *reinterpret_cast<const float4 *>(C - cp);
@@ -371,9 +377,14 @@ __global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DY
                             p2 = ghost4(p1, c4, 1.0f);
                         }
                     }
-                    segment_axis<ORDER>(m2, m1, c4, p1, p2, cA[ND - 2], cS[ND - 2], cD[ND - 2], L01, L23,
-                                        has_drift<DYN, ND>(ND - 2), has_bound<DYN, ND>(ND - 2),
-                                        local && has_drift<DYN, ND>(ND - 2) && !has_bound<DYN, ND>(ND - 2));
+                    if (DYN == DYN_CAPTURE)
+                        segment_axis_P<ORDER>(m2, m1, c4, p1, p2, cA[ND - 2], cS[ND - 2], cD[ND - 2], L01, L23,
+                                              has_drift<DYN, ND>(ND - 2), has_bound<DYN, ND>(ND - 2), Pc[1][0],
+                                              Pc[1][1]);
+                    else
+                        segment_axis<ORDER>(m2, m1, c4, p1, p2, cA[ND - 2], cS[ND - 2], cD[ND - 2], L01, L23,
+                                            has_drift<DYN, ND>(ND - 2), has_bound<DYN, ND>(ND - 2),
+                                            local && has_drift<DYN, ND>(ND - 2) && !has_bound<DYN, ND>(ND - 2));
                 }
                 // last axis: window v[k] = phi(s0 - 2 + k)
                 float L[4] = {L01.x, L01.y, L23.x, L23.y};
@@ -392,8 +403,14 @@ __global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DY
                         for (int k = 2; k < 8; ++k)
                             if (s0 + k - 2 >= nl) v[k] = C[k - 2];
                     }
+                    float Pth[4];
                     axis_last<ORDER>(v, cA[ND - 1], cS[ND - 1], cD[ND - 1], L, has_drift<DYN, ND>(ND - 1),
-                                     has_bound<DYN, ND>(ND - 1));
+                                     has_bound<DYN, ND>(ND - 1), DYN == DYN_CAPTURE ? Pth : nullptr);
+                    if (DYN == DYN_CAPTURE) {
+                        const float Px[4] = {Pc[0][0].x, Pc[0][0].y, Pc[0][1].x, Pc[0][1].y};
+                        const float Py[4] = {Pc[1][0].x, Pc[1][0].y, Pc[1][1].x, Pc[1][1].y};
+                        capture_term(g, dy, ldgf(g.coord[0] + s), ldgf(g.coord[1] + r), Px, Py, Pth, L);
+                    }
                 }
                 float4 out = update_nodes(dt, stage, use_l, c4, L, px, lx, use_g, gx, nvalid, fin);
                 if (FULL || nvalid == 4) {

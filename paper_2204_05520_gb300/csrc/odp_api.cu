@@ -419,6 +419,7 @@ extern "C" odp_status odp_set_dynamics(odp_grid *g, odp_dyn kind, const double *
     case ODP_DYN_DUBINS3D: need = 2; angle = 2; nd_req = 3; break;
     case ODP_DYN_DUBINSCAR4D: need = 2; angle = 3; nd_req = 4; break;
     case ODP_DYN_REL6D: need = 4; angle = 2; nd_req = 6; break;
+    case ODP_DYN_DUBINS_CAPTURE: need = 3; angle = 2; nd_req = 3; break;
     default: return fail(ODP_EINVAL, "unknown dynamics %d", int(kind));
     }
     if (nd_req > 0 && g->ndim != nd_req)
@@ -432,6 +433,8 @@ extern "C" odp_status odp_set_dynamics(odp_grid *g, odp_dyn kind, const double *
     }
     if (angle >= 0 && !g->periodic[angle])
         return fail(ODP_EINVAL, "axis %d holds an angle and must be periodic", angle);
+    if (kind == ODP_DYN_DUBINS_CAPTURE && g->local_diss)
+        return fail(ODP_EINVAL, "per-node dissipation is not available for the capture model");
     DynDesc dy{};
     dy.kind = int(kind);
     dy.umode = int(u_mode);
@@ -453,6 +456,7 @@ extern "C" odp_status odp_set_dynamics(odp_grid *g, odp_dyn kind, const double *
     case DYN_ADVECTION: ce = configure_stage_si(g->ndim, dy.kind); break;
     case DYN_DUBINS3D:
     case DYN_DUBINSCAR4D: ce = configure_stage_dubins(g->ndim); break;
+    case DYN_CAPTURE: ce = configure_stage_capture(); break;
     default: ce = configure_stage_rel6d(); break;
     }
     if (ce != cudaSuccess) return fail(ODP_ECUDA, "configuring the stage kernels: %s", cudaGetErrorString(ce));
@@ -503,6 +507,8 @@ extern "C" odp_status odp_set_dissipation(odp_grid *g, int per_node)
 {
     if (!g) return fail(ODP_EINVAL, "grid is NULL");
     if (per_node != 0 && per_node != 1) return fail(ODP_EINVAL, "per_node must be 0 or 1");
+    if (per_node && g->has_dyn && g->dyn.kind == DYN_CAPTURE)
+        return fail(ODP_EINVAL, "per-node dissipation is not available for the capture model");
     if (g->local_diss != per_node) {
         g->local_diss = per_node;
         g->dyn.local_diss = per_node;
@@ -521,7 +527,17 @@ extern "C" odp_status odp_set_step_limit(odp_grid *g, int64_t max_steps)
 // ---------------------------------------------------------------------------
 // the time-loop graph
 // ---------------------------------------------------------------------------
-static unsigned dynamic_alpha_mask(const odp_grid *g) { return g->dyn.kind == DYN_REL6D ? (1u << 2) : 0u; }
+// alpha components that depend on phi and are reduced again every stage
+static unsigned dynamic_alpha_mask(const odp_grid *g)
+{
+    return g->dyn.kind == DYN_REL6D ? (1u << 2) : (g->dyn.kind == DYN_CAPTURE ? 7u : 0u);
+}
+
+static cudaError_t launch_alpha_dynamic(const odp_grid *g, int slot, cudaStream_t s)
+{
+    if (g->dyn.kind == DYN_CAPTURE) return launch_alpha_dynamic_capture(g->desc, g->dyn, g->state, g->order, slot, s);
+    return launch_alpha_dynamic_rel6d(g->desc, g->dyn, g->state, g->order, slot, s);
+}
 
 static cudaError_t launch_stage_any(odp_grid *g, int stage, cudaStream_t s)
 {
@@ -534,22 +550,24 @@ static cudaError_t launch_stage_any(odp_grid *g, int stage, cudaStream_t s)
     case DYN_DUBINS3D:
     case DYN_DUBINSCAR4D:
         return launch_stage_dubins(g->ndim, D, g->dyn, g->state, g->l, gob, g->order, stage, g->brt, s);
+    case DYN_CAPTURE:
+        return launch_stage_capture(D, g->dyn, g->state, g->l, gob, g->order, stage, g->brt, s);
     default:
         return launch_stage_rel6d(D, g->dyn, g->state, g->l, gob, g->order, stage, g->brt, s);
     }
 }
 
-// The kernels of one full time step, in order, on stream s: the Rel6D alpha
+// The kernels of one full time step, in order, on stream s: the per-stage alpha
 // pass, the CFL step, the stage pass(es) and the closing k_advance.  Used for
 // the captured graph body (in_graph = 1) and for the host-stepped loop.
 static cudaError_t launch_step(odp_grid *g, cudaStream_t s, cudaGraphConditionalHandle h_loop,
                                cudaGraphConditionalHandle h_snap, int in_graph, int64_t *launches)
 {
-    const bool dyn_alpha = g->dyn.kind == DYN_REL6D;
+    const bool dyn_alpha = dynamic_alpha_mask(g) != 0;
     int64_t n = 0;
     cudaError_t e = cudaSuccess;
     if (dyn_alpha) {
-        e = launch_alpha_dynamic_rel6d(g->desc, g->dyn, g->state, g->order, 0, s);
+        e = launch_alpha_dynamic(g, 0, s);
         ++n;
     }
     if (e == cudaSuccess) {
@@ -565,7 +583,7 @@ static cudaError_t launch_step(odp_grid *g, cudaStream_t s, cudaGraphConditional
             e = launch_stage_any(g, 1, s);
             ++n;
             if (e == cudaSuccess && dyn_alpha) {
-                e = launch_alpha_dynamic_rel6d(g->desc, g->dyn, g->state, g->order, 1, s);
+                e = launch_alpha_dynamic(g, 1, s);
                 ++n;
             }
             if (e == cudaSuccess) {
@@ -591,6 +609,7 @@ static cudaError_t launch_alpha_static_any(odp_grid *g, cudaStream_t s)
     case DYN_ADVECTION: return launch_alpha_static_si(g->ndim, g->desc, g->dyn, g->state, s);
     case DYN_DUBINS3D:
     case DYN_DUBINSCAR4D: return launch_alpha_static_dubins(g->ndim, g->desc, g->dyn, g->state, s);
+    case DYN_CAPTURE: return launch_alpha_static_capture(g->desc, g->dyn, g->state, s);
     default: return launch_alpha_static_rel6d(g->desc, g->dyn, g->state, s);
     }
 }
@@ -843,7 +862,7 @@ extern "C" odp_status odp_solve_status(odp_grid *g, odp_solve_stats *stats)
         double b = (g->time_order == 1) ? per_stage_rw : (2 * per_stage_rw + 4.0);
         if (g->brt) b += 4.0;
         if (g->has_obst) b += 4.0;
-        if (g->dyn.kind == DYN_REL6D) b += 4.0 * g->time_order;
+        if (dynamic_alpha_mask(g)) b += 4.0 * g->time_order;
         stats->bytes = b * double(g->total) * double(h.steps);
         stats->launches = g->launches_per_step * h.steps;
     }

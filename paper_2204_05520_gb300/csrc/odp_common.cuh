@@ -59,7 +59,8 @@ ODP_HD float bits_to_float(unsigned u)
 #endif
 }
 
-enum DynKind { DYN_SINGLE_INT = 0, DYN_DUBINS3D = 1, DYN_DUBINSCAR4D = 2, DYN_REL6D = 3, DYN_ADVECTION = 4 };
+enum DynKind { DYN_SINGLE_INT = 0, DYN_DUBINS3D = 1, DYN_DUBINSCAR4D = 2, DYN_REL6D = 3, DYN_ADVECTION = 4,
+               DYN_CAPTURE = 5 };
 enum Mode { MODE_MIN = 0, MODE_MAX = 1 };
 
 // Error flags raised on the device.

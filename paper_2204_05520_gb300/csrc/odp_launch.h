@@ -30,6 +30,16 @@ cudaError_t launch_alpha_static_dubins(int nd, const GridDesc &g, const DynDesc 
 cudaError_t launch_alpha_static_rel6d(const GridDesc &g, const DynDesc &dy, SolveState *st,
                                       cudaStream_t s);
 
+// The pursuit-evasion capture model (Section 4.2): stage pass, shared-memory
+// limits, static alpha (zero: every component is per stage) and the
+// per-stage alpha of cur (slot 0) or nxt (slot 1).
+cudaError_t launch_stage_capture(const GridDesc &g, const DynDesc &dy, SolveState *st, const float *l,
+                                 const float *gob, int order, int stage, int brt, cudaStream_t s);
+cudaError_t configure_stage_capture();
+cudaError_t launch_alpha_static_capture(const GridDesc &g, const DynDesc &dy, SolveState *st, cudaStream_t s);
+cudaError_t launch_alpha_dynamic_capture(const GridDesc &g, const DynDesc &dy, SolveState *st, int order, int slot,
+                                         cudaStream_t s);
+
 // Grid-wide max of the Rel6D heading-rate alpha of cur (slot 0) or nxt (slot 1).
 cudaError_t launch_alpha_dynamic_rel6d(const GridDesc &g, const DynDesc &dy, SolveState *st,
                                        int order, int slot, cudaStream_t s);

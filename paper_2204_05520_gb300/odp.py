@@ -18,7 +18,8 @@ import numpy as np
 from . import _build
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, ENUMERIC, EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
-DYN = {"single_integrator": 0, "dubins3d": 1, "dubinscar4d": 2, "rel6d": 3, "advection": 4}
+DYN = {"single_integrator": 0, "dubins3d": 1, "dubinscar4d": 2, "rel6d": 3, "advection": 4,
+       "dubins_capture": 5}
 MODE = {"min": 0, "max": 1}
 SET = {"brs": 0, "brt": 1}
 

@@ -418,3 +418,38 @@ def test_batch_refuses_per_node_dissipation():
         with pytest.raises(odp.OdpError) as e:
             odp.batch_solve([g], [0.5])
         assert e.value.code == odp.EINVAL
+
+
+# ---------------------------------------------------------------------------
+# the pursuit-evasion capture model of Section 4.2 (coupled switching
+# function; every alpha component reduced per stage)
+# ---------------------------------------------------------------------------
+
+CAPTURE_CASES = [
+    inputs.dubins_capture(),                                              # 40^3, the paper's grid, T = 1.5
+    inputs.dubins_capture(n=(21, 23, 18), space_order=2, time_order=2, horizon=0.5),
+    inputs.dubins_capture(n=(25, 25, 20), u_mode="min", d_mode="max", set_kind="brs", horizon=0.5),
+    inputs.reach_avoid(inputs.dubins_capture(n=(31, 29, 24), horizon=0.8),
+                       inputs.cylinder_obstacle(0.6, center=(1.5, 0.0))),
+]
+
+
+@pytest.mark.parametrize("problem", CAPTURE_CASES, ids=lambda p: "%s_o%d%d_%s_%s" % (
+    p.name, p.space_order, p.time_order, p.set_kind, p.u_mode))
+def test_capture_model_matches_oracle(problem):
+    check(problem)
+
+
+def test_capture_model_refuses_per_node_dissipation():
+    p = inputs.dubins_capture(n=(9, 9, 8))
+    with odp.Grid.for_problem(p) as g:
+        with pytest.raises(odp.OdpError) as e:
+            odp.set_dissipation(g.handle, True)
+        assert e.value.code == odp.EINVAL
+        g.set_target(p.target_values())
+        with pytest.raises(odp.OdpError) as e:
+            odp.batch_solve([g], [0.5])
+        assert e.value.code == odp.EINVAL
+    with pytest.raises(odp.OdpError) as e:
+        odp.Grid.for_problem(dataclasses.replace(p, dissipation="local"))
+    assert e.value.code == odp.EINVAL
