@@ -188,8 +188,10 @@ __device__ bool batch_item(const BatchGrid &B, int blk, int round, int phase)
 // Rounds [round0, round1) of the batch.  sorted: grid ids by step count
 // (descending); item_start: first item of each sorted grid (n + 1 entries);
 // active: active items of every round.
+// The upwind instantiations are held to 3 CTAs of 8 warps per SM (at most 85
+// registers: each SM sub-partition holds 16384 registers for its warps).
 template <int ORDER, int R>
-__global__ void __launch_bounds__(256) k_batch_run(const BatchGrid *__restrict__ bg, const int *__restrict__ sorted,
+__global__ void __launch_bounds__(256, ORDER == 1 ? 3 : 2) k_batch_run(const BatchGrid *__restrict__ bg, const int *__restrict__ sorted,
                                                    const int *__restrict__ item_start, int n,
                                                    const int *__restrict__ active, const int *__restrict__ active_rk2,
                                                    int round0, int round1, BatchBarrier *bar)
