@@ -247,6 +247,80 @@ __global__ void k_batch_finish(const BatchGrid *bg, int n)
 }
 
 // ---------------------------------------------------------------------------
+// plane-streaming rounds (Dubins3D and DubinsCar4D batches)
+// ---------------------------------------------------------------------------
+// One launch per round and RK phase covers the plane items of the grids still
+// active (a prefix of the item list, grids sorted by step count).  CTA i finds
+// its grid, copies the grid's record into shared memory and runs one item of
+// the plane pass with the grid's buffers, step and alpha of that round: the
+// same per-node arithmetic as the solo solve.
+template <int ND, int ORDER, int DYN>
+__global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DYN>()))
+    k_batch_plane(const BatchGrid *__restrict__ bg, const int *__restrict__ sorted,
+                  const int *__restrict__ item_start, int n, int round, int phase)
+{
+    __shared__ BatchGrid sB;
+    const int i = blockIdx.x;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (item_start[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    {
+        const int words = int(sizeof(BatchGrid) / 4);
+        const unsigned *srcw = reinterpret_cast<const unsigned *>(bg + sorted[lo]);
+        unsigned *dstw = reinterpret_cast<unsigned *>(&sB);
+        for (int w = threadIdx.x; w < words; w += blockDim.x) dstw[w] = srcw[w];
+    }
+    __syncthreads();
+    const BatchGrid &B = sB;
+    PlaneArgs pa;
+    const bool first = (round == 0);
+    if (B.time_order == 1) {
+        pa.stage = 0;
+        pa.src = first ? B.l : ((round & 1) ? B.b : B.a);
+        pa.dst = (round & 1) ? B.a : B.b;
+        pa.prev = pa.src;
+    } else if (phase == 0) {
+        pa.stage = 1;
+        pa.src = first ? B.l : B.a;
+        pa.dst = B.b;
+        pa.prev = pa.src;
+    } else {
+        pa.stage = 2;
+        pa.src = B.b;
+        pa.prev = first ? B.l : B.a;
+        pa.dst = B.a;
+    }
+    pa.l = B.l;
+    pa.gob = nullptr;
+    pa.alpha_bits = B.alpha_bits;
+    pa.dt = float(round == B.n_steps - 1 ? B.dt_last : B.dt_cfl);
+    pa.brt = B.brt;
+    pa.flags = &B.state->flags;
+    plane_pass<ND, ORDER, DYN, false, -1, 0>(B.g, B.dy, pa, uint32_t(i - item_start[lo]));
+}
+
+template <int ND, int DYN>
+static cudaError_t launch_plane_round(int order, int ctas, int threads, int smem, const BatchGrid *bg,
+                                      const int *sorted, const int *item_start, int n, int round, int phase,
+                                      cudaStream_t s)
+{
+    if (order == 1) {
+        cudaError_t e = cudaFuncSetAttribute(k_batch_plane<ND, 1, DYN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem);
+        if (e != cudaSuccess) return e;
+        k_batch_plane<ND, 1, DYN><<<ctas, threads, smem, s>>>(bg, sorted, item_start, n, round, phase);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_batch_plane<ND, 2, DYN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem);
+        if (e != cudaSuccess) return e;
+        k_batch_plane<ND, 2, DYN><<<ctas, threads, smem, s>>>(bg, sorted, item_start, n, round, phase);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 struct BatchWorkspace {
@@ -347,6 +421,12 @@ extern "C" odp_status odp_batch_solve(odp_grid *const *grids, int n, const doubl
         if (g->desc.R != 4) all_r4 = 0;
     }
     const int R = all_r4 ? 4 : 1;
+    // Dubins3D or DubinsCar4D batches whose grids all take the plane pass run
+    // it round by round; the others run the persistent row-blocked kernel
+    const int kind0 = grids[0]->dyn.kind;
+    bool plane = kind0 == DYN_DUBINS3D || kind0 == DYN_DUBINSCAR4D;
+    for (int i = 0; i < n && plane; ++i)
+        if (grids[i]->dyn.kind != kind0 || !grids[i]->desc.pg.use) plane = false;
     cudaStream_t s = grids[0]->stream;
     BatchWorkspace &W = workspace();
     std::lock_guard<std::mutex> lock(W.mu);
@@ -375,6 +455,17 @@ extern "C" odp_status odp_batch_solve(odp_grid *const *grids, int n, const doubl
         B.time_order = time_order;
         B.brt = set == ODP_BRT ? 1 : 0;
         B.items = (B.g.nthreads_rb + 255) / 256;
+        if (plane) {
+            // the parallelism comes from the many grids: stream-axis chunks
+            // of up to 16 planes (the single-solve geometry cuts finer)
+            PlaneGeom &pg = B.g.pg;
+            const int pencils = pg.items / (pg.nbands * pg.nchunks);
+            pg.chunk = pg.ns < 16 ? pg.ns : 16;
+            pg.nchunks = (pg.ns + pg.chunk - 1) / pg.chunk;
+            pg.items = pencils * pg.nbands * pg.nchunks;
+            pg.div_nchunks = make_fastdiv(uint32_t(pg.nchunks));
+            B.items = pg.items;
+        }
     }
     if (size_t(n) > W.cap_grids || W.device != device) {
         cudaFree(W.bg);
@@ -431,6 +522,60 @@ extern "C" odp_status odp_batch_solve(odp_grid *const *grids, int n, const doubl
     ODP_TRY_CUDA(cudaMemcpyAsync(W.ints, packed.data(), sizeof(int) * nints, cudaMemcpyHostToDevice, s));
     const int *d_sorted = W.ints, *d_start = W.ints + n, *d_active = W.ints + 2 * n + 1;
     const int *d_active_rk2 = d_active + rounds;
+
+    if (plane) {
+        int threads = 32, smem = 0;
+        for (int i = 0; i < n; ++i) {
+            threads = std::max(threads, hb[size_t(i)].g.pg.threads);
+            smem = std::max(smem, hb[size_t(i)].g.pg.smem[space_order - 1]);
+        }
+        ODP_TRY_CUDA(cudaEventRecord(W.ev0, s));
+        for (int r = 0; r < rounds; ++r) {
+            for (int phase = 0; phase < time_order; ++phase) {
+                const int ctas = phase == 0 ? active[size_t(r)] : active_rk2[size_t(r)];
+                if (ctas == 0) continue;
+                cudaError_t e = kind0 == DYN_DUBINS3D
+                                    ? launch_plane_round<3, DYN_DUBINS3D>(space_order, ctas, threads, smem, W.bg,
+                                                                          d_sorted, d_start, n, r, phase, s)
+                                    : launch_plane_round<4, DYN_DUBINSCAR4D>(space_order, ctas, threads, smem, W.bg,
+                                                                             d_sorted, d_start, n, r, phase, s);
+                ODP_TRY_CUDA(e);
+            }
+        }
+        ODP_TRY_CUDA(cudaEventRecord(W.ev1, s));
+        k_batch_finish<<<(n + 127) / 128, 128, 0, s>>>(W.bg, n);
+        ODP_TRY_CUDA(cudaGetLastError());
+        ODP_TRY_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < n; ++i) {
+            odp_grid *g = grids[i];
+            g->solved = true;
+            g->n_tau = 2;
+            g->keep = 0;
+            g->time_order = time_order;
+            g->order = space_order;
+            g->brt = set == ODP_BRT ? 1 : 0;
+            g->timed = false;
+        }
+        if (stats) {
+            memset(stats, 0, sizeof(*stats));
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, W.ev0, W.ev1);
+            stats->device_ms = ms;
+            stats->rounds = rounds;
+            stats->ctas_per_sm = 0;       // one launch per round, occupancy by the hardware
+            stats->rows_per_thread = 0;   // plane pass
+            double updates = 0.0, bytes = 0.0;
+            for (int i = 0; i < n; ++i) {
+                const double nodes = double(grids[i]->total) * double(hb[size_t(i)].n_steps);
+                updates += nodes;
+                const double per = (time_order == 1 ? 8.0 : 20.0) + (set == ODP_BRT ? 4.0 : 0.0);
+                bytes += per * nodes;
+            }
+            stats->point_updates = updates;
+            stats->bytes = bytes;
+        }
+        return ODP_OK;
+    }
 
     int sms = 0;
     ODP_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));

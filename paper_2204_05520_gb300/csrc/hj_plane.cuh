@@ -50,8 +50,7 @@ __device__ __forceinline__ float4 ghost4(const float4 &pb, const float4 &pi, flo
                        keep_sign_ghost(pb.z, pi.z, k), keep_sign_ghost(pb.w, pi.w, k));
 }
 
-// One plane-streaming stage pass.  ND >= 3.  The launch geometry (bands,
-// chunks, threads, shared bytes) is PlaneGeom, computed on the host.  FULL:
+// The plane-streaming stage pass.  ND >= 3.  FULL:
 // the last axis is a multiple of 4 nodes (no partial segment).
 //
 // Halo rows of a band: rows of the neighbouring band (or wrapped rows of a
@@ -83,12 +82,30 @@ constexpr bool plane_late_outer_loads()
     return DYN == DYN_DUBINSCAR4D && ORDER == 2;
 }
 
+// Arguments of one plane-streaming stage pass over one grid.
+struct PlaneArgs {
+    const float *src;             // phi the derivatives are taken of
+    const float *prev;            // phi^n for the Heun average (stage 2)
+    const float *l;               // target, for the BRT min
+    const float *gob;             // reach-avoid obstacle or nullptr
+    float *dst;
+    const unsigned *alpha_bits;   // alpha of this stage (float bits)
+    float dt;
+    int stage, brt;
+    int *flags;                   // FLAG_NONFINITE is or-ed in here
+};
+
+// One work item (band of plane rows x chunk of the stream axis at fixed
+// outer indices) of the plane-streaming pass; the CTA calls it with its
+// item number.  The launch geometry (bands, chunks, threads, shared bytes)
+// is PlaneGeom, computed on the host.
 template <int ND, int ORDER, int DYN, bool FULL, int STAGE, int GOB>
-__global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DYN>())) k_stage_plane(GridDesc g, DynDesc dy, SolveState *st,
-                                                     const float *__restrict__ l,
-                                                     const float *__restrict__ gob, int stage_rt, int brt)
+__device__ __forceinline__ void plane_pass(const GridDesc &g, const DynDesc &dy, const PlaneArgs &pa, uint32_t item)
 {
-    const int stage = STAGE >= 0 ? STAGE : stage_rt;
+    const int stage = STAGE >= 0 ? STAGE : pa.stage;
+    const int brt = pa.brt;
+    const float *__restrict__ l = pa.l;
+    const float *__restrict__ gob = pa.gob;
     // per-node dissipation (Algorithm 1's second loop) runs in the generic
     // instantiation only
     const bool local = STAGE < 0 && dy.local_diss != 0;
@@ -102,21 +119,20 @@ __global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DY
     const int tile = 4 + (pg.rb + 2 * O) * cp;
 
     const int tid = threadIdx.x;
-    const float *__restrict__ src = (stage == 2) ? st->nxt : st->cur;
-    float *dst = (stage == 2) ? st->cur : st->nxt;
-    const float *prev = st->cur;
-    const unsigned *ab = st->alpha_bits[stage == 2 ? 1 : 0];
+    const float *__restrict__ src = pa.src;
+    float *dst = pa.dst;
+    const float *prev = pa.prev;
+    const unsigned *ab = pa.alpha_bits;
     float cD[ND];
 #pragma unroll
     for (int d = 0; d < ND; ++d) cD[d] = 0.5f * bits_to_float(ab[d]) * g.inv_dz[d];
-    const float dt = float(st->dt);
+    const float dt = pa.dt;
     const bool use_l = brt && stage != 1;
     const bool use_g = (GOB >= 0 ? GOB == 1 : gob != nullptr) && stage != 1;   // reach-avoid obstacle
 
     // work item: chunk fastest, then band, then outer pencil.  Outer pencils
     // are numbered block by block (blocks of up to 8 indices per outer axis),
     // so CTAs that run together read each other's neighbour planes from L2.
-    const uint32_t item = blockIdx.x;
     const uint32_t q1 = fast_div(item, pg.div_nchunks);
     const int chunk = int(item - q1 * uint32_t(pg.nchunks));
     const uint32_t outer = fast_div(q1, pg.div_nbands);
@@ -452,7 +468,28 @@ __global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DY
         run(std::true_type{});
     else
         run(std::false_type{});
-    if (!(fin.x == 0.0f && fin.y == 0.0f)) atomicOr(&st->flags, FLAG_NONFINITE);
+    if (!(fin.x == 0.0f && fin.y == 0.0f)) atomicOr(pa.flags, FLAG_NONFINITE);
+}
+
+// The stage pass of a single solve: buffers, dt and alpha from its state.
+template <int ND, int ORDER, int DYN, bool FULL, int STAGE, int GOB>
+__global__ void __launch_bounds__(512) __maxnreg__((plane_max_regs<ND, ORDER, DYN>()))
+    k_stage_plane(GridDesc g, DynDesc dy, SolveState *st, const float *__restrict__ l, const float *__restrict__ gob,
+                  int stage_rt, int brt)
+{
+    const int stage = STAGE >= 0 ? STAGE : stage_rt;
+    PlaneArgs pa;
+    pa.src = (stage == 2) ? st->nxt : st->cur;
+    pa.dst = (stage == 2) ? st->cur : st->nxt;
+    pa.prev = st->cur;
+    pa.l = l;
+    pa.gob = gob;
+    pa.alpha_bits = st->alpha_bits[stage == 2 ? 1 : 0];
+    pa.dt = float(st->dt);
+    pa.stage = stage;
+    pa.brt = brt;
+    pa.flags = &st->flags;
+    plane_pass<ND, ORDER, DYN, FULL, STAGE, GOB>(g, dy, pa, blockIdx.x);
 }
 
 }  // namespace odp
