@@ -1,5 +1,6 @@
 """FP64 CPU oracle of the time-dependent HJ level-set method (Algorithm 1 of
-arXiv 2204.05520), loaded through ctypes.
+arXiv 2204.05520) and of its time-to-reach sweeping (Algorithm 2), loaded
+through ctypes.
 
 TEST INFRASTRUCTURE.  Only the test suite, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this package.  The CUDA library
@@ -29,6 +30,7 @@ DYN_IDS = {"single_integrator": 0, "dubins3d": 1, "dubinscar4d": 2, "rel6d": 3, 
 MODE_IDS = {"min": 0, "max": 1}
 SET_IDS = {"brs": 0, "brt": 1}
 MAX_INPUTS = 8
+TTR_SCHEMES = {"gauss_seidel": 0, "jacobi": 1}
 
 OK, EINVAL, ENOMEM, ETIMEOUT, ENUMERIC = 0, -1, -2, -5, -6
 
@@ -73,8 +75,11 @@ def _load():
                                      i32, i32, i32, f64, i64, P, P, P, P, P]
             lib.og_step.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, P, P, f64, i32, i32,
                                     i32, i32, P, P]
+            lib.og_ttr.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, f64, f64, i64, i32,
+                                   P, P, P]
+            lib.og_ttr_node.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, P, P]
             for f in (lib.og_spacing, lib.og_eval_dynamics, lib.og_terms, lib.og_solve,
-                      lib.og_step):
+                      lib.og_step, lib.og_ttr, lib.og_ttr_node):
                 f.restype = i32
             _lib = lib
     return _lib
@@ -262,3 +267,51 @@ def solve(problem, l=None, snapshots: bool = False, max_steps: int = 10_000_000,
         "snapshots": None if snaps is None else snaps.reshape((len(tau),) + shape),
         "steps": steps, "alpha": alpha, "last_dt": last_dt.value, "rc": rc,
     }
+
+
+def ttr(problem, l=None, eps: float = 1e-5, big: float = 1e4, max_sweeps: int = 100_000,
+        scheme: str = "gauss_seidel", raise_on_error: bool = True) -> dict:
+    """Time-to-reach function of ``problem`` by Lax-Friedrichs sweeping
+    (Algorithm 2; readings R21-R25 of ``odp_oracle.c``).
+
+    The target set is {l <= 0}; ``l`` defaults to ``problem.target_values()``
+    (float32) promoted to float64, so that target membership is decided on
+    the values the CUDA library sees.  ``problem``'s grid, dynamics and
+    parameters are used (u_mode "min", d_mode "max").  Returns dict(phi,
+    sweeps, change (max |phi - phi_old| of the last sweep), rc).
+    """
+    lib = _load()
+    p = problem
+    n_a, lo_a, hi_a, per_a = _grid_args(p.n, p.lo, p.hi, p.periodic)
+    if l is None:
+        l = p.target_values()
+    l64 = np.ascontiguousarray(l, dtype=np.float64).reshape(-1)
+    prm = np.ascontiguousarray(p.params, dtype=np.float64)
+    phi = np.zeros(l64.size)
+    sweeps = ctypes.c_int64(0)
+    change = ctypes.c_double(0.0)
+    rc = lib.og_ttr(len(n_a), _ptr(n_a), _ptr(lo_a), _ptr(hi_a), _ptr(per_a), DYN_IDS[p.dynamics],
+                    _ptr(prm), len(prm), MODE_IDS[p.u_mode], MODE_IDS[p.d_mode], _ptr(l64),
+                    float(big), float(eps), int(max_sweeps), TTR_SCHEMES[scheme], _ptr(phi),
+                    ctypes.byref(sweeps), ctypes.byref(change))
+    if rc and raise_on_error:
+        raise OracleError(rc, "ttr")
+    return {"phi": phi.reshape(tuple(p.n)), "sweeps": int(sweeps.value), "change": change.value,
+            "rc": rc}
+
+
+def ttr_node(problem, phi, idx) -> float:
+    """Algorithm 2's value for one interior node ``idx`` of ``phi``."""
+    lib = _load()
+    p = problem
+    n_a, lo_a, hi_a, per_a = _grid_args(p.n, p.lo, p.hi, p.periodic)
+    prm = np.ascontiguousarray(p.params, dtype=np.float64)
+    phi64 = np.ascontiguousarray(phi, dtype=np.float64).reshape(-1)
+    i_a = np.ascontiguousarray(idx, dtype=np.int64)
+    out = ctypes.c_double(0.0)
+    rc = lib.og_ttr_node(len(n_a), _ptr(n_a), _ptr(lo_a), _ptr(hi_a), _ptr(per_a),
+                         DYN_IDS[p.dynamics], _ptr(prm), len(prm), MODE_IDS[p.u_mode],
+                         MODE_IDS[p.d_mode], _ptr(phi64), _ptr(i_a), ctypes.byref(out))
+    if rc:
+        raise OracleError(rc, "ttr_node")
+    return out.value

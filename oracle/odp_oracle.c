@@ -1,6 +1,7 @@
 /*
  * odp_oracle.c -- plain FP64 CPU oracle of the time-dependent HJ level-set
- * method of OptimizedDP (arXiv 2204.05520), Algorithm 1.
+ * method of OptimizedDP (arXiv 2204.05520), Algorithm 1, and of its
+ * time-to-reach function by Lax-Friedrichs sweeping, Algorithm 2.
  *
  * TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the CPU
  * baseline leg of the benchmark load this library.  It shares no code, header,
@@ -51,6 +52,31 @@
  *     difference of smaller magnitude among those at i-1 and i (i and i+1);
  *     on equal magnitude the centred one (at i).  The comparison is taken in
  *     float32 (see og_one_sided).
+ *  R21 time-to-reach Hamiltonian (Section 2.2, Algorithm 2): the control
+ *     shortens and the disturbance lengthens the time, so u* = argmin_u and
+ *     d* = argmax_d of pbar . f (Algorithm 2's argmin; the equation's printed
+ *     min/max of -p.f would pick the opposite control), and the update's H is
+ *     the static Hamiltonian Hs = -pbar . f(z, u*, d*) - 1, whose zero is the
+ *     TTR equation; Algorithm 2's printed "H_i <- pbar . zdot" drops its sign
+ *     and constant (taken literally, a node next to the target never leaves
+ *     the initial large value).  sigma_d = |f_d(z, u*, d*)| per axis and
+ *     c = 1 / sum_d(sigma_d / dz_d), the multi-axis form of c = dz / sigma;
+ *     a node with sum_d(sigma_d / dz_d) = 0 keeps its value.
+ *  R22 sweep loop: repeat while max|phi - phi_old| > eps (the printed "<" is
+ *     inverted), the change taken over every node after the boundary update;
+ *     a sweep cap ends a loop that has not converged.
+ *  R23 boundary nodes (first and last node of a non-periodic axis) are not
+ *     swept; after the interior pass each non-periodic axis in turn (lower
+ *     face, then upper face) sets phi_b <- min(max(2 phi_{b+1} - phi_{b+2},
+ *     phi_{b+2}), phi_b) along that axis with the current values, so edges
+ *     and corners see the faces of earlier axes.  Periodic axes wrap and have
+ *     no boundary.  Every axis needs at least 4 nodes.
+ *  R24 Gauss-Seidel order with alternating directions (Section 5.3): sweep k
+ *     visits the nodes in nested C-order loops, axis d descending when bit d
+ *     of k mod 2^ndim is set, updating phi in place.
+ *  R25 Jacobi variant (Section 5.1: parallel updates may need more sweeps):
+ *     every interior node of a sweep is computed from the previous sweep's
+ *     values; the boundary update is that of R23.
  */
 #include <math.h>
 #include <stdint.h>
@@ -751,4 +777,183 @@ int og_solve(int ndim, const int64_t *n, const double *lo, const double *hi,
     free(phi1);
     free(L);
     return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Time-to-reach function by Lax-Friedrichs sweeping (Section 2.2, the TTR    */
+/* HJ equation and Algorithm 2; alternating directions of Section 5.3).       */
+/* Readings (also in the file header): R21 Hamiltonian and update, R22 the    */
+/* sweep loop and its stopping test, R23 boundary nodes, R24 sweep order,     */
+/* R25 the Jacobi variant.                                                    */
+/* ------------------------------------------------------------------------- */
+enum { OG_TTR_GAUSS_SEIDEL = 0, OG_TTR_JACOBI = 1 };
+
+/* Node interior to every non-periodic axis: updated by the sweep itself. */
+static int og_ttr_interior(const og_grid *g, const int64_t *idx)
+{
+    for (int d = 0; d < g->ndim; ++d)
+        if (!g->periodic[d] && (idx[d] == 0 || idx[d] == g->n[d] - 1)) return 0;
+    return 1;
+}
+
+/* phi of the neighbour one cell away along axis d (wrapping on a periodic
+ * axis; interior nodes have both neighbours inside on the other axes). */
+static double og_ttr_nb(const og_grid *g, const double *phi, const int64_t *idx, int64_t flat,
+                        int d, int off)
+{
+    int64_t j = idx[d] + off;
+    if (j < 0) j += g->n[d];
+    if (j >= g->n[d]) j -= g->n[d];
+    return phi[flat + (j - idx[d]) * g->stride[d]];
+}
+
+/* The Lax-Friedrichs value of one interior node (Algorithm 2, reading R21):
+ *   pbar_d = (phi(i+e_d) - phi(i-e_d)) / (2 dz_d)      central derivative
+ *   u*, d* = argmin_u, argmax_d pbar . f(z, u, d)       optimal inputs
+ *   Hs     = -pbar . f(z, u*, d*) - 1                   static Hamiltonian
+ *   sigma_d = |dHs/dp_d| = |f_d(z, u*, d*)|
+ *   phi_new = (-Hs + sum_d sigma_d (phi(i+e_d) + phi(i-e_d)) / (2 dz_d))
+ *             / sum_d (sigma_d / dz_d)
+ * A node whose sum_d sigma_d / dz_d is 0 keeps its value. */
+static double og_ttr_value(const og_grid *g, const og_dyn *dy, const double *phi,
+                           const int64_t *idx, int64_t flat)
+{
+    int nd = g->ndim;
+    double z[OG_MAXD], p[OG_MAXD], up[OG_MAXD], dn[OG_MAXD];
+    og_state(g, idx, z);
+    for (int d = 0; d < nd; ++d) {
+        up[d] = og_ttr_nb(g, phi, idx, flat, d, +1);
+        dn[d] = og_ttr_nb(g, phi, idx, flat, d, -1);
+        p[d] = (up[d] - dn[d]) / (2.0 * g->dz[d]);
+    }
+    double u[OG_MAXD] = {0}, dd[OG_MAXD] = {0}, f[OG_MAXD];
+    og_opt_inputs(dy, z, p, u, dd);
+    og_dynamics(dy, z, u, dd, f);
+    double pf = 0.0;
+    for (int d = 0; d < nd; ++d) pf += p[d] * f[d];
+    double Hs = -pf - 1.0;
+    double denom = 0.0, avg = 0.0;
+    for (int d = 0; d < nd; ++d) {
+        double sigma = fabs(f[d]);
+        denom += sigma / g->dz[d];
+        avg += sigma * (up[d] + dn[d]) / (2.0 * g->dz[d]);
+    }
+    if (denom == 0.0) return phi[flat];
+    return (-Hs + avg) / denom;
+}
+
+/* Boundary nodes after the interior pass (reading R23): for each
+ * non-periodic axis in order, the lower face then the upper face,
+ *   phi_b <- min(max(2 phi_{b+1} - phi_{b+2}, phi_{b+2}), phi_b)
+ * along that axis with the current values. */
+static void og_ttr_boundary(const og_grid *g, double *phi)
+{
+    int64_t idx[OG_MAXD];
+    for (int d = 0; d < g->ndim; ++d) {
+        if (g->periodic[d]) continue;
+        int64_t n = g->n[d], s = g->stride[d];
+        for (int side = 0; side < 2; ++side) {
+            int64_t b = side ? n - 1 : 0;
+            int64_t step = side ? -s : s;      /* toward the interior */
+            for (int64_t i = 0; i < g->total; ++i) {
+                og_unflatten(g, i, idx);
+                if (idx[d] != b) continue;
+                double p1 = phi[i + step], p2 = phi[i + 2 * step];
+                double e = fmax(2.0 * p1 - p2, p2);
+                phi[i] = fmin(e, phi[i]);
+            }
+        }
+    }
+}
+
+/* Flat index of the k-th node of sweep `dirs` (reading R24): nested loops in
+ * C order over y, axis d visited in descending order when bit d is set. */
+static int64_t og_ttr_order(const og_grid *g, int64_t k, unsigned dirs, int64_t *idx)
+{
+    og_unflatten(g, k, idx);
+    int64_t flat = 0;
+    for (int d = 0; d < g->ndim; ++d) {
+        if ((dirs >> d) & 1u) idx[d] = g->n[d] - 1 - idx[d];
+        flat += idx[d] * g->stride[d];
+    }
+    return flat;
+}
+
+/* Algorithm 2.  l: target function (target set T = {l <= 0}), phi starts at
+ * 0 on T and `big` elsewhere (Section 2.2).  Sweeps repeat while the largest
+ * change of a sweep exceeds eps (reading R22), at most max_sweeps times.
+ * scheme: OG_TTR_GAUSS_SEIDEL (in place, alternating directions) or
+ * OG_TTR_JACOBI (every interior node from the previous sweep's values,
+ * reading R25).  Returns OG_ETIMEOUT if max_sweeps ran out first. */
+int og_ttr(int ndim, const int64_t *n, const double *lo, const double *hi, const int *periodic,
+           int kind, const double *prm, int n_prm, int umode, int dmode, const double *l,
+           double big, double eps, int64_t max_sweeps, int scheme, double *phi_out,
+           int64_t *sweeps_out, double *change_out)
+{
+    og_grid g;
+    og_dyn dy;
+    int rc = og_setup(&g, &dy, ndim, n, lo, hi, periodic, kind, prm, n_prm, umode, dmode);
+    if (rc) return rc;
+    if (umode != OG_MIN || dmode != OG_MAX) return OG_EINVAL;
+    if (scheme != OG_TTR_GAUSS_SEIDEL && scheme != OG_TTR_JACOBI) return OG_EINVAL;
+    if (!(eps >= 0.0) || !(big > 0.0) || max_sweeps < 1) return OG_EINVAL;
+    for (int d = 0; d < ndim; ++d)
+        if (g.n[d] < 4) return OG_EINVAL;
+    int64_t N = g.total;
+    double *phi = phi_out;
+    double *old = malloc(sizeof(double) * N);
+    if (!old) return OG_ENOMEM;
+    for (int64_t i = 0; i < N; ++i) phi[i] = (l[i] <= 0.0) ? 0.0 : big;
+
+    int64_t sweeps = 0;
+    double change = 0.0;
+    rc = OG_ETIMEOUT;
+    int64_t idx[OG_MAXD];
+    while (sweeps < max_sweeps) {
+        memcpy(old, phi, sizeof(double) * N);
+        if (scheme == OG_TTR_GAUSS_SEIDEL) {
+            unsigned dirs = (unsigned)(sweeps % ((int64_t)1 << ndim));
+            for (int64_t k = 0; k < N; ++k) {
+                int64_t i = og_ttr_order(&g, k, dirs, idx);
+                if (!og_ttr_interior(&g, idx)) continue;
+                phi[i] = fmin(og_ttr_value(&g, &dy, phi, idx, i), phi[i]);
+            }
+        } else {
+            for (int64_t i = 0; i < N; ++i) {
+                og_unflatten(&g, i, idx);
+                if (!og_ttr_interior(&g, idx)) continue;
+                phi[i] = fmin(og_ttr_value(&g, &dy, old, idx, i), old[i]);
+            }
+        }
+        og_ttr_boundary(&g, phi);
+        change = 0.0;
+        for (int64_t i = 0; i < N; ++i) change = fmax(change, fabs(phi[i] - old[i]));
+        ++sweeps;
+        if (!isfinite(change)) { rc = OG_ENUMERIC; break; }
+        if (!(change > eps)) { rc = OG_OK; break; }
+    }
+    free(old);
+    if (sweeps_out) *sweeps_out = sweeps;
+    if (change_out) *change_out = change;
+    return rc;
+}
+
+/* The value Algorithm 2 gives one interior node from phi (reading R21), for
+ * tests that enumerate sweep orders themselves. */
+int og_ttr_node(int ndim, const int64_t *n, const double *lo, const double *hi, const int *periodic,
+                int kind, const double *prm, int n_prm, int umode, int dmode, const double *phi,
+                const int64_t *idx, double *value)
+{
+    og_grid g;
+    og_dyn dy;
+    int rc = og_setup(&g, &dy, ndim, n, lo, hi, periodic, kind, prm, n_prm, umode, dmode);
+    if (rc) return rc;
+    int64_t flat = 0;
+    for (int d = 0; d < ndim; ++d) {
+        if (idx[d] < 0 || idx[d] >= g.n[d]) return OG_EINVAL;
+        flat += idx[d] * g.stride[d];
+    }
+    if (!og_ttr_interior(&g, idx)) return OG_EINVAL;
+    *value = og_ttr_value(&g, &dy, phi, idx, flat);
+    return OG_OK;
 }
