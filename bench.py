@@ -37,6 +37,8 @@ UNIT = "updates/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
 FALLBACK_HBM_GBS = 6800.0
+# time-to-reach sweeping (Algorithm 2) on the grids of the paper's tables
+TTR_WORKLOADS = tuple("ttr_%s_%d" % (m, n) for m in ("dubins3d", "dubinscar4d") for n in (60, 80, 100))
 
 
 def parse_args():
@@ -46,7 +48,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=("dubinscar4d", "dubins3d", "rel6d", "dubinscar4d_reach_avoid",
-                                           "batch512", "served"),
+                                           "batch512", "served") + TTR_WORKLOADS,
                     default="dubinscar4d")
     ap.add_argument("--rates", default="10,30,100,300,1000,2000",
                     help="served workload: Poisson arrival rates (req/s)")
@@ -209,6 +211,42 @@ def oracle_sample(problem, n_steps: int):
     return problem.points * steps / secs, secs, oracle.num_threads(), steps
 
 
+def oracle_ttr_sample(problem, n_sweeps: int):
+    """Time the FP64 oracle's sweeps on the full grid, stopped by its sweep cap
+    after `n_sweeps` sweeps; returns (updates/s, seconds, threads, sweeps)."""
+    import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    r = oracle.ttr(problem, max_sweeps=n_sweeps, raise_on_error=False)
+    secs = time.perf_counter() - t0
+    # the Gauss-Seidel sweep is sequential: one core
+    return problem.points * r["sweeps"] / secs, secs, 1, r["sweeps"]
+
+
+def run_reference_ttr(args, problem):
+    for _ in range(args.warmup):
+        oracle_ttr_sample(problem, 1)
+    total_updates, total_s, threads = 0.0, 0.0, 1
+    for _ in range(args.steps):
+        ups, secs, threads, _ = oracle_ttr_sample(problem, 1)
+        total_updates += ups * secs
+        total_s += secs
+    value = total_updates / total_s
+    sample = "one sweep of the full %s grid (%d nodes) per benchmark step" % (problem.name, problem.points)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": problem.name, "method": "Lax-Friedrichs sweeping"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = rank_info()
     if rank != 0:
@@ -216,6 +254,8 @@ def run_reference(args):
     from paper_2204_05520_gb300 import inputs
 
     problem = inputs.workload(args.workload)
+    if args.workload in TTR_WORKLOADS:
+        return run_reference_ttr(args, problem)
     for _ in range(args.warmup):
         oracle_sample(problem, 1)
     total_updates, total_s, threads = 0.0, 0.0, 1
@@ -361,6 +401,108 @@ def run_ours(args):
             "e2e": e2e,
             "clocks": clocks,
             "alg_bytes_per_solve": bytes_per_solve,
+        }
+        print(json.dumps(line), flush=True)
+    grid.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_ttr(args):
+    """Time-to-reach sweeping (Algorithm 2): one benchmark step is one complete
+    solve (every sweep until the change drops to eps = 1e-5)."""
+    import numpy as np
+    import torch
+
+    from paper_2204_05520_gb300 import _build, inputs, odp
+
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    dist = dist_setup(world, True)
+    _build.build()
+    odp.load()
+    device = torch.device("cuda", local)
+    problem = inputs.workload(args.workload)
+    N = problem.points
+    l_host = problem.target_values()
+    stream = torch.cuda.Stream()
+    l_dev = torch.from_numpy(l_host).to(device)
+    grid = odp.Grid.for_problem(problem, stream=stream)
+    if args.host_loop:
+        odp.set_loop_mode(grid.handle, True)
+    grid.set_target(l_dev)
+    st = None
+    for _ in range(max(1, args.warmup)):
+        st = grid.solve_ttr(stats=True)
+    sweeps = int(st["sweeps"])
+    sampler = ClockSampler(local)
+    torch.cuda.synchronize()
+    barrier(dist)
+    sampler.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        grid.solve_ttr()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    clocks = sampler.stop()
+    ms_total = max_over_ranks(dist, ev0.elapsed_time(ev1), device)
+    last = odp.solve_status(grid.handle)   # raises if the device flagged an error
+    ms_per_step = ms_total / args.steps
+    value = world * N * sweeps / (ms_per_step / 1000.0)
+    peak, peak_kind = hbm_peak()
+    alg_bytes = float(st["bytes"])
+    achieved = alg_bytes / (ms_per_step / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_ttr_tiles (whole sweep loop timed)", "peak_source": peak_kind,
+                "alg_bytes_per_launch": alg_bytes / (sweeps * int(st["tile_planes"])),
+                "avg_launch_ms": ms_per_step / (sweeps * int(st["tile_planes"])),
+                "note": "the sweep is bounded by its serial hyperplane depth, not by bandwidth"}
+    e2e = None
+    if not args.no_e2e:
+        l_pin = torch.from_numpy(l_host).pin_memory()
+        out_pin = torch.empty_like(l_pin).pin_memory()
+        torch.cuda.synchronize()
+        barrier(dist)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            grid.set_target(l_pin)
+            grid.solve_ttr()
+            grid.readback(out_pin)
+        t_e2e = max_over_ranks(dist, time.perf_counter() - t0, device)
+        e2e = {"value": world * N * sweeps * args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N,
+               "ms_per_step": 1000.0 * t_e2e / args.steps}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        want = max(1, min(sweeps, int(2e8 // N)))
+        ups, secs, threads, nsw = oracle_ttr_sample(problem, want)
+        cpu = {"value": ups, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "%d sweeps of the full %s grid (%d nodes), %.1f s" % (nsw, problem.name, N, secs)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": problem.name, "nodes": N, "method": "Lax-Friedrichs sweeping",
+                       "order": "Gauss-Seidel, alternating directions, hyperplane wavefronts",
+                       "sweeps_per_solve": sweeps, "eps": 1e-5, "big": 1e4,
+                       "tile_planes_per_sweep": int(st["tile_planes"]),
+                       "l2": "working set (%.0f MB)%s L2 (129 MB)" % (
+                           8.0 * N / 1e6, " larger than" if 8.0 * N > 129e6 else " inside"),
+                       "parallelism": "independent solve per GPU",
+                       "sweep_loop": "host-stepped" if args.host_loop else "one CUDA graph"},
+            "gpu_launches": int(st["launches"]) * args.steps + args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+            "solve_ms": ms_per_step,
         }
         print(json.dumps(line), flush=True)
     grid.close()
@@ -528,6 +670,8 @@ def main():
         return run_batch(args)
     if args.workload == "served":
         return run_served(args)
+    if args.workload in TTR_WORKLOADS:
+        return run_ttr(args)
     return run_ours(args)
 
 

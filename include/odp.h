@@ -359,6 +359,55 @@ odp_status odp_solve_noalloc(int ndim, const int32_t *n, const double *lo, const
                              odp_mode u_mode, odp_mode d_mode, const float *l, double T, odp_set set,
                              int space_order, int time_order, double cfl, float *out, void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Time-to-reach function (Section 2.2, Algorithm 2): the static HJ equation
+ * -min_u max_d grad(phi) . f(z, u, d) = 1 outside the target set {l <= 0},
+ * phi = 0 on it, solved by Lax-Friedrichs sweeping.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t sweeps;       /* sweeps taken                                        */
+    double change;        /* largest |phi - phi_old| of the last sweep            */
+    double device_ms;     /* device time of the sweep loop (CUDA events)          */
+    double bytes;         /* algorithmic HBM bytes: one read and one write of
+                             every node per sweep                                */
+    int64_t launches;     /* kernels launched by the sweep loop                   */
+    int64_t tile_planes;  /* tile hyperplanes (launches of the interior pass) per
+                             sweep                                               */
+} odp_ttr_stats;
+
+/* Time-to-reach function of the grid's dynamics and target (Algorithm 2).
+ * phi starts at 0 on the target nodes (l <= 0, decided in float32 on the
+ * values given to odp_set_target) and at `big` elsewhere (the paper uses a
+ * large value such as 10000 for infinity).  Each sweep visits the interior
+ * nodes (those not first or last on a non-periodic axis) in the nested C-order
+ * loops of Algorithm 2, axis d descending when bit d of the sweep index mod
+ * 2^ndim is set (alternating directions, Section 5.3), and updates in place
+ *   phi_i <- min(phi_i, (1 + pbar . f(z, u*, d*)
+ *                        + sum_d sigma_d (phi(i+e_d) + phi(i-e_d)) / (2 h_d))
+ *                       / sum_d(sigma_d / h_d))
+ * with pbar the central difference of the current values, u* minimising and
+ * d* maximising pbar . f, sigma_d = |f_d(z, u*, d*)| (a node with
+ * sum_d sigma_d / h_d = 0 keeps its value).  The library evaluates the
+ * equal form (1 + sum_d w_d phi(i + sign(f_d) e_d)) / sum_d w_d, w_d =
+ * |f_d| / h_d (the smaller neighbour on an input axis), which has no
+ * cancellation in float32.  Then each non-periodic axis in
+ * turn sets its first and last nodes to min(max(2 phi_1 - phi_2, phi_2),
+ * phi_b) along that axis.  Sweeps repeat while max|phi - phi_old| > eps, at
+ * most max_sweeps times.  The GPU visits the nodes hyperplane by hyperplane,
+ * which gives every node the same neighbour values as the sequential order.
+ * The result is the grid's value: read it with odp_value_readback(g, -1, ...).
+ * Models: single integrator (1-4 dimensions), Dubins3D, DubinsCar4D, with
+ * u_mode ODP_MIN and d_mode ODP_MAX; every axis needs at least 4 nodes.
+ * The loop runs as one CUDA graph with a device-side while node
+ * (odp_set_loop_mode(g, 1): one sweep at a time from the host).
+ * stats: NULL enqueues the work and returns; non-NULL synchronises the stream
+ * and fills *stats.
+ * Errors: ODP_ESTATE (no dynamics or target), ODP_EINVAL (model, modes,
+ * dimensions, eps < 0, big not a positive finite float, max_sweeps < 1),
+ * ODP_ENOMEM, ODP_ECUDA; with stats != NULL also ODP_ETIMEOUT (max_sweeps
+ * reached first) and ODP_ENUMERIC. */
+odp_status odp_solve_ttr(odp_grid *g, double eps, double big, int64_t max_sweeps, odp_ttr_stats *stats);
+
 /* Measurement helper (no paper counterpart): launch the fused stage kernel of
  * the grid's last solve `reps` times on its stream, outside the graph, and
  * return the mean device time of one launch in *ms_out (CUDA events; the call

@@ -216,6 +216,7 @@ static void release(odp_grid *g)
     if (!g) return;
     cudaSetDevice(g->device);
     if (g->stream) cudaStreamSynchronize(g->stream);
+    ttr_release(g);
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
     if (g->capture_stream) cudaStreamDestroy(g->capture_stream);

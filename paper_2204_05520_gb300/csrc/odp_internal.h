@@ -13,6 +13,12 @@ namespace odp {
 odp_status fail(odp_status code, const char *fmt, ...);
 }  // namespace odp
 
+struct odp_grid;
+namespace odp {
+// Free the time-to-reach plan of a grid (tile lists, state, graph).
+void ttr_release(odp_grid *g);
+}  // namespace odp
+
 // Kernel arguments (grid and dynamics descriptors) are frozen into the graph
 // when it is captured, so any change of scheme or dynamics rebuilds it.
 struct GraphKey {
@@ -63,5 +69,6 @@ struct odp_grid {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int64_t launches_per_step = 0;
     int host_loop = 0;                // 1: the time loop is stepped from the host
+    void *ttr = nullptr;              // time-to-reach plan (ttr.cu), built on first use
 };
 

@@ -268,6 +268,25 @@ def workload(name: str) -> Problem:
         return rel6d()
     if name == "dubinscar4d_reach_avoid":
         return reach_avoid(dubinscar4d(), dubins_obstacle())
+    if name.startswith("ttr_"):
+        return ttr_workload(name[4:])
+    raise KeyError(name)
+
+
+TTR_SIDES = {"dubins3d": (60, 80, 100), "dubinscar4d": (60, 80, 100)}
+
+
+def ttr_workload(name: str) -> Problem:
+    """Time-to-reach grids of the paper's Section 6 tables (3D Dubins car
+    60^3-100^3, 4D Dubins car 60^4-100^4), named "dubins3d_<side>" or
+    "dubinscar4d_<side>" (any side >= 4): the Dubins models above on cubic
+    grids, cylinder target of radius 1 (the tau schedule is unused)."""
+    model, side = name.rsplit("_", 1)
+    side = int(side)
+    if model == "dubins3d":
+        return dataclasses.replace(dubins3d(n=(side,) * 3), name="ttr_dubins3d_%d" % side)
+    if model == "dubinscar4d":
+        return dataclasses.replace(dubinscar4d(n=(side,) * 4), name="ttr_dubinscar4d_%d" % side)
     raise KeyError(name)
 
 

@@ -45,6 +45,14 @@ class SolveStats(ctypes.Structure):
                 "launches": self.launches}
 
 
+class TtrStats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int64), ("change", ctypes.c_double), ("device_ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("launches", ctypes.c_int64), ("tile_planes", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class BatchStats(ctypes.Structure):
     _fields_ = [("device_ms", ctypes.c_double), ("rounds", ctypes.c_int64),
                 ("ctas_per_sm", ctypes.c_int32), ("rows_per_thread", ctypes.c_int32),
@@ -116,6 +124,7 @@ def load():
             "odp_solve_status": ([P, P], i32),
             "odp_value_readback": ([P, i32, P, i64, i32], i32),
             "odp_time_stage": ([P, i32, i32, P], i32),
+            "odp_solve_ttr": ([P, f64, f64, i64, P], i32),
             "odp_plan_geometry": ([i32, P, P, i32], i32),
             "odp_batch_solve": ([P, i32, P, i32, i32, i32, f64, P], i32),
             "odp_batch_set_autotune": ([i32], i32),
@@ -248,6 +257,15 @@ def solve_hjb(g, tau, set_kind="brt", space_order=1, time_order=1, cfl=0.8, keep
     _check(load().odp_solve_hjb(g, t, len(tau), SET[set_kind], int(space_order), int(time_order),
                                 float(cfl), 1 if keep_snapshots else 0,
                                 ctypes.byref(st) if st is not None else None), "odp_solve_hjb")
+    return st.as_dict() if st is not None else None
+
+
+def solve_ttr(g, eps=1e-5, big=1e4, max_sweeps=100000, stats=False):
+    """Enqueue the time-to-reach sweep (Algorithm 2); with ``stats`` wait for
+    it and return its statistics."""
+    st = TtrStats() if stats else None
+    _check(load().odp_solve_ttr(g, float(eps), float(big), int(max_sweeps),
+                                ctypes.byref(st) if st is not None else None), "odp_solve_ttr")
     return st.as_dict() if st is not None else None
 
 
@@ -446,3 +464,6 @@ class Grid:
 
     def readback(self, out, tau_index: int = -1):
         return value_readback(self.handle, out, tau_index)
+
+    def solve_ttr(self, eps=1e-5, big=1e4, max_sweeps=100000, stats=False):
+        return solve_ttr(self.handle, eps, big, max_sweeps, stats)
