@@ -325,6 +325,20 @@ static cudaError_t launch_plane_round(int order, int ctas, int threads, int smem
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+
+void plane_geometry_many(GridDesc &D)
+{
+    // the parallelism comes from the many grids: stream-axis chunks of up to
+    // 16 planes (the single-solve geometry cuts finer)
+    PlaneGeom &pg = D.pg;
+    if (!pg.use) return;
+    const int pencils = pg.items / (pg.nbands * pg.nchunks);
+    pg.chunk = pg.ns < 16 ? pg.ns : 16;
+    pg.nchunks = (pg.ns + pg.chunk - 1) / pg.chunk;
+    pg.items = pencils * pg.nbands * pg.nchunks;
+    pg.div_nchunks = make_fastdiv(uint32_t(pg.nchunks));
+}
+
 struct BatchWorkspace {
     std::mutex mu;
     int device = -1;
@@ -458,15 +472,8 @@ extern "C" odp_status odp_batch_solve(odp_grid *const *grids, int n, const doubl
         B.brt = set == ODP_BRT ? 1 : 0;
         B.items = (B.g.nthreads_rb + 255) / 256;
         if (plane) {
-            // the parallelism comes from the many grids: stream-axis chunks
-            // of up to 16 planes (the single-solve geometry cuts finer)
-            PlaneGeom &pg = B.g.pg;
-            const int pencils = pg.items / (pg.nbands * pg.nchunks);
-            pg.chunk = pg.ns < 16 ? pg.ns : 16;
-            pg.nchunks = (pg.ns + pg.chunk - 1) / pg.chunk;
-            pg.items = pencils * pg.nbands * pg.nchunks;
-            pg.div_nchunks = make_fastdiv(uint32_t(pg.nchunks));
-            B.items = pg.items;
+            plane_geometry_many(B.g);
+            B.items = B.g.pg.items;
         }
     }
     if (size_t(n) > W.cap_grids || W.device != device) {

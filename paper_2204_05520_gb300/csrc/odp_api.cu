@@ -140,7 +140,7 @@ static odp_status bind(const odp_grid *g)
 // two axes; a CTA streams a chunk of axis ndim-3 for fixed outer indices.  The
 // chunk length is chosen so that a launch has about four CTAs per SM.  Grids
 // whose planes do not fit in shared memory use the row-blocked pass instead.
-static void plane_geometry(GridDesc &D, int sms)
+void odp::plane_geometry(GridDesc &D, int sms)
 {
     PlaneGeom &pg = D.pg;
     pg = PlaneGeom{};

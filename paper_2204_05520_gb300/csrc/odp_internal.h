@@ -17,6 +17,12 @@ struct odp_grid;
 namespace odp {
 // Free the time-to-reach plan of a grid (tile lists, state, graph).
 void ttr_release(odp_grid *g);
+// Geometry of the plane-streaming pass of a grid (D.pg; pg.use = 0 when the
+// pass does not apply), aiming at about twelve CTAs per SM on `sms` SMs.
+void plane_geometry(GridDesc &D, int sms);
+// The same geometry for a grid advanced together with many others: stream
+// chunks of up to 16 planes (the parallelism comes from the many grids).
+void plane_geometry_many(GridDesc &D);
 }  // namespace odp
 
 // Kernel arguments (grid and dynamics descriptors) are frozen into the graph

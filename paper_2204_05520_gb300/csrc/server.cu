@@ -220,6 +220,76 @@ __global__ void __launch_bounds__(256) k_serve_run(const ServeGrid *__restrict__
     }
 }
 
+// The plane-streaming pass over the active solves of one class (model, space
+// order, time order) in round `round` of a serving step: solve g takes its
+// step step0 + round.  The same per-node arithmetic as the single solve.
+template <int ND, int ORDER, int DYN>
+__global__ void __launch_bounds__(512) __maxnreg__(((ND == 3 && ORDER == 1) ? 80 : plane_max_regs<ND, ORDER, DYN>()))
+    k_serve_plane(const ServeGrid *__restrict__ sg, const int *__restrict__ members,
+                  const int *__restrict__ item_start, int n, int round, int phase)
+{
+    __shared__ ServeGrid sB;
+    const int i = blockIdx.x;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (item_start[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    {
+        const int words = int(sizeof(ServeGrid) / 4);
+        const unsigned *srcw = reinterpret_cast<const unsigned *>(sg + members[lo]);
+        unsigned *dstw = reinterpret_cast<unsigned *>(&sB);
+        for (int w = threadIdx.x; w < words; w += blockDim.x) dstw[w] = srcw[w];
+    }
+    __syncthreads();
+    const ServeGrid &B = sB;
+    const int step = B.step0 + round;
+    const bool first = (step == 0);
+    PlaneArgs pa;
+    if (B.time_order == 1) {
+        pa.stage = 0;
+        pa.src = first ? B.l : ((step & 1) ? B.b : B.a);
+        pa.dst = (step & 1) ? B.a : B.b;
+        pa.prev = pa.src;
+    } else if (phase == 0) {
+        pa.stage = 1;
+        pa.src = first ? B.l : B.a;
+        pa.dst = B.b;
+        pa.prev = pa.src;
+    } else {
+        pa.stage = 2;
+        pa.src = B.b;
+        pa.prev = first ? B.l : B.a;
+        pa.dst = B.a;
+    }
+    pa.l = B.l;
+    pa.gob = nullptr;
+    pa.alpha_bits = B.alpha_bits;
+    pa.dt = float(step == B.n_steps - 1 ? B.dt_last : B.dt_cfl);
+    pa.brt = B.brt;
+    pa.flags = B.flags;
+    plane_pass<ND, ORDER, DYN, false, -1, 0>(B.g, B.dy, pa, uint32_t(i - item_start[lo]));
+}
+
+template <int ND, int DYN>
+static cudaError_t launch_serve_plane(int order, int ctas, int threads, int smem, const ServeGrid *sg,
+                                      const int *members, const int *item_start, int n, int round, int phase,
+                                      cudaStream_t s)
+{
+    if (order == 1) {
+        cudaError_t e = cudaFuncSetAttribute(k_serve_plane<ND, 1, DYN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem);
+        if (e != cudaSuccess) return e;
+        k_serve_plane<ND, 1, DYN><<<ctas, threads, smem, s>>>(sg, members, item_start, n, round, phase);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_serve_plane<ND, 2, DYN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem);
+        if (e != cudaSuccess) return e;
+        k_serve_plane<ND, 2, DYN><<<ctas, threads, smem, s>>>(sg, members, item_start, n, round, phase);
+    }
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // device arena: first-fit blocks inside one allocation made at creation
 // ---------------------------------------------------------------------------
@@ -399,6 +469,8 @@ static void describe(Request &r, float *block, size_t tab_floats, size_t arr_flo
     D.planes = int(rows / D.nr);
     D.nthreads_rb = D.segs * D.row_groups * D.planes;
     D.div_row_groups = make_fastdiv(uint32_t(D.row_groups));
+    plane_geometry(D, 152);
+    plane_geometry_many(D);
     DynDesc &dy = r.rec.dy;
     dy = DynDesc{};
     dy.kind = r.kind;
@@ -615,25 +687,6 @@ extern "C" odp_status odp_server_step(odp_server *s, int rounds, int *n_done)
     };
     std::stable_sort(sorted.begin(), sorted.end(), [&](int x, int y) { return remaining(x) > remaining(y); });
     const int launch_rounds = std::min(rounds, remaining(sorted[0]));
-    std::vector<int> packed;
-    packed.reserve(size_t(n) * 2 + 1 + size_t(launch_rounds));
-    packed.insert(packed.end(), sorted.begin(), sorted.end());
-    int acc = 0, any_rk2 = 0;
-    packed.push_back(0);
-    for (int k = 0; k < n; ++k) {
-        const Request &r = s->reqs.at(s->resident[size_t(sorted[size_t(k)])]);
-        acc += r.rec.items;
-        packed.push_back(acc);
-        any_rk2 |= r.time_order == 2;
-    }
-    {
-        int k = n;
-        for (int rr = 0; rr < launch_rounds; ++rr) {
-            while (k > 0 && remaining(sorted[size_t(k) - 1]) <= rr) --k;
-            packed.push_back(packed[size_t(n) + size_t(k)]);
-        }
-    }
-    ODP_SRV_CUDA(cudaMemcpyAsync(s->d_ints, packed.data(), sizeof(int) * packed.size(), cudaMemcpyHostToDevice, st));
     // the step offsets and schedules of every record
     for (int i = 0; i < n; ++i) {
         const Request &r = s->reqs.at(s->resident[size_t(i)]);
@@ -646,16 +699,117 @@ extern "C" odp_status odp_server_step(odp_server *s, int rounds, int *n_done)
     // flags are per launch slot: cleared before every launch (a failure is
     // kept in the request's host state once read back)
     ODP_SRV_CUDA(cudaMemsetAsync(s->d_flags, 0, sizeof(int) * size_t(n), st));
-    const int *d_sorted = s->d_ints, *d_start = s->d_ints + n, *d_active = s->d_ints + 2 * n + 1;
-    int ctas = s->per_sm * s->sms;
-    if (ctas > acc) ctas = std::max(1, acc);
-    const ServeGrid *rec_arg = s->d_rec;
-    ServeBarrier *bar_arg = s->d_bar;
-    int n_arg = n, rk2_arg = any_rk2, rounds_arg = launch_rounds;
-    void *args[] = {(void *)&rec_arg, (void *)&d_sorted, (void *)&d_start, (void *)&n_arg, (void *)&d_active,
-                    (void *)&rk2_arg, (void *)&rounds_arg, (void *)&bar_arg};
-    ODP_SRV_CUDA(cudaLaunchCooperativeKernel((const void *)k_serve_run<4>, dim3(ctas), dim3(256), args, 0, st));
-    s->launches += 1;
+
+    // When every resident grid takes the plane-streaming pass, each round
+    // (and RK phase) is one launch per class of solves (model, space order,
+    // time order); otherwise one persistent cooperative launch of the
+    // row-blocked pass runs all rounds.
+    bool plane = true;
+    for (int i = 0; i < n && plane; ++i)
+        if (!s->reqs.at(s->resident[size_t(i)]).rec.g.pg.use) plane = false;
+    if (plane) {
+        struct Cls {
+            int kind, order, time_order, threads = 32, smem = 0;
+            std::vector<int> members, start, active;
+        };
+        std::vector<Cls> cls;
+        for (int k = 0; k < n; ++k) {
+            const int i = sorted[size_t(k)];
+            const Request &r = s->reqs.at(s->resident[size_t(i)]);
+            size_t c = 0;
+            while (c < cls.size() &&
+                   !(cls[c].kind == r.kind && cls[c].order == r.order && cls[c].time_order == r.time_order))
+                ++c;
+            if (c == cls.size()) {
+                Cls nc;
+                nc.kind = r.kind;
+                nc.order = r.order;
+                nc.time_order = r.time_order;
+                nc.start.push_back(0);
+                cls.push_back(nc);
+            }
+            Cls &C = cls[c];
+            C.members.push_back(i);
+            C.start.push_back(C.start.back() + r.rec.g.pg.items);
+            C.threads = std::max(C.threads, r.rec.g.pg.threads);
+            C.smem = std::max(C.smem, r.rec.g.pg.smem[r.order - 1]);
+        }
+        std::vector<int> packed;
+        std::vector<size_t> off(cls.size());
+        for (size_t c = 0; c < cls.size(); ++c) {
+            Cls &C = cls[c];
+            off[c] = packed.size();
+            packed.insert(packed.end(), C.members.begin(), C.members.end());
+            packed.insert(packed.end(), C.start.begin(), C.start.end());
+            // members are in order of remaining steps: round rr's active
+            // items are a prefix
+            C.active.assign(size_t(launch_rounds), 0);
+            int k = int(C.members.size());
+            for (int rr = 0; rr < launch_rounds; ++rr) {
+                while (k > 0 && remaining(C.members[size_t(k) - 1]) <= rr) --k;
+                C.active[size_t(rr)] = C.start[size_t(k)];
+            }
+        }
+        if (packed.size() > s->cap_ints) {
+            cudaFree(s->d_ints);
+            s->d_ints = nullptr;
+            s->cap_ints = 0;
+            ODP_SRV_CUDA(cudaMalloc(&s->d_ints, sizeof(int) * packed.size() * 2));
+            s->cap_ints = packed.size() * 2;
+        }
+        ODP_SRV_CUDA(cudaMemcpyAsync(s->d_ints, packed.data(), sizeof(int) * packed.size(), cudaMemcpyHostToDevice, st));
+        for (int rr = 0; rr < launch_rounds; ++rr) {
+            for (int phase = 0; phase < 2; ++phase) {
+                for (size_t c = 0; c < cls.size(); ++c) {
+                    const Cls &C = cls[c];
+                    if (phase == 1 && C.time_order != 2) continue;
+                    const int ctas = C.active[size_t(rr)];
+                    if (ctas == 0) continue;
+                    const int nc = int(C.members.size());
+                    const int *d_members = s->d_ints + off[c], *d_start = d_members + nc;
+                    cudaError_t e = C.kind == ODP_DYN_DUBINS3D
+                                        ? launch_serve_plane<3, DYN_DUBINS3D>(C.order, ctas, C.threads, C.smem,
+                                                                              s->d_rec, d_members, d_start, nc, rr,
+                                                                              phase, st)
+                                        : launch_serve_plane<4, DYN_DUBINSCAR4D>(C.order, ctas, C.threads, C.smem,
+                                                                                 s->d_rec, d_members, d_start, nc, rr,
+                                                                                 phase, st);
+                    ODP_SRV_CUDA(e);
+                    s->launches += 1;
+                }
+            }
+        }
+    } else {
+        std::vector<int> packed;
+        packed.reserve(size_t(n) * 2 + 1 + size_t(launch_rounds));
+        packed.insert(packed.end(), sorted.begin(), sorted.end());
+        int acc = 0, any_rk2 = 0;
+        packed.push_back(0);
+        for (int k = 0; k < n; ++k) {
+            const Request &r = s->reqs.at(s->resident[size_t(sorted[size_t(k)])]);
+            acc += r.rec.items;
+            packed.push_back(acc);
+            any_rk2 |= r.time_order == 2;
+        }
+        {
+            int k = n;
+            for (int rr = 0; rr < launch_rounds; ++rr) {
+                while (k > 0 && remaining(sorted[size_t(k) - 1]) <= rr) --k;
+                packed.push_back(packed[size_t(n) + size_t(k)]);
+            }
+        }
+        ODP_SRV_CUDA(cudaMemcpyAsync(s->d_ints, packed.data(), sizeof(int) * packed.size(), cudaMemcpyHostToDevice, st));
+        const int *d_sorted = s->d_ints, *d_start = s->d_ints + n, *d_active = s->d_ints + 2 * n + 1;
+        int ctas = s->per_sm * s->sms;
+        if (ctas > acc) ctas = std::max(1, acc);
+        const ServeGrid *rec_arg = s->d_rec;
+        ServeBarrier *bar_arg = s->d_bar;
+        int n_arg = n, rk2_arg = any_rk2, rounds_arg = launch_rounds;
+        void *args[] = {(void *)&rec_arg, (void *)&d_sorted, (void *)&d_start, (void *)&n_arg, (void *)&d_active,
+                        (void *)&rk2_arg, (void *)&rounds_arg, (void *)&bar_arg};
+        ODP_SRV_CUDA(cudaLaunchCooperativeKernel((const void *)k_serve_run<4>, dim3(ctas), dim3(256), args, 0, st));
+        s->launches += 1;
+    }
     std::vector<int> flags(static_cast<size_t>(n));
     ServeBarrier hbar{};
     ODP_SRV_CUDA(cudaMemcpyAsync(flags.data(), s->d_flags, sizeof(int) * size_t(n), cudaMemcpyDeviceToHost, st));

@@ -76,8 +76,30 @@ def test_results_are_the_same_alone_and_in_the_mix():
             ref = solo(p)
             l = p.target_values()
             assert np.abs(v - ref).max() <= REL_TOL * float(l.max() - l.min())
+            # the same per-node arithmetic as the single solve
+            assert np.array_equal(v, ref)
             srv.release(ids[k])
         assert srv.info()["used_bytes"] == 0
+
+
+def test_row_blocked_fallback_in_the_mix():
+    # a grid whose last axis is too long for the plane-streaming pass sends
+    # the whole step to the persistent row-blocked kernel; every result still
+    # equals its solo solve
+    problems = [inputs.dubins3d(n=(6, 7, 520), horizon=0.3),
+                inputs.dubins3d(n=(21, 21, 20), horizon=0.4),
+                inputs.dubinscar4d(n=(10, 11, 9, 12), horizon=0.3)]
+    with odp.Server(hbm_budget_bytes=64 << 20) as srv:
+        ids = [srv.submit(p) for p in problems]
+        steps = 0
+        while any(srv.poll(i)["state"] < odp.REQ_DONE for i in ids):
+            srv.step(rounds=8)
+            steps += 1
+            assert steps < 1000
+        for i, p in zip(ids, problems):
+            v = srv.readback(i, np.empty(p.n, np.float32))
+            assert np.array_equal(v, solo(p))
+            srv.release(i)
 
 
 def test_admission_respects_the_budget():
