@@ -172,44 +172,10 @@ __global__ void __launch_bounds__(TTR_MAX_THREADS) k_ttr_tiles(GridDesc g, DynDe
             r /= tg.NT[d];
         }
     }
-    // tile and face halo into shared memory (edges and corners are not read)
-    for (int q = threadIdx.x; q < tg.hvol; q += blockDim.x) {
-        int r = q, outside = 0;
-        int a[ND];
-#pragma unroll
-        for (int d = ND - 1; d >= 0; --d) {
-            const int e = tg.T[d] + 2;
-            a[d] = r % e - 1;
-            r /= e;
-            outside += (a[d] < 0 || a[d] >= tg.T[d]) ? 1 : 0;
-        }
-        if (outside > 1) continue;
-        bool ok = true;
-        int addr = 0;
-#pragma unroll
-        for (int d = 0; d < ND; ++d) {
-            int y = t[d] * tg.T[d] + a[d];
-            const int n = g.n[d];
-            if (y < 0 || y >= n) {
-                if (!g.periodic[d]) {
-                    ok = false;
-                    break;
-                }
-                y = y < 0 ? y + n : y - n;
-                if (y < 0 || y >= n) {
-                    ok = false;
-                    break;
-                }
-            }
-            const int x = ((dirs >> d) & 1u) ? n - 1 - y : y;
-            addr += x * g.stride[d];
-        }
-        if (ok) sh[q] = phi[addr];
-    }
-
-    // this thread's node
-    int a[ND], x[ND], pos = 0, level = 0, addr = 0;
-    bool mine = threadIdx.x < unsigned(tg.tvol);
+    // this thread's slot of the tile
+    int a[ND], y[ND], x[ND], pos = 0, level = 0, addr = 0;
+    const bool inside = threadIdx.x < unsigned(tg.tvol);
+    bool mine = inside;
     {
         int r = threadIdx.x;
 #pragma unroll
@@ -219,20 +185,67 @@ __global__ void __launch_bounds__(TTR_MAX_THREADS) k_ttr_tiles(GridDesc g, DynDe
         }
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
-            const int y = t[d] * tg.T[d] + a[d];
+            y[d] = t[d] * tg.T[d] + a[d];
             const int n = g.n[d];
-            if (y >= n) mine = false;
-            x[d] = ((dirs >> d) & 1u) ? n - 1 - y : y;
+            if (y[d] >= n) mine = false;
+            x[d] = ((dirs >> d) & 1u) ? n - 1 - y[d] : y[d];
             if (!g.periodic[d] && (x[d] <= 0 || x[d] >= n - 1)) mine = false;
             pos += (a[d] + 1) * tg.hs[d];
             level += a[d];
             addr += x[d] * g.stride[d];
         }
     }
-    float w[ND], den = 0.0f;
+    // The shared copy: every thread loads its own slot (a slot past the end
+    // of a periodic axis holds the wrapped node) and, on a tile face, the
+    // face halo slot beyond it; slots outside a non-periodic axis are never
+    // read and stay unloaded.
+    if (inside) {
+#pragma unroll
+        for (int k = -1; k < ND; ++k) {
+            // k = -1: the own slot; k = 0 .. ND-1: the halo below (a = 0) or
+            // above (a = T - 1) along axis k
+            int off = 0, shift = 0;
+            if (k >= 0) {
+                if (a[k] == 0) {
+                    off = -tg.hs[k];
+                    shift = -1;
+                } else if (a[k] == tg.T[k] - 1) {
+                    off = tg.hs[k];
+                    shift = 1;
+                } else {
+                    continue;
+                }
+            }
+            bool ok = true;
+            int src = 0;
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                int yy = y[d] + (d == k ? shift : 0);
+                const int n = g.n[d];
+                if (yy < 0 || yy >= n) {
+                    if (!g.periodic[d]) {
+                        ok = false;
+                        break;
+                    }
+                    yy = yy < 0 ? yy + n : yy - n;
+                    if (yy < 0 || yy >= n) {
+                        ok = false;
+                        break;
+                    }
+                }
+                src += (((dirs >> d) & 1u) ? n - 1 - yy : yy) * g.stride[d];
+            }
+            if (ok) sh[pos + off] = phi[src];
+        }
+    }
+    float w[ND], inv_den = 0.0f;
     bool fwd[ND];
-    if (mine) ttr_node_terms<DYN, ND>(g, dy, x, w, fwd, den);
-    if (!(den > 0.0f)) mine = false;   // sum_d sigma_d / h_d = 0: the node keeps its value
+    if (mine) {
+        float den;
+        ttr_node_terms<DYN, ND>(g, dy, x, w, fwd, den);
+        if (den > 0.0f) inv_den = 1.0f / den;
+        else mine = false;   // sum_d sigma_d / h_d = 0: the node keeps its value
+    }
     // offset of phi(x + e_d) in the shared copy
     int o[ND];
 #pragma unroll
@@ -250,7 +263,7 @@ __global__ void __launch_bounds__(TTR_MAX_THREADS) k_ttr_tiles(GridDesc g, DynDe
                 num = fmaf(w[d], nb, num);
             }
             const float old = sh[pos];
-            const float v = fminf(num / den, old);
+            const float v = fminf(num * inv_den, old);
             sh[pos] = v;
             change = old - v;
         }
