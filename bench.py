@@ -37,6 +37,7 @@ UNIT = "updates/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, nominal
 # time-to-reach sweeping (Algorithm 2) on the grids of the paper's tables
 TTR_WORKLOADS = tuple("ttr_%s_%d" % (m, n) for m in ("dubins3d", "dubinscar4d") for n in (60, 80, 100))
 
@@ -197,6 +198,21 @@ def barrier(dist):
 # CPU oracle: baseline sample and the reference arm
 # ---------------------------------------------------------------------------
 
+def cpu_model() -> str:
+    """The host CPU's model name (from /proc/cpuinfo), or the machine type."""
+    import platform
+
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
 def oracle_sample(problem, n_steps: int):
     """Time the FP64 oracle on the full workload, stopped by its step limit
     after `n_steps` time steps; returns (updates/s, seconds, threads, steps)."""
@@ -240,7 +256,7 @@ def run_reference_ttr(args, problem):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": problem.name, "method": "Lax-Friedrichs sweeping"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -272,7 +288,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": problem.name},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -346,7 +362,8 @@ def run_ours(args):
     peak, peak_kind = hbm_peak()
     achieved = bytes_per_solve / (ms_per_step / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": dram_traffic(problem.name),
+                "frac": achieved / peak, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+                "traffic": dram_traffic(problem.name),
                 "kernel": "k_stage_plane (whole time loop timed)", "peak_source": peak_kind,
                 "alg_bytes_per_launch": bytes_per_solve / stage_launches,
                 "avg_launch_ms": ms_per_step / stage_launches,
@@ -378,7 +395,17 @@ def run_ours(args):
         ups, secs, threads, nst = oracle_sample(problem, 5)
         cpu = {"value": ups, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "%d time steps of the full %s grid (%d nodes), %.1f s" % (
-                   nst, problem.name, N, secs)}
+                   nst, problem.name, N, secs),
+               "cpu_model": cpu_model()}
+        if args.workload in ("dubins3d", "dubinscar4d"):
+            # the same oracle on one core (one time step of the full grid)
+            import oracle
+
+            oracle.set_threads(1)
+            ups1, secs1, _, nst1 = oracle_sample(problem, 1 if N > 1e6 else 10)
+            oracle.set_threads(threads)
+            cpu["single_core"] = {"value": ups1, "unit": UNIT, "cores": 1,
+                                  "sample": "%d time step(s) of the full grid, %.1f s" % (nst1, secs1)}
 
     if rank == 0:
         line = {
@@ -401,6 +428,7 @@ def run_ours(args):
             "e2e": e2e,
             "clocks": clocks,
             "alg_bytes_per_solve": bytes_per_solve,
+            "solves_per_s": world * 1000.0 / ms_per_step,
         }
         print(json.dumps(line), flush=True)
     grid.close()
