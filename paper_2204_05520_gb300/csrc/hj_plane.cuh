@@ -244,8 +244,10 @@ __device__ __forceinline__ void plane_pass(const GridDesc &g, const DynDesc &dy,
     drift<DYN, ND>(g, dy, idx, cA, cS);
     // the budget-capped passes keep the two drift rows in shared memory
     // (after the two tiles, 32 bytes per thread) and reload them each plane
+    // (only active threads touch them: a batched launch may run more threads
+    // than this grid's geometry counts, and its shared bytes are sized by it)
     float4 *cA_sm = reinterpret_cast<float4 *>(smem + 2 * tile) + 2 * tid;
-    if (LATE) {
+    if (LATE && active) {
         cA_sm[0] = make_float4(cA[0][0], cA[0][1], cA[0][2], cA[0][3]);
         cA_sm[1] = make_float4(cA[1][0], cA[1][1], cA[1][2], cA[1][3]);
     }
