@@ -56,6 +56,8 @@ def parse_args():
     ap.add_argument("--window", type=float, default=3.0,
                     help="served workload: seconds of arrivals per rate (at most 2000 requests)")
     ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--max-resident-mnodes", type=float, default=0.0,
+                    help="served workload: cap on the grid nodes of resident solves, millions (0: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dissipation", choices=("global", "local"), default="global",
@@ -621,6 +623,7 @@ def run_served(args):
     points = []
     budget = int(args.budget_gb * (1 << 30))
     with odp.Server(budget, stream=stream) as srv:
+        srv.set_max_resident(int(args.max_resident_mnodes * 1e6))
         for rate in rates:
             count = int(min(2000, max(10, rate * args.window)))
             stream_reqs = inputs.served_requests(rate, count=count, seed=1)
@@ -683,7 +686,8 @@ def run_served(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": "served_poisson_dubins3d_dubinscar4d", "budget_gb": args.budget_gb,
-                           "window_s": args.window, "rounds_per_launch": 8},
+                           "window_s": args.window, "rounds_per_launch": 8,
+                           "max_resident_nodes": int(args.max_resident_mnodes * 1e6)},
                 "rates": points, "one_at_a_time_solves_per_s": single,
                 "speedup_vs_one_at_a_time": best / single if single else None}
         print(json.dumps(line), flush=True)

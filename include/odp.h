@@ -308,11 +308,21 @@ odp_status odp_server_destroy(odp_server *s);
  * alone exceeds the budget). */
 odp_status odp_server_submit(odp_server *s, const odp_request *req, uint64_t *req_id);
 
+/* Cap the work in flight: admission stops while the resident (admitted,
+ * unfinished) solves hold max_nodes grid nodes or more, and a request that
+ * would take them past the cap waits (unless nothing is resident).
+ * max_nodes = 0 (the default) admits whatever fits the HBM budget.  Above
+ * saturation a cap keeps queued requests waiting in arrival order instead of
+ * slowing every resident solve.  Errors: ODP_EINVAL (negative cap). */
+odp_status odp_server_set_max_resident(odp_server *s, int64_t max_nodes);
+
 /* One scheduling step: admit queued requests in arrival order while their
- * arrays fit the budget, advance every resident solve by up to `rounds` of its
- * own time steps in one persistent launch, retire the solves that reached
- * their horizon (their values stay in HBM).  *n_done (may be NULL) counts the
- * requests finished by this step.  Synchronises the stream.
+ * arrays fit the budget (and the resident-node cap), advance every resident
+ * solve by up to `rounds` of its own time steps (one plane-streaming launch
+ * per round and class of solves, or one persistent launch of the row-blocked
+ * pass when a resident grid cannot take the plane pass), retire the solves
+ * that reached their horizon (their values stay in HBM).  *n_done (may be
+ * NULL) counts the requests finished by this step.  Synchronises the stream.
  * Errors: ODP_EINVAL, ODP_ECUDA. */
 odp_status odp_server_step(odp_server *s, int rounds, int *n_done);
 

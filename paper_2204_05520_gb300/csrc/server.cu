@@ -390,6 +390,7 @@ struct odp_server {
     size_t cap_rec = 0, cap_ints = 0;
     int per_sm = 0, sms = 0;
     int64_t launches = 0;
+    int64_t max_nodes = 0;             // resident-node cap (0: none)
     std::mutex mu;
 };
 
@@ -585,6 +586,14 @@ extern "C" odp_status odp_server_submit(odp_server *s, const odp_request *q, uin
     return ODP_OK;
 }
 
+extern "C" odp_status odp_server_set_max_resident(odp_server *s, int64_t max_nodes)
+{
+    if (!s || max_nodes < 0) return fail(ODP_EINVAL, "need a server and a cap >= 0");
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->max_nodes = max_nodes;
+    return ODP_OK;
+}
+
 extern "C" odp_status odp_server_step(odp_server *s, int rounds, int *n_done)
 {
     if (!s || rounds < 1) return fail(ODP_EINVAL, "need a server and rounds >= 1");
@@ -593,10 +602,19 @@ extern "C" odp_status odp_server_step(odp_server *s, int rounds, int *n_done)
     cudaStream_t st = s->stream;
     if (n_done) *n_done = 0;
 
-    // 1. admission in arrival order while the arrays fit the budget
+    // 1. admission in arrival order while the arrays fit the budget and the
+    // resident nodes stay within the cap
     std::vector<uint64_t> fresh;
+    auto nodes_of = [](const Request &r) {
+        int64_t v = 1;
+        for (int d = 0; d < r.ndim; ++d) v *= r.n[d];
+        return v;
+    };
+    int64_t in_flight = 0;
+    for (uint64_t id : s->resident) in_flight += nodes_of(s->reqs.at(id));
     while (!s->queue.empty()) {
         Request &r = s->reqs.at(s->queue.front());
+        if (s->max_nodes > 0 && !s->resident.empty() && in_flight + nodes_of(r) > s->max_nodes) break;
         size_t tf, af;
         const size_t need = request_bytes(r, &tf, &af);
         const size_t off = s->arena->take(need);
@@ -614,6 +632,7 @@ extern "C" odp_status odp_server_step(odp_server *s, int rounds, int *n_done)
                                        size_t(nl) * 4, size_t(nl) * 4, size_t(r.rec.g.rows), cudaMemcpyHostToDevice,
                                        st));
         r.state = ODP_REQ_RESIDENT;
+        in_flight += nodes_of(r);
         r.t_admit = now_s();
         r.done_steps = 0;
         s->resident.push_back(r.id);

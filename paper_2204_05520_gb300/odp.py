@@ -136,6 +136,7 @@ def load():
             "odp_server_readback": ([P, ctypes.c_uint64, P, i64, i32], i32),
             "odp_server_release": ([P, ctypes.c_uint64], i32),
             "odp_server_info": ([P, P], i32),
+            "odp_server_set_max_resident": ([P, i64], i32),
             "odp_solve_noalloc": ([i32, P, P, P, P, i32, P, i32, i32, i32, P, f64, i32, i32, i32, f64,
                                    P, P], i32),
         }
@@ -369,6 +370,10 @@ class Server:
         rid = ctypes.c_uint64()
         _check(load().odp_server_submit(self.handle, ctypes.byref(q), ctypes.byref(rid)), "odp_server_submit")
         return rid.value
+
+    def set_max_resident(self, max_nodes: int):
+        """Cap the grid nodes of resident (admitted, unfinished) solves; 0: none."""
+        _check(load().odp_server_set_max_resident(self.handle, int(max_nodes)), "odp_server_set_max_resident")
 
     def step(self, rounds: int = 8) -> int:
         done = ctypes.c_int(0)

@@ -133,3 +133,29 @@ def test_unsupported_and_oversized_requests_are_refused():
         with pytest.raises(odp.OdpError) as e:
             srv.submit(inputs.dubins3d(n=(101, 101, 101)))
         assert e.value.code == odp.ENOMEM
+
+
+def test_resident_cap_admits_in_arrival_order():
+    p = inputs.dubins3d(n=(31, 31, 32), horizon=0.5)
+    nodes = 31 * 31 * 32
+    ref = solo(p)
+    with odp.Server(hbm_budget_bytes=256 << 20) as srv:
+        srv.set_max_resident(int(nodes * 2.5))
+        ids = [srv.submit(p) for _ in range(5)]
+        srv.step(rounds=1)
+        info = srv.info()
+        assert info["resident"] == 2 and info["queued"] == 3
+        steps = 0
+        while any(srv.poll(i)["state"] < odp.REQ_DONE for i in ids):
+            srv.step(rounds=16)
+            steps += 1
+            assert srv.info()["resident"] <= 2
+            assert steps < 1000
+        done = [srv.poll(i)["t_done"] for i in ids]
+        assert done == sorted(done)          # first come, first served
+        for i in ids:
+            assert np.array_equal(srv.readback(i, np.empty(p.n, np.float32)), ref)
+            srv.release(i)
+        with pytest.raises(odp.OdpError) as e:
+            srv.set_max_resident(-1)
+        assert e.value.code == odp.EINVAL
