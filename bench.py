@@ -201,9 +201,16 @@ def barrier(dist):
 # ---------------------------------------------------------------------------
 
 def cpu_model() -> str:
-    """The host CPU's model name (from /proc/cpuinfo), or the machine type."""
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or the machine type."""
     import platform
 
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip().lower() == "model name":
+                return "%s (%s)" % (line.split(":", 1)[1].strip(), platform.machine())
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         with open("/proc/cpuinfo") as fh:
             for line in fh:
