@@ -337,7 +337,7 @@ def run_ours(args):
             grid.solve_problem(problem)
     st = odp.solve_status(grid.handle)
     steps_per_solve = int(st["steps"])
-    launches_per_solve = int(st["launches"]) + 1   # + the once-per-solve alpha reduction
+    launches_per_solve = int(st["launches"])   # the once-per-solve launches included
     bytes_per_solve = float(st["bytes"])
 
     sampler = ClockSampler(local)

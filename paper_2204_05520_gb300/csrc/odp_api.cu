@@ -72,9 +72,12 @@ __global__ void k_dt(SolveState *st, GridDesc g)
 
 // Close a full step: advance t, count it, swap the Euler ping-pong buffers,
 // clear the phi-dependent alpha components, move to the next tau segment
-// when this one is done, and set the loop and snapshot conditions.
-__global__ void k_advance(SolveState *st, int swap, unsigned dyn_mask, cudaGraphConditionalHandle h_loop,
-                          cudaGraphConditionalHandle h_snap, int keep, int in_graph)
+// when this one is done, and set the loop and snapshot conditions.  With
+// next_dt (models whose alpha does not depend on phi) it also takes the next
+// step's CFL step, which k_dt would otherwise compute at the top of the step.
+__global__ void k_advance(SolveState *st, GridDesc g, int swap, unsigned dyn_mask, int next_dt,
+                          cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_snap, int keep,
+                          int in_graph)
 {
     for (int d = 0; d < 8; ++d) st->alpha_last[d] = st->alpha_bits[swap ? 0 : 1][d];
     st->t = after_step(st->t, st->dt, st->t_end, st->last);
@@ -106,6 +109,12 @@ __global__ void k_advance(SolveState *st, int swap, unsigned dyn_mask, cudaGraph
     }
     st->go = go;
     st->snap_now = snap;
+    if (next_dt && go) {
+        const double dt_cfl = cfl_dt(st->alpha_bits[0], g.dz, g.ndim, st->cfl);
+        int last = 0;
+        st->dt = clipped_step(dt_cfl, st->t, st->t_end, &last);
+        st->last = last;
+    }
     if (in_graph) {
         cudaGraphSetConditional(h_loop, go);
         if (keep) cudaGraphSetConditional(h_snap, snap);
@@ -571,7 +580,9 @@ static cudaError_t launch_step(odp_grid *g, cudaStream_t s, cudaGraphConditional
         e = launch_alpha_dynamic(g, 0, s);
         ++n;
     }
-    if (e == cudaSuccess) {
+    // phi-independent alpha: the step's dt comes from the previous step's
+    // k_advance (or, for the first step, the k_dt launched before the loop)
+    if (e == cudaSuccess && dyn_alpha) {
         k_dt<<<1, 1, 0, s>>>(g->state, g->desc);
         ++n;
         e = cudaGetLastError();
@@ -594,8 +605,8 @@ static cudaError_t launch_step(odp_grid *g, cudaStream_t s, cudaGraphConditional
         }
     }
     if (e == cudaSuccess) {
-        k_advance<<<1, 1, 0, s>>>(g->state, g->time_order == 1 ? 1 : 0, dynamic_alpha_mask(g), h_loop, h_snap,
-                                  g->keep, in_graph);
+        k_advance<<<1, 1, 0, s>>>(g->state, g->desc, g->time_order == 1 ? 1 : 0, dynamic_alpha_mask(g),
+                                  dyn_alpha ? 0 : 1, h_loop, h_snap, g->keep, in_graph);
         ++n;
         e = cudaGetLastError();
     }
@@ -806,6 +817,10 @@ extern "C" odp_status odp_solve_hjb(odp_grid *g, const double *tau, int n_tau, o
     ODP_CUDA(cudaMemcpyAsync(g->phi_a, g->l, bytes, cudaMemcpyDeviceToDevice, st));
     if (g->keep) ODP_CUDA(cudaMemcpyAsync(g->snapshots, g->l, bytes, cudaMemcpyDeviceToDevice, st));
     ODP_CUDA(launch_alpha_static_any(g, st));
+    if (!dynamic_alpha_mask(g)) {   // the first step's dt (later ones: k_advance)
+        k_dt<<<1, 1, 0, st>>>(g->state, g->desc);
+        ODP_CUDA(cudaGetLastError());
+    }
     g->timed = stats != nullptr;
     if (g->timed) ODP_CUDA(cudaEventRecord(g->ev0, st));
     if (g->host_loop) {
@@ -865,7 +880,8 @@ extern "C" odp_status odp_solve_status(odp_grid *g, odp_solve_stats *stats)
         if (g->has_obst) b += 4.0;
         if (dynamic_alpha_mask(g)) b += 4.0 * g->time_order;
         stats->bytes = b * double(g->total) * double(h.steps);
-        stats->launches = g->launches_per_step * h.steps;
+        // the once-per-solve alpha reduction (and first k_dt) included
+        stats->launches = g->launches_per_step * h.steps + (dynamic_alpha_mask(g) ? 1 : 2);
     }
     return status_of(h);
 }
