@@ -159,3 +159,51 @@ def test_resident_cap_admits_in_arrival_order():
         with pytest.raises(odp.OdpError) as e:
             srv.set_max_resident(-1)
         assert e.value.code == odp.EINVAL
+
+
+def test_cancelled_busy_and_failed_requests():
+    p = inputs.dubins3d(n=(31, 31, 32), horizon=0.5)
+    per = 4 * 3 * 31 * 31 * 32
+
+    def state(srv, rid):
+        try:
+            return srv.poll(rid)["state"]
+        except odp.OdpError as e:          # a failed request reports ODP_ENUMERIC
+            assert e.code == odp.ENUMERIC
+            return odp.REQ_FAILED
+
+    with odp.Server(hbm_budget_bytes=int(per * 2.5) + (1 << 16)) as srv:
+        ids = [srv.submit(p) for _ in range(4)]
+        srv.step(rounds=1)
+        assert srv.info()["resident"] == 2 and srv.info()["queued"] == 2
+        # a queued request can be cancelled; a running one cannot
+        srv.release(ids[3])
+        assert srv.info()["queued"] == 1
+        with pytest.raises(odp.OdpError) as e:
+            srv.poll(ids[3])
+        assert e.value.code == odp.EINVAL
+        with pytest.raises(odp.OdpError) as e:
+            srv.release(ids[0])
+        assert e.value.code == odp.EBUSY
+        # a target holding a NaN: the device flags the solve, the others finish
+        bad = p.target_values().copy()
+        bad[15, 15, 5] = np.nan
+        rb = srv.submit(p, target=bad)
+        ref = solo(p)
+        pending, outcome, steps = set(ids[:3] + [rb]), {}, 0
+        while pending:
+            srv.step(rounds=16)
+            steps += 1
+            assert steps < 1000
+            for i in list(pending):
+                st = state(srv, i)
+                if st >= odp.REQ_DONE:
+                    # finished requests hold their HBM until released
+                    if st == odp.REQ_DONE:
+                        assert np.array_equal(srv.readback(i, np.empty(p.n, np.float32)), ref)
+                    outcome[i] = st
+                    srv.release(i)
+                    pending.discard(i)
+        assert outcome[rb] == odp.REQ_FAILED
+        assert all(outcome[i] == odp.REQ_DONE for i in ids[:3])
+        assert srv.info()["used_bytes"] == 0
