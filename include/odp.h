@@ -221,24 +221,28 @@ odp_status odp_value_readback(odp_grid *g, int tau_index, float *dst, int64_t n_
  * advanced together).
  * ------------------------------------------------------------------------ */
 typedef struct {
-    double device_ms;      /* device time of the persistent launch            */
+    double device_ms;      /* device time of the batch's launches             */
     int64_t rounds;        /* lockstep rounds (the largest step count)        */
-    int32_t ctas_per_sm;   /* launch shape chosen by the autotuner            */
+    int32_t ctas_per_sm;   /* launch shape chosen by the autotuner (0: the
+                              plane-streaming rounds, occupancy by hardware)  */
     int32_t rows_per_thread;
     double point_updates;  /* sum over grids of nodes x steps                  */
     double bytes;          /* algorithmic HBM bytes                            */
 } odp_batch_stats;
 
-/* Solve n independent grids over [0, T[i]] in one persistent cooperative
- * launch.  Every grid must have its dynamics and target set and live on the
- * same device; work is issued on grids[0]'s stream and the call synchronises
- * it.  Each grid takes exactly the step sequence of a single odp_solve_hjb
- * over tau = {0, T[i]} (same float64 step schedule, same per-node kernel
- * arithmetic) and its final value is read back with odp_value_readback(g, -1).
- * Supported models: Dubins3D, DubinsCar4D, and the 2-3D single integrator
- * (Rel6D needs a per-stage alpha pass and is refused).  The launch shape
- * (CTAs per SM) is autotuned on the first rounds of a batch and cached per
- * batch signature.  stats may be NULL.
+/* Solve n independent grids over [0, T[i]] together.  Every grid must have
+ * its dynamics and target set and live on the same device; work is issued on
+ * grids[0]'s stream and the call synchronises it.  Each grid takes exactly
+ * the step sequence of a single odp_solve_hjb over tau = {0, T[i]} (same
+ * float64 step schedule, same per-node kernel arithmetic) and its final value
+ * is read back with odp_value_readback(g, -1).  When every grid is a Dubins3D
+ * or DubinsCar4D grid that the plane-streaming pass takes, each round (step
+ * index) and RK phase is one launch over every grid still running; other
+ * batches run one persistent cooperative launch of the row-blocked pass, its
+ * shape (CTAs per SM) autotuned on the first rounds and cached per batch
+ * signature.  Supported models: Dubins3D, DubinsCar4D, and the 2-3D single
+ * integrator (Rel6D needs a per-stage alpha pass and is refused; so are grids
+ * with an obstacle or per-node dissipation).  stats may be NULL.
  * Errors: ODP_EINVAL, ODP_ESTATE, ODP_ENOMEM, ODP_ECUDA. */
 odp_status odp_batch_solve(odp_grid *const *grids, int n, const double *T, odp_set set, int space_order,
                            int time_order, double cfl, odp_batch_stats *stats);
