@@ -196,3 +196,56 @@ def test_ttr_sweep_order_matches_enumeration(case):
         r = oracle.ttr(p, max_sweeps=k + 1, eps=0.0, raise_on_error=False)
         assert r["sweeps"] == k + 1
         assert np.array_equal(r["phi"], phi), "sweep %d" % k
+
+
+@pytest.mark.parametrize("case", ["si3", "dubins3d", "dubinscar4d"])
+def test_ttr_update_equals_its_upwind_weighted_form(case):
+    # With sigma_d = |f_d(z, u*, d*)| each axis's Lax-Friedrichs part equals
+    # |f_d| / h_d times the neighbour the flow points to (the smaller one on
+    # an input axis), so Algorithm 2's update equals
+    # (1 + sum_d w_d phi_nb(d)) / sum_d w_d, w_d = |f_d| / h_d -- the
+    # cancellation-free form the CUDA kernel evaluates.  Checked here in
+    # float64 against the oracle's printed form at random nodes of random
+    # fields.
+    rng = np.random.Generator(np.random.PCG64(11))
+    if case == "si3":
+        p = chebyshev_square((7, 8, 9), u_max=1.3)
+    elif case == "dubins3d":
+        p = inputs.dubins3d(n=(9, 8, 12), v=1.4, w_max=0.7)
+    else:
+        p = inputs.dubinscar4d(n=(7, 6, 5, 8), a_max=0.8, w_max=1.2)
+    nd = p.ndim
+    dz = [(p.hi[d] - p.lo[d]) / (p.n[d] if p.periodic[d] else p.n[d] - 1) for d in range(nd)]
+    axes = p.nodes()
+    for _ in range(40):
+        phi = rng.uniform(0.0, 10.0, size=p.n)
+        idx = tuple(int(rng.integers(0 if p.periodic[d] else 1, p.n[d] if p.periodic[d] else p.n[d] - 1))
+                    for d in range(nd))
+        up, dn = [], []
+        for d in range(nd):
+            i_up, i_dn = list(idx), list(idx)
+            i_up[d] = (idx[d] + 1) % p.n[d]
+            i_dn[d] = (idx[d] - 1) % p.n[d]
+            up.append(phi[tuple(i_up)])
+            dn.append(phi[tuple(i_dn)])
+        # flow components and which axes a bounded input drives
+        if case == "si3":
+            drift, inp = [None] * nd, [p.params[0]] * nd
+        elif case == "dubins3d":
+            th = axes[2][idx[2]]
+            drift = [p.params[0] * np.cos(th), p.params[0] * np.sin(th), None]
+            inp = [None, None, p.params[1]]
+        else:
+            v, th = axes[2][idx[2]], axes[3][idx[3]]
+            drift = [v * np.cos(th), v * np.sin(th), None, None]
+            inp = [None, None, p.params[0], p.params[1]]
+        num, den = 1.0, 0.0
+        for d in range(nd):
+            if inp[d] is not None:
+                w, nb = inp[d] / dz[d], min(up[d], dn[d])
+            else:
+                w, nb = abs(drift[d]) / dz[d], (up[d] if drift[d] >= 0 else dn[d])
+            num += w * nb
+            den += w
+        got = oracle.ttr_node(p, phi, idx)
+        assert abs(got - num / den) <= 1e-12 * max(1.0, abs(got)), (idx, got, num / den)
