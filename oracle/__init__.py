@@ -73,13 +73,14 @@ def _load():
                                      P, P, P, P, P, P, P, P]
             lib.og_solve.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, P, P, P, i32, i32,
                                      i32, i32, i32, f64, i64, P, P, P, P, P]
+            lib.og_solve_seq.argtypes = lib.og_solve.argtypes
             lib.og_step.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, P, P, f64, i32, i32,
                                     i32, i32, P, P]
             lib.og_ttr.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, f64, f64, i64, i32,
                                    P, P, P]
             lib.og_ttr_node.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, P, P]
             for f in (lib.og_spacing, lib.og_eval_dynamics, lib.og_terms, lib.og_solve,
-                      lib.og_step, lib.og_ttr, lib.og_ttr_node):
+                      lib.og_solve_seq, lib.og_step, lib.og_ttr, lib.og_ttr_node):
                 f.restype = i32
             _lib = lib
     return _lib
@@ -227,13 +228,16 @@ def step(problem, phi, dt, l=None, g=None) -> dict:
 
 
 def solve(problem, l=None, snapshots: bool = False, max_steps: int = 10_000_000,
-          raise_on_error: bool = True, phi0=None, g=None) -> dict:
+          raise_on_error: bool = True, phi0=None, g=None, l_seq=None, g_seq=None) -> dict:
     """Run the full solve of ``problem`` (an ``inputs.Problem``).
 
     ``l`` defaults to ``problem.target_values()`` (float32) promoted to float64.
     ``g`` (optional) is an obstacle (reach-avoid); it defaults to the
     problem's own obstacle, if it has one.
     ``phi0`` (optional) is the value to start from instead of ``l``.
+    ``l_seq`` / ``g_seq`` (optional, shape (n_tau,) + grid) are time-varying
+    target and obstacle sets, one per tau (reading R26); with ``l_seq`` the
+    solve starts from ``l_seq[0]``.
     Returns dict(final, snapshots (or None), steps (per segment), alpha,
     last_dt, rc).
     """
@@ -253,9 +257,17 @@ def solve(problem, l=None, snapshots: bool = False, max_steps: int = 10_000_000,
     steps = np.zeros(len(tau) - 1, dtype=np.int64)
     alpha = np.zeros(len(n_a))
     last_dt = ctypes.c_double(0.0)
-    rc = lib.og_solve(len(n_a), _ptr(n_a), _ptr(lo_a), _ptr(hi_a), _ptr(per_a),
+    if l_seq is not None:
+        ls = np.ascontiguousarray(l_seq, dtype=np.float64).reshape(len(tau), -1)
+        gs = None if g_seq is None else np.ascontiguousarray(g_seq, dtype=np.float64).reshape(len(tau), -1)
+        fn, a_l, a_g = lib.og_solve_seq, ls, gs
+    else:
+        if g_seq is not None:
+            raise ValueError("g_seq needs l_seq")
+        fn, a_l, a_g = lib.og_solve, l64, g64
+    rc = fn(len(n_a), _ptr(n_a), _ptr(lo_a), _ptr(hi_a), _ptr(per_a),
                       DYN_IDS[p.dynamics], _ptr(prm), len(prm), MODE_IDS[p.u_mode],
-                      MODE_IDS[p.d_mode], _ptr(l64), _ptr(g64), _ptr(p0), _ptr(tau), len(tau),
+                      MODE_IDS[p.d_mode], _ptr(a_l), _ptr(a_g), _ptr(p0), _ptr(tau), len(tau),
                       SET_IDS[p.set_kind],
                       p.space_order, p.time_order, _local(p), float(p.cfl), int(max_steps), _ptr(snaps),
                       _ptr(final), _ptr(steps), _ptr(alpha), ctypes.byref(last_dt))

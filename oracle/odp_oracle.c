@@ -48,6 +48,12 @@
  *     phi <- max(phi, g), taken after the BRT min with l (target first, then
  *     obstacle, in the order the solver options list them); g is
  *     time-invariant here.
+ *  R26 time-varying target and obstacle (Section 2.1's time-varying variants,
+ *     the target and obstacle computation methods of Section 4.3): with the
+ *     sets sampled at every tau, l_k = l(., tau_k) and g_k = g(., tau_k), phi
+ *     starts from l_0 and every step of segment (tau_k, tau_k+1] takes its
+ *     post-step min with l_k+1 and max with g_k+1, the sets at the end of the
+ *     segment in which the step lands.
  *  R10 ENO2: p- = D-phi + (h/2) c, p+ = D+phi - (h/2) c', c (c') the second
  *     difference of smaller magnitude among those at i-1 and i (i and i+1);
  *     on equal magnitude the centred one (at i).  The comparison is taken in
@@ -702,13 +708,13 @@ int og_step(int ndim, const int64_t *n, const double *lo, const double *hi, cons
  *  alpha_out   NULL or ndim doubles: alpha of the last stage
  *  last_dt     NULL or the last step's dt
  */
-int og_solve(int ndim, const int64_t *n, const double *lo, const double *hi,
-             const int *periodic, int kind, const double *prm, int n_prm, int umode,
-             int dmode, const double *l, const double *obst, const double *phi0,
-             const double *tau, int n_tau,
-             int set_kind, int space_order, int time_order, int local_alpha, double cfl, int64_t max_steps,
-             double *snapshots, double *final_out, int64_t *steps_out,
-             double *alpha_out, double *last_dt)
+static int og_solve_impl(int ndim, const int64_t *n, const double *lo, const double *hi,
+                         const int *periodic, int kind, const double *prm, int n_prm, int umode,
+                         int dmode, const double *l, const double *obst, const double *l_seq,
+                         const double *g_seq, const double *phi0, const double *tau, int n_tau,
+                         int set_kind, int space_order, int time_order, int local_alpha, double cfl,
+                         int64_t max_steps, double *snapshots, double *final_out, int64_t *steps_out,
+                         double *alpha_out, double *last_dt)
 {
     og_grid g;
     og_dyn dy;
@@ -727,7 +733,7 @@ int og_solve(int ndim, const int64_t *n, const double *lo, const double *hi,
     double *phi1 = malloc(sizeof(double) * N);
     double *L = malloc(sizeof(double) * N);
     if (!phi || !phi1 || !L) { free(phi); free(phi1); free(L); return OG_ENOMEM; }
-    memcpy(phi, phi0 ? phi0 : l, sizeof(double) * N);
+    memcpy(phi, phi0 ? phi0 : (l_seq ? l_seq : l), sizeof(double) * N);
     if (snapshots) memcpy(snapshots, phi, sizeof(double) * N);
 
     double alpha[OG_MAXD] = {0}, alpha2[OG_MAXD] = {0};
@@ -737,6 +743,9 @@ int og_solve(int ndim, const int64_t *n, const double *lo, const double *hi,
     for (int k = 0; k + 1 < n_tau && rc == OG_OK; ++k) {
         double t = tau[k], t_end = tau[k + 1];
         int64_t seg_steps = 0;
+        /* sets of this segment: time-varying ones at its end (reading R26) */
+        const double *lk = l_seq ? l_seq + (int64_t)(k + 1) * N : l;
+        const double *gk = g_seq ? g_seq + (int64_t)(k + 1) * N : obst;
         while (t_end - t > 1e-12 * t_end) {
             if (total_steps >= max_steps) { rc = OG_ETIMEOUT; break; }
             /* stage 1: alpha, dt, phi1 = phi + dt L(phi) */
@@ -756,8 +765,8 @@ int og_solve(int ndim, const int64_t *n, const double *lo, const double *hi,
             int bad = 0;
             for (int64_t i = 0; i < N; ++i) {
                 double v = phi1[i];
-                if (set_kind == OG_BRT && l[i] < v) v = l[i];
-                if (obst && obst[i] > v) v = obst[i];
+                if (set_kind == OG_BRT && lk[i] < v) v = lk[i];
+                if (gk && gk[i] > v) v = gk[i];
                 if (!isfinite(v)) bad = 1;
                 phi[i] = v;
             }
@@ -777,6 +786,37 @@ int og_solve(int ndim, const int64_t *n, const double *lo, const double *hi,
     free(phi1);
     free(L);
     return rc;
+}
+
+int og_solve(int ndim, const int64_t *n, const double *lo, const double *hi,
+             const int *periodic, int kind, const double *prm, int n_prm, int umode,
+             int dmode, const double *l, const double *obst, const double *phi0,
+             const double *tau, int n_tau,
+             int set_kind, int space_order, int time_order, int local_alpha, double cfl, int64_t max_steps,
+             double *snapshots, double *final_out, int64_t *steps_out,
+             double *alpha_out, double *last_dt)
+{
+    return og_solve_impl(ndim, n, lo, hi, periodic, kind, prm, n_prm, umode, dmode, l, obst, NULL, NULL, phi0,
+                         tau, n_tau, set_kind, space_order, time_order, local_alpha, cfl, max_steps, snapshots,
+                         final_out, steps_out, alpha_out, last_dt);
+}
+
+/* og_solve with time-varying sets (reading R26): l_seq (target) and g_seq
+ * (obstacle, or NULL) hold n_tau arrays each, the sets at tau[0..n_tau-1];
+ * phi starts from l_seq[0] (or phi0) and the steps of segment k take the
+ * post-step min / max with l_seq[k+1] / g_seq[k+1]. */
+int og_solve_seq(int ndim, const int64_t *n, const double *lo, const double *hi,
+                 const int *periodic, int kind, const double *prm, int n_prm, int umode,
+                 int dmode, const double *l_seq, const double *g_seq, const double *phi0,
+                 const double *tau, int n_tau,
+                 int set_kind, int space_order, int time_order, int local_alpha, double cfl, int64_t max_steps,
+                 double *snapshots, double *final_out, int64_t *steps_out,
+                 double *alpha_out, double *last_dt)
+{
+    if (!l_seq) return OG_EINVAL;
+    return og_solve_impl(ndim, n, lo, hi, periodic, kind, prm, n_prm, umode, dmode, l_seq, NULL, l_seq, g_seq,
+                         phi0, tau, n_tau, set_kind, space_order, time_order, local_alpha, cfl, max_steps,
+                         snapshots, final_out, steps_out, alpha_out, last_dt);
 }
 
 /* ------------------------------------------------------------------------- */
