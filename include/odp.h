@@ -162,6 +162,24 @@ odp_status odp_set_target(odp_grid *g, const float *l, int64_t n_elems, int on_d
  * odp_batch_solve.  Errors: ODP_EINVAL, ODP_ENOMEM. */
 odp_status odp_set_obstacle(odp_grid *g, const float *gv, int64_t n_elems, int on_device);
 
+/* Time-varying target (Section 2.1's time-varying variants; the target and
+ * obstacle computation methods of Section 4.3): n_sets = n_tau arrays of
+ * n_elems = odp_grid_points(g) floats, l_seq[k] the target at tau[k], dense C
+ * order one after the other (on_device as for odp_set_target).  A solve then
+ * starts from l_seq[0] and every step of segment (tau[k], tau[k+1]] takes its
+ * BRT min with l_seq[k+1], the set at the end of the segment it lands in.
+ * The schedule replaces the grid's target (odp_set_target replaces the
+ * schedule again); l_seq == NULL removes it.  Solves whose n_tau differs from
+ * n_sets are refused, and so are batched solves and the time-to-reach sweep
+ * on a grid with a schedule.  Errors: ODP_EINVAL, ODP_ENOMEM, ODP_ECUDA. */
+odp_status odp_set_target_schedule(odp_grid *g, const float *l_seq, int n_sets, int64_t n_elems, int on_device);
+
+/* Time-varying obstacle: as odp_set_target_schedule, g_seq[k] the obstacle
+ * at tau[k]; the steps of segment (tau[k], tau[k+1]] take their max with
+ * g_seq[k+1].  It replaces the grid's obstacle (odp_set_obstacle replaces it
+ * again); g_seq == NULL removes the obstacle.  Errors: as above. */
+odp_status odp_set_obstacle_schedule(odp_grid *g, const float *g_seq, int n_sets, int64_t n_elems, int on_device);
+
 /* Lax-Friedrichs dissipation of later solves (no change to the CFL step):
  * per_node = 0 (default) uses the grid alpha, the largest rate over the grid
  * per component (Section 2.1); per_node = 1 uses each node's own alpha_i, the

@@ -425,6 +425,7 @@ extern "C" odp_status odp_batch_solve(odp_grid *const *grids, int n, const doubl
         if (!g) return fail(ODP_EINVAL, "grid %d is NULL", i);
         if (!g->has_dyn || !g->has_target) return fail(ODP_ESTATE, "grid %d lacks dynamics or target", i);
         if (g->has_obst) return fail(ODP_EINVAL, "grid %d has an obstacle: the batched solve has no reach-avoid", i);
+        if (g->l_seq_n) return fail(ODP_EINVAL, "grid %d has a target schedule: the batched solve takes one target", i);
         if (g->local_diss)
             return fail(ODP_EINVAL, "grid %d uses per-node dissipation: the batched solve uses the grid alpha", i);
         if (g->device != device) return fail(ODP_EINVAL, "grid %d is on another device", i);

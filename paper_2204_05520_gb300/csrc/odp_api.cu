@@ -77,7 +77,7 @@ __global__ void k_dt(SolveState *st, GridDesc g)
 // step's CFL step, which k_dt would otherwise compute at the top of the step.
 __global__ void k_advance(SolveState *st, GridDesc g, int swap, unsigned dyn_mask, int next_dt,
                           cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_snap, int keep,
-                          int in_graph)
+                          cudaGraphConditionalHandle h_seq, int seq, int in_graph)
 {
     for (int d = 0; d < 8; ++d) st->alpha_last[d] = st->alpha_bits[swap ? 0 : 1][d];
     st->t = after_step(st->t, st->dt, st->t_end, st->last);
@@ -92,21 +92,24 @@ __global__ void k_advance(SolveState *st, GridDesc g, int swap, unsigned dyn_mas
             st->alpha_bits[0][d] = 0u;
             st->alpha_bits[1][d] = 0u;
         }
-    int go = 1, snap = 0;
+    int go = 1, snap = 0, next_sets = 0;
     if (segment_done(st->t, st->t_end)) {
         snap = keep;
         st->snap_index = st->seg + 1;
         st->seg += 1;
-        if (st->seg >= st->n_seg)
+        if (st->seg >= st->n_seg) {
             go = 0;
-        else
+        } else {
             st->t_end = st->tau[st->seg + 1];
+            next_sets = seq;   // time-varying sets: load the new segment's
+        }
     }
     if (st->flags) go = 0;
     if (go && st->steps >= st->max_steps) {
         st->flags |= FLAG_TIMEOUT;
         go = 0;
     }
+    if (!go) next_sets = 0;
     st->go = go;
     st->snap_now = snap;
     if (next_dt && go) {
@@ -118,6 +121,21 @@ __global__ void k_advance(SolveState *st, GridDesc g, int swap, unsigned dyn_mas
     if (in_graph) {
         cudaGraphSetConditional(h_loop, go);
         if (keep) cudaGraphSetConditional(h_snap, snap);
+        if (seq) cudaGraphSetConditional(h_seq, next_sets);
+    }
+}
+
+// Time-varying sets: the target and obstacle of segment seg (the sets at its
+// end, tau[seg + 1]) into the buffers the stage kernels read.
+__global__ void k_seq_sets(const SolveState *st, float *l, const float *l_seq, float *obst, const float *g_seq,
+                           int total_pad)
+{
+    const long long k = st->seg + 1;
+    const float *ls = l_seq ? l_seq + k * total_pad : nullptr;
+    const float *gs = g_seq ? g_seq + k * total_pad : nullptr;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total_pad; i += gridDim.x * blockDim.x) {
+        if (ls) l[i] = ls[i];
+        if (gs) obst[i] = gs[i];
     }
 }
 
@@ -235,6 +253,8 @@ static void release(odp_grid *g)
     cudaFree(g->phi_b);
     cudaFree(g->l);
     cudaFree(g->obst);
+    cudaFree(g->l_seq);
+    cudaFree(g->g_seq);
     cudaFree(g->tables);
     cudaFree(g->state);
     cudaFree(g->tau);
@@ -484,12 +504,98 @@ extern "C" odp_status odp_set_target(odp_grid *g, const float *l, int64_t n_elem
                                size_t(g->n_last) * sizeof(float), size_t(g->rows),
                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));
     g->has_target = true;
+    if (g->l_seq_n) {   // a time-invariant target replaces a schedule
+        g->l_seq_n = 0;
+        g->sched_version += 1;
+    }
+    return ODP_OK;
+}
+
+// n_sets dense arrays of n_elems floats into the padded layout at *dst
+// (grown to hold them; padding lanes zero).
+static odp_status copy_sets(odp_grid *g, float **dst, int *cap, const float *src, int n_sets, int64_t n_elems,
+                            int on_device, const char *what)
+{
+    if (n_sets < 2) return fail(ODP_EINVAL, "a %s schedule needs a set per tau (at least 2)", what);
+    if (n_elems != g->total) return fail(ODP_EINVAL, "%s sets have %lld values, grid has %lld", what,
+                                         (long long)n_elems, (long long)g->total);
+    const size_t per = size_t(g->total_pad);
+    if (n_sets > *cap) {
+        ODP_CUDA(cudaStreamSynchronize(g->stream));
+        cudaFree(*dst);
+        *dst = nullptr;
+        *cap = 0;
+        if (cudaMalloc(dst, sizeof(float) * per * size_t(n_sets)) != cudaSuccess) {
+            cudaGetLastError();
+            *dst = nullptr;
+            return fail(ODP_ENOMEM, "%s schedule of %d sets", what, n_sets);
+        }
+        *cap = n_sets;
+        ODP_CUDA(cudaMemsetAsync(*dst, 0, sizeof(float) * per * size_t(n_sets), g->stream));
+    }
+    for (int k = 0; k < n_sets; ++k)
+        ODP_CUDA(cudaMemcpy2DAsync(*dst + size_t(k) * per, size_t(g->n_pad) * sizeof(float),
+                                   src + k * n_elems, size_t(g->n_last) * sizeof(float),
+                                   size_t(g->n_last) * sizeof(float), size_t(g->rows),
+                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));
+    return ODP_OK;
+}
+
+extern "C" odp_status odp_set_target_schedule(odp_grid *g, const float *l_seq, int n_sets, int64_t n_elems,
+                                              int on_device)
+{
+    if (!g) return fail(ODP_EINVAL, "grid is NULL");
+    if (!l_seq) {
+        if (g->l_seq_n) g->sched_version += 1;
+        g->l_seq_n = 0;
+        return ODP_OK;
+    }
+    ODP_BIND(g);
+    odp_status rc = copy_sets(g, &g->l_seq, &g->l_seq_cap, l_seq, n_sets, n_elems, on_device, "target");
+    if (rc != ODP_OK) return rc;
+    g->l_seq_n = n_sets;
+    g->has_target = true;
+    g->sched_version += 1;
+    return ODP_OK;
+}
+
+extern "C" odp_status odp_set_obstacle_schedule(odp_grid *g, const float *g_seq, int n_sets, int64_t n_elems,
+                                                int on_device)
+{
+    if (!g) return fail(ODP_EINVAL, "grid is NULL");
+    if (!g_seq) {
+        if (g->g_seq_n) {
+            g->sched_version += 1;
+            g->has_obst = false;
+        }
+        g->g_seq_n = 0;
+        return ODP_OK;
+    }
+    ODP_BIND(g);
+    const size_t bytes = size_t(g->total_pad) * sizeof(float);
+    if (!g->obst) {
+        if (cudaMalloc(&g->obst, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            g->obst = nullptr;
+            return fail(ODP_ENOMEM, "obstacle array of %zu bytes", bytes);
+        }
+        ODP_CUDA(cudaMemsetAsync(g->obst, 0, bytes, g->stream));
+    }
+    odp_status rc = copy_sets(g, &g->g_seq, &g->g_seq_cap, g_seq, n_sets, n_elems, on_device, "obstacle");
+    if (rc != ODP_OK) return rc;
+    g->g_seq_n = n_sets;
+    g->has_obst = true;
+    g->sched_version += 1;
     return ODP_OK;
 }
 
 extern "C" odp_status odp_set_obstacle(odp_grid *g, const float *gv, int64_t n_elems, int on_device)
 {
     if (!g) return fail(ODP_EINVAL, "grid is NULL");
+    if (g->g_seq_n) {   // a time-invariant obstacle (or none) replaces a schedule
+        g->g_seq_n = 0;
+        g->sched_version += 1;
+    }
     if (!gv) {
         g->has_obst = false;
         return ODP_OK;
@@ -570,8 +676,19 @@ static cudaError_t launch_stage_any(odp_grid *g, int stage, cudaStream_t s)
 // The kernels of one full time step, in order, on stream s: the per-stage alpha
 // pass, the CFL step, the stage pass(es) and the closing k_advance.  Used for
 // the captured graph body (in_graph = 1) and for the host-stepped loop.
+static int seq_active(const odp_grid *g) { return (g->l_seq_n > 0 || g->g_seq_n > 0) ? 1 : 0; }
+
+static cudaError_t launch_seq_sets(odp_grid *g, cudaStream_t s)
+{
+    const int blocks = int(std::min<int64_t>((g->total_pad + 255) / 256, 152 * 8));
+    k_seq_sets<<<blocks, 256, 0, s>>>(g->state, g->l, g->l_seq_n ? g->l_seq : nullptr, g->obst,
+                                      g->g_seq_n ? g->g_seq : nullptr, int(g->total_pad));
+    return cudaGetLastError();
+}
+
 static cudaError_t launch_step(odp_grid *g, cudaStream_t s, cudaGraphConditionalHandle h_loop,
-                               cudaGraphConditionalHandle h_snap, int in_graph, int64_t *launches)
+                               cudaGraphConditionalHandle h_snap, cudaGraphConditionalHandle h_seq, int in_graph,
+                               int64_t *launches)
 {
     const bool dyn_alpha = dynamic_alpha_mask(g) != 0;
     int64_t n = 0;
@@ -606,7 +723,7 @@ static cudaError_t launch_step(odp_grid *g, cudaStream_t s, cudaGraphConditional
     }
     if (e == cudaSuccess) {
         k_advance<<<1, 1, 0, s>>>(g->state, g->desc, g->time_order == 1 ? 1 : 0, dynamic_alpha_mask(g),
-                                  dyn_alpha ? 0 : 1, h_loop, h_snap, g->keep, in_graph);
+                                  dyn_alpha ? 0 : 1, h_loop, h_snap, g->keep, h_seq, seq_active(g), in_graph);
         ++n;
         e = cudaGetLastError();
     }
@@ -651,13 +768,14 @@ static odp_status build_graph(odp_grid *g)
     ODP_CUDA(cudaGraphAddNode(&loop_node, g->graph, nullptr, nullptr, 0, &wp));
     cudaGraph_t body = wp.conditional.phGraph_out[0];
 
-    cudaGraphConditionalHandle h_snap = 0;
+    cudaGraphConditionalHandle h_snap = 0, h_seq = 0;
     if (g->keep) ODP_CUDA(cudaGraphConditionalHandleCreate(&h_snap, body, 0, 0));
+    if (seq_active(g)) ODP_CUDA(cudaGraphConditionalHandleCreate(&h_seq, body, 0, 0));
 
     cudaStream_t s = g->capture_stream;
     ODP_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     int64_t launches = 0;
-    cudaError_t e = launch_step(g, s, h_loop, h_snap, 1, &launches);
+    cudaError_t e = launch_step(g, s, h_loop, h_snap, h_seq, 1, &launches);
     cudaStreamCaptureStatus cs;
     const cudaGraphNode_t *deps = nullptr;
     size_t ndeps = 0;
@@ -698,6 +816,25 @@ static odp_status build_graph(odp_grid *g)
                         cudaGetErrorString(e2));
         }
     }
+    if (seq_active(g)) {
+        cudaGraphNodeParams ip{};
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = h_seq;
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        cudaGraphNode_t if_node;
+        ODP_CUDA(cudaGraphAddNode(&if_node, body, leaf.data(), nullptr, leaf.size(), &ip));
+        cudaGraph_t seq_body = ip.conditional.phGraph_out[0];
+        ODP_CUDA(cudaStreamBeginCaptureToGraph(s, seq_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        e = launch_seq_sets(g, s);
+        cudaGraph_t cap3 = seq_body;
+        e2 = cudaStreamEndCapture(s, &cap3);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            cudaGetLastError();
+            g->graph = nullptr;
+            return fail(ODP_ECUDA, "capturing the set copy: %s / %s", cudaGetErrorString(e), cudaGetErrorString(e2));
+        }
+    }
     cudaError_t ei = cudaGraphInstantiate(&g->exec, g->graph, 0);
     if (ei != cudaSuccess) {
         g->exec = nullptr;
@@ -718,8 +855,9 @@ static odp_status run_host_loop(odp_grid *g)
     SolveState *h = nullptr;
     ODP_CUDA(cudaMallocHost(&h, sizeof(SolveState)));
     odp_status rc = ODP_OK;
+    int seg_before = 0;
     for (;;) {
-        cudaError_t e = launch_step(g, s, 0, 0, 0, nullptr);
+        cudaError_t e = launch_step(g, s, 0, 0, 0, 0, nullptr);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h, g->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e == cudaSuccess && h->snap_now) {
@@ -727,6 +865,9 @@ static odp_status run_host_loop(odp_grid *g)
             k_snapshot<<<blocks, 256, 0, s>>>(g->state, int(g->total_pad));
             e = cudaGetLastError();
         }
+        // a new segment started: its time-varying sets (the graph's IF node)
+        if (e == cudaSuccess && seq_active(g) && h->go && h->seg != seg_before) e = launch_seq_sets(g, s);
+        seg_before = h->seg;
         if (e != cudaSuccess) {
             rc = fail(ODP_ECUDA, "host-stepped time loop: %s", cudaGetErrorString(e));
             break;
@@ -753,6 +894,10 @@ extern "C" odp_status odp_solve_hjb(odp_grid *g, const double *tau, int n_tau, o
     if (!g->has_dyn) return fail(ODP_ESTATE, "odp_set_dynamics was not called");
     if (!g->has_target) return fail(ODP_ESTATE, "odp_set_target was not called");
     if (!tau || n_tau < 2) return fail(ODP_EINVAL, "need n_tau >= 2");
+    if (g->l_seq_n && g->l_seq_n != n_tau)
+        return fail(ODP_EINVAL, "the target schedule holds %d sets, the solve has %d taus", g->l_seq_n, n_tau);
+    if (g->g_seq_n && g->g_seq_n != n_tau)
+        return fail(ODP_EINVAL, "the obstacle schedule holds %d sets, the solve has %d taus", g->g_seq_n, n_tau);
     if (tau[0] != 0.0) return fail(ODP_EINVAL, "tau[0] must be 0");
     for (int k = 1; k < n_tau; ++k)
         if (!(tau[k] > tau[k - 1]) || !std::isfinite(tau[k]))
@@ -790,6 +935,7 @@ extern "C" odp_status odp_solve_hjb(odp_grid *g, const double *tau, int n_tau, o
     key.keep = g->keep;
     key.obstacle = g->has_obst ? 1 : 0;
     key.dyn_version = g->dyn_version;
+    key.sched_version = g->sched_version;
     if (!g->exec || !(key == g->key)) {
         odp_status rc = build_graph(g);
         if (rc != ODP_OK) return rc;
@@ -814,8 +960,15 @@ extern "C" odp_status odp_solve_hjb(odp_grid *g, const double *tau, int n_tau, o
     const size_t bytes = size_t(g->total_pad) * sizeof(float);
     ODP_CUDA(cudaMemcpyAsync(g->tau, tau, sizeof(double) * size_t(n_tau), cudaMemcpyHostToDevice, st));
     ODP_CUDA(cudaMemcpyAsync(g->state, &h, sizeof(h), cudaMemcpyHostToDevice, st));
-    ODP_CUDA(cudaMemcpyAsync(g->phi_a, g->l, bytes, cudaMemcpyDeviceToDevice, st));
-    if (g->keep) ODP_CUDA(cudaMemcpyAsync(g->snapshots, g->l, bytes, cudaMemcpyDeviceToDevice, st));
+    // phi(0): the target, or the first set of a target schedule; a schedule's
+    // first segment takes the sets at tau[1]
+    const float *phi0 = g->l_seq_n ? g->l_seq : g->l;
+    ODP_CUDA(cudaMemcpyAsync(g->phi_a, phi0, bytes, cudaMemcpyDeviceToDevice, st));
+    if (g->keep) ODP_CUDA(cudaMemcpyAsync(g->snapshots, phi0, bytes, cudaMemcpyDeviceToDevice, st));
+    if (g->l_seq_n)
+        ODP_CUDA(cudaMemcpyAsync(g->l, g->l_seq + g->total_pad, bytes, cudaMemcpyDeviceToDevice, st));
+    if (g->g_seq_n)
+        ODP_CUDA(cudaMemcpyAsync(g->obst, g->g_seq + g->total_pad, bytes, cudaMemcpyDeviceToDevice, st));
     ODP_CUDA(launch_alpha_static_any(g, st));
     if (!dynamic_alpha_mask(g)) {   // the first step's dt (later ones: k_advance)
         k_dt<<<1, 1, 0, st>>>(g->state, g->desc);

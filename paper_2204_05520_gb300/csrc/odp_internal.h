@@ -30,10 +30,11 @@ void plane_geometry_many(GridDesc &D);
 struct GraphKey {
     int order = 0, time_order = 0, brt = 0, keep = 0, obstacle = 0;
     long long dyn_version = -1;
+    long long sched_version = -1;     // time-varying target / obstacle schedules
     bool operator==(const GraphKey &o) const
     {
         return order == o.order && time_order == o.time_order && brt == o.brt && keep == o.keep &&
-               obstacle == o.obstacle && dyn_version == o.dyn_version;
+               obstacle == o.obstacle && dyn_version == o.dyn_version && sched_version == o.sched_version;
     }
 };
 
@@ -76,5 +77,12 @@ struct odp_grid {
     int64_t launches_per_step = 0;
     int host_loop = 0;                // 1: the time loop is stepped from the host
     void *ttr = nullptr;              // time-to-reach plan (ttr.cu), built on first use
+    // time-varying sets (odp_set_target_schedule / odp_set_obstacle_schedule):
+    // n sets of total_pad floats each; during a solve l and obst hold the
+    // current segment's sets
+    float *l_seq = nullptr, *g_seq = nullptr;
+    int l_seq_n = 0, g_seq_n = 0;
+    int l_seq_cap = 0, g_seq_cap = 0;
+    long long sched_version = 0;
 };
 

@@ -564,6 +564,7 @@ extern "C" odp_status odp_solve_ttr(odp_grid *g, double eps, double big, int64_t
 {
     if (!g) return fail(ODP_EINVAL, "grid is NULL");
     if (!g->has_dyn || !g->has_target) return fail(ODP_ESTATE, "dynamics and target must be set first");
+    if (g->l_seq_n) return fail(ODP_EINVAL, "the time-to-reach sweep takes one target set, not a schedule");
     if (!ttr_model(g->dyn.kind))
         return fail(ODP_EINVAL, "the time-to-reach sweep supports the single integrator, Dubins3D and DubinsCar4D");
     if (g->dyn.umode != MODE_MIN || g->dyn.dmode != MODE_MAX)

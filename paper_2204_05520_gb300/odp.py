@@ -117,6 +117,8 @@ def load():
             "odp_set_dynamics": ([P, i32, P, i32, i32, i32], i32),
             "odp_set_target": ([P, P, i64, i32], i32),
             "odp_set_obstacle": ([P, P, i64, i32], i32),
+            "odp_set_target_schedule": ([P, P, i32, i64, i32], i32),
+            "odp_set_obstacle_schedule": ([P, P, i32, i64, i32], i32),
             "odp_set_dissipation": ([P, i32], i32),
             "odp_set_step_limit": ([P, i64], i32),
             "odp_set_loop_mode": ([P, i32], i32),
@@ -232,6 +234,26 @@ def set_obstacle(g, gv):
     n = grid_points(g)
     ptr, dev = _buffer(gv, n, writable=False)
     _check(load().odp_set_obstacle(g, ptr, n, dev), "odp_set_obstacle")
+
+
+def _schedule(g, seq, fn, where):
+    n = grid_points(g)
+    if seq is None:
+        _check(fn(g, None, 0, n, 0), where)
+        return
+    k = int(seq.shape[0])
+    ptr, dev = _buffer(seq, k * n, writable=False)
+    _check(fn(g, ptr, k, n, dev), where)
+
+
+def set_target_schedule(g, l_seq):
+    """Time-varying target: one set per tau, shape (n_tau,) + grid (None removes)."""
+    _schedule(g, l_seq, load().odp_set_target_schedule, "odp_set_target_schedule")
+
+
+def set_obstacle_schedule(g, g_seq):
+    """Time-varying obstacle: one set per tau, shape (n_tau,) + grid (None removes)."""
+    _schedule(g, g_seq, load().odp_set_obstacle_schedule, "odp_set_obstacle_schedule")
 
 
 def set_dissipation(g, per_node: bool):
@@ -457,6 +479,12 @@ class Grid:
 
     def set_obstacle(self, gv):
         set_obstacle(self.handle, gv)
+
+    def set_target_schedule(self, l_seq):
+        set_target_schedule(self.handle, l_seq)
+
+    def set_obstacle_schedule(self, g_seq):
+        set_obstacle_schedule(self.handle, g_seq)
 
     def solve(self, tau, set_kind="brt", space_order=1, time_order=1, cfl=0.8,
               keep_snapshots=False, stats=False):
