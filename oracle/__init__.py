@@ -31,6 +31,10 @@ MODE_IDS = {"min": 0, "max": 1}
 SET_IDS = {"brs": 0, "brt": 1}
 MAX_INPUTS = 8
 TTR_SCHEMES = {"gauss_seidel": 0, "jacobi": 1}
+# computation methods of the solver (reading R27)
+TARGET_METHODS = {"None": 0, "minVWithVTarget": 1, "maxVWithVTarget": 2, "minVWithVInit": 3,
+                  "maxVWithVInit": 4, "minVWithV0": 5, "maxVWithV0": 6}
+OBSTACLE_METHODS = {"maxVWithObstacle": 1, "minVWithObstacle": 2}
 
 OK, EINVAL, ENOMEM, ETIMEOUT, ENUMERIC = 0, -1, -2, -5, -6
 
@@ -74,13 +78,15 @@ def _load():
             lib.og_solve.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, P, P, P, i32, i32,
                                      i32, i32, i32, f64, i64, P, P, P, P, P]
             lib.og_solve_seq.argtypes = lib.og_solve.argtypes
+            lib.og_solve_methods.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, P, P, P, P, P, i32,
+                                             i32, i32, i32, i32, i32, f64, i64, P, P, P, P, P]
             lib.og_step.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, P, P, f64, i32, i32,
                                     i32, i32, P, P]
             lib.og_ttr.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, f64, f64, i64, i32,
                                    P, P, P]
             lib.og_ttr_node.argtypes = [i32, P, P, P, P, i32, P, i32, i32, i32, P, P, P]
             for f in (lib.og_spacing, lib.og_eval_dynamics, lib.og_terms, lib.og_solve,
-                      lib.og_solve_seq, lib.og_step, lib.og_ttr, lib.og_ttr_node):
+                      lib.og_solve_seq, lib.og_solve_methods, lib.og_step, lib.og_ttr, lib.og_ttr_node):
                 f.restype = i32
             _lib = lib
     return _lib
@@ -327,3 +333,42 @@ def ttr_node(problem, phi, idx) -> float:
     if rc:
         raise OracleError(rc, "ttr_node")
     return out.value
+
+
+def solve_methods(problem, target_method: str, obstacle_method: str = "maxVWithObstacle", l=None, g=None,
+                  l_seq=None, g_seq=None, phi0=None, snapshots: bool = False, max_steps: int = 10_000_000,
+                  raise_on_error: bool = True) -> dict:
+    """``solve`` with any computation method of the solver's table (reading
+    R27): ``target_method`` a key of TARGET_METHODS, ``obstacle_method`` a key
+    of OBSTACLE_METHODS (used when an obstacle ``g`` or ``g_seq`` is given).
+    Returns the dict of ``solve``."""
+    lib = _load()
+    p = problem
+    n_a, lo_a, hi_a, per_a = _grid_args(p.n, p.lo, p.hi, p.periodic)
+    if l is None and l_seq is None:
+        l = p.target_values()
+    tau = np.ascontiguousarray(p.tau, dtype=np.float64)
+    l64 = None if l is None else np.ascontiguousarray(l, dtype=np.float64).reshape(-1)
+    g64 = None if g is None else np.ascontiguousarray(g, dtype=np.float64).reshape(-1)
+    ls = None if l_seq is None else np.ascontiguousarray(l_seq, dtype=np.float64).reshape(len(tau), -1)
+    gs = None if g_seq is None else np.ascontiguousarray(g_seq, dtype=np.float64).reshape(len(tau), -1)
+    p0 = None if phi0 is None else np.ascontiguousarray(phi0, dtype=np.float64).reshape(-1)
+    prm = np.ascontiguousarray(p.params, dtype=np.float64)
+    N = p.points
+    final = np.zeros(N)
+    snaps = np.zeros((len(tau), N)) if snapshots else None
+    steps = np.zeros(len(tau) - 1, dtype=np.int64)
+    alpha = np.zeros(len(n_a))
+    last_dt = ctypes.c_double(0.0)
+    rc = lib.og_solve_methods(len(n_a), _ptr(n_a), _ptr(lo_a), _ptr(hi_a), _ptr(per_a), DYN_IDS[p.dynamics],
+                              _ptr(prm), len(prm), MODE_IDS[p.u_mode], MODE_IDS[p.d_mode], _ptr(l64), _ptr(g64),
+                              _ptr(ls), _ptr(gs), _ptr(p0), _ptr(tau), len(tau), TARGET_METHODS[target_method],
+                              OBSTACLE_METHODS[obstacle_method], p.space_order, p.time_order, _local(p),
+                              float(p.cfl), int(max_steps), _ptr(snaps), _ptr(final), _ptr(steps), _ptr(alpha),
+                              ctypes.byref(last_dt))
+    if rc and raise_on_error:
+        raise OracleError(rc, "solve_methods")
+    shape = tuple(p.n)
+    return {"final": final.reshape(shape),
+            "snapshots": None if snaps is None else snaps.reshape((len(tau),) + shape),
+            "steps": steps, "alpha": alpha, "last_dt": last_dt.value, "rc": rc}

@@ -54,6 +54,13 @@
  *     starts from l_0 and every step of segment (tau_k, tau_k+1] takes its
  *     post-step min with l_k+1 and max with g_k+1, the sets at the end of the
  *     segment in which the step lands.
+ *  R27 computation methods (Section 4.3's table; its time indices are
+ *     garbled): after each full step, first the target side -- min / max
+ *     with the target set of the segment (minVWithVTarget, maxVWithVTarget),
+ *     with the value before the step (minVWithVInit, maxVWithVInit: the
+ *     "value over time"), or with the initial value phi(0) (minVWithV0,
+ *     maxVWithV0) -- then the obstacle side, max / min with g
+ *     (maxVWithObstacle, minVWithObstacle).
  *  R10 ENO2: p- = D-phi + (h/2) c, p+ = D+phi - (h/2) c', c (c') the second
  *     difference of smaller magnitude among those at i-1 and i (i and i+1);
  *     on equal magnitude the centred one (at i).  The comparison is taken in
@@ -708,13 +715,26 @@ int og_step(int ndim, const int64_t *n, const double *lo, const double *hi, cons
  *  alpha_out   NULL or ndim doubles: alpha of the last stage
  *  last_dt     NULL or the last step's dt
  */
+/* Post-step operations (the computation methods of Section 4.3, reading
+ * R27).  Target side, applied first: */
+enum { OG_T_NONE = 0,        /* plain PDE (BRS)                                  */
+       OG_T_MIN_TARGET = 1,  /* minVWithVTarget: min with the target (BRT)       */
+       OG_T_MAX_TARGET = 2,  /* maxVWithVTarget                                  */
+       OG_T_MIN_INIT = 3,    /* minVWithVInit: min with the value before the step */
+       OG_T_MAX_INIT = 4,    /* maxVWithVInit                                    */
+       OG_T_MIN_V0 = 5,      /* minVWithV0: min with the initial value phi(0)    */
+       OG_T_MAX_V0 = 6 };    /* maxVWithV0                                       */
+/* obstacle side, applied after the target side: */
+enum { OG_O_MAX = 1,         /* maxVWithObstacle                                 */
+       OG_O_MIN = 2 };       /* minVWithObstacle                                 */
+
 static int og_solve_impl(int ndim, const int64_t *n, const double *lo, const double *hi,
                          const int *periodic, int kind, const double *prm, int n_prm, int umode,
                          int dmode, const double *l, const double *obst, const double *l_seq,
                          const double *g_seq, const double *phi0, const double *tau, int n_tau,
-                         int set_kind, int space_order, int time_order, int local_alpha, double cfl,
-                         int64_t max_steps, double *snapshots, double *final_out, int64_t *steps_out,
-                         double *alpha_out, double *last_dt)
+                         int set_kind, int obst_mode, int space_order, int time_order, int local_alpha,
+                         double cfl, int64_t max_steps, double *snapshots, double *final_out,
+                         int64_t *steps_out, double *alpha_out, double *last_dt)
 {
     og_grid g;
     og_dyn dy;
@@ -726,14 +746,17 @@ static int og_solve_impl(int ndim, const int64_t *n, const double *lo, const dou
     if (space_order != 1 && space_order != 2) return OG_EINVAL;
     if (time_order != 1 && time_order != 2) return OG_EINVAL;
     if (!(cfl > 0.0)) return OG_EINVAL;
-    if (set_kind != OG_BRS && set_kind != OG_BRT) return OG_EINVAL;
+    if (set_kind < OG_T_NONE || set_kind > OG_T_MAX_V0) return OG_EINVAL;
+    if (obst_mode != OG_O_MAX && obst_mode != OG_O_MIN) return OG_EINVAL;
 
     int64_t N = g.total;
     double *phi = malloc(sizeof(double) * N);
     double *phi1 = malloc(sizeof(double) * N);
     double *L = malloc(sizeof(double) * N);
-    if (!phi || !phi1 || !L) { free(phi); free(phi1); free(L); return OG_ENOMEM; }
+    double *v0 = malloc(sizeof(double) * N);
+    if (!phi || !phi1 || !L || !v0) { free(phi); free(phi1); free(L); free(v0); return OG_ENOMEM; }
     memcpy(phi, phi0 ? phi0 : (l_seq ? l_seq : l), sizeof(double) * N);
+    memcpy(v0, phi, sizeof(double) * N);
     if (snapshots) memcpy(snapshots, phi, sizeof(double) * N);
 
     double alpha[OG_MAXD] = {0}, alpha2[OG_MAXD] = {0};
@@ -765,8 +788,19 @@ static int og_solve_impl(int ndim, const int64_t *n, const double *lo, const dou
             int bad = 0;
             for (int64_t i = 0; i < N; ++i) {
                 double v = phi1[i];
-                if (set_kind == OG_BRT && lk[i] < v) v = lk[i];
-                if (gk && gk[i] > v) v = gk[i];
+                switch (set_kind) {
+                case OG_T_MIN_TARGET: if (lk[i] < v) v = lk[i]; break;
+                case OG_T_MAX_TARGET: if (lk[i] > v) v = lk[i]; break;
+                case OG_T_MIN_INIT: if (phi[i] < v) v = phi[i]; break;   /* phi[i]: before the step */
+                case OG_T_MAX_INIT: if (phi[i] > v) v = phi[i]; break;
+                case OG_T_MIN_V0: if (v0[i] < v) v = v0[i]; break;
+                case OG_T_MAX_V0: if (v0[i] > v) v = v0[i]; break;
+                default: break;
+                }
+                if (gk) {
+                    if (obst_mode == OG_O_MAX && gk[i] > v) v = gk[i];
+                    if (obst_mode == OG_O_MIN && gk[i] < v) v = gk[i];
+                }
                 if (!isfinite(v)) bad = 1;
                 phi[i] = v;
             }
@@ -785,6 +819,7 @@ static int og_solve_impl(int ndim, const int64_t *n, const double *lo, const dou
     free(phi);
     free(phi1);
     free(L);
+    free(v0);
     return rc;
 }
 
@@ -797,8 +832,8 @@ int og_solve(int ndim, const int64_t *n, const double *lo, const double *hi,
              double *alpha_out, double *last_dt)
 {
     return og_solve_impl(ndim, n, lo, hi, periodic, kind, prm, n_prm, umode, dmode, l, obst, NULL, NULL, phi0,
-                         tau, n_tau, set_kind, space_order, time_order, local_alpha, cfl, max_steps, snapshots,
-                         final_out, steps_out, alpha_out, last_dt);
+                         tau, n_tau, set_kind, OG_O_MAX, space_order, time_order, local_alpha, cfl, max_steps,
+                         snapshots, final_out, steps_out, alpha_out, last_dt);
 }
 
 /* og_solve with time-varying sets (reading R26): l_seq (target) and g_seq
@@ -815,8 +850,26 @@ int og_solve_seq(int ndim, const int64_t *n, const double *lo, const double *hi,
 {
     if (!l_seq) return OG_EINVAL;
     return og_solve_impl(ndim, n, lo, hi, periodic, kind, prm, n_prm, umode, dmode, l_seq, NULL, l_seq, g_seq,
-                         phi0, tau, n_tau, set_kind, space_order, time_order, local_alpha, cfl, max_steps,
-                         snapshots, final_out, steps_out, alpha_out, last_dt);
+                         phi0, tau, n_tau, set_kind, OG_O_MAX, space_order, time_order, local_alpha, cfl,
+                         max_steps, snapshots, final_out, steps_out, alpha_out, last_dt);
+}
+
+/* og_solve with any computation method of Section 4.3 (reading R27):
+ * target_mode one of OG_T_*, obst_mode OG_O_MAX or OG_O_MIN (used when an
+ * obstacle, or obstacle schedule, is given); l_seq / g_seq as og_solve_seq
+ * (either may be NULL; then l / obst are the sets of every segment). */
+int og_solve_methods(int ndim, const int64_t *n, const double *lo, const double *hi,
+                     const int *periodic, int kind, const double *prm, int n_prm, int umode,
+                     int dmode, const double *l, const double *obst, const double *l_seq,
+                     const double *g_seq, const double *phi0, const double *tau, int n_tau,
+                     int target_mode, int obst_mode, int space_order, int time_order, int local_alpha,
+                     double cfl, int64_t max_steps, double *snapshots, double *final_out,
+                     int64_t *steps_out, double *alpha_out, double *last_dt)
+{
+    if (!l && !l_seq) return OG_EINVAL;
+    return og_solve_impl(ndim, n, lo, hi, periodic, kind, prm, n_prm, umode, dmode, l ? l : l_seq, obst, l_seq,
+                         g_seq, phi0, tau, n_tau, target_mode, obst_mode, space_order, time_order, local_alpha,
+                         cfl, max_steps, snapshots, final_out, steps_out, alpha_out, last_dt);
 }
 
 /* ------------------------------------------------------------------------- */
