@@ -41,6 +41,15 @@ def test_every_declared_symbol_is_exported(lib):
     assert not missing, missing
 
 
+def test_binding_marshals_every_declared_entry_point(lib):
+    # the ctypes binding sets argument and result types for each declared
+    # function (an unset one would pass 64-bit arguments as C ints)
+    for name in declared_entry_points():
+        fn = getattr(lib, name)
+        assert fn.restype is not None, name
+        assert fn.argtypes is not None, name
+
+
 def test_library_reports_version_and_no_error(lib):
     assert "sm_103a" in odp.version()
     assert odp.last_error() == ""
