@@ -272,12 +272,74 @@ def run_reference_ttr(args, problem):
     return 0
 
 
+def oracle_solve_estimate(problem):
+    """Seconds the FP64 oracle would take for the whole solve of ``problem``:
+    the time of one step (the oracle stopped after 3 and after 1 steps, the
+    difference halved, so that fixed per-call costs cancel) times the step
+    count of its CFL schedule (the last step of each tau segment clipped)."""
+    import math
+
+    import oracle
+
+    oracle.build()
+    l = problem.target_values()
+    secs = []
+    for k in (1, 3):
+        t0 = time.perf_counter()
+        r = oracle.solve(problem, l=l, max_steps=k, raise_on_error=False)
+        secs.append(time.perf_counter() - t0)
+    per_step = max(secs[1] - secs[0], 0.0) / 2.0
+    dz = [(problem.hi[d] - problem.lo[d]) / (problem.n[d] if problem.periodic[d] else problem.n[d] - 1)
+          for d in range(problem.ndim)]
+    dt = problem.cfl / sum(float(r["alpha"][d]) / dz[d] for d in range(problem.ndim))
+    tau = problem.tau
+    steps = sum(math.ceil((tau[k + 1] - tau[k]) / dt - 1e-9) for k in range(len(tau) - 1))
+    return per_step * steps, steps, oracle.num_threads()
+
+
+def run_reference_solves(args):
+    """Reference arm of the batched and served workloads (solves/s): the
+    oracle solves the workload's problems one at a time; each benchmark step
+    takes the next problem, timing one full time step and extrapolating to
+    its step count (a whole oracle solve of a large grid takes minutes)."""
+    from paper_2204_05520_gb300 import inputs
+
+    if args.workload == "batch512":
+        problems = inputs.batch_problems(count=512, seed=0)
+        metric, name = "batched solves/s", "batch512_dubins3d"
+    else:
+        problems = [p for _, p in inputs.served_requests(100.0, count=max(40, args.steps + args.warmup), seed=1)]
+        metric, name = "served solves/s (saturation) with p50/p99 latency", "served_poisson_dubins3d_dubinscar4d"
+    for i in range(args.warmup):
+        oracle_solve_estimate(problems[i % len(problems)])
+    total, threads = 0.0, 1
+    for i in range(args.steps):
+        est, _, threads = oracle_solve_estimate(problems[(args.warmup + i) % len(problems)])
+        total += est
+    value = args.steps / total
+    sample = ("%d problems of the workload solved one at a time: the time of one full step of each (oracle "
+              "stopped after 3 and after 1 steps), times its CFL step count" % args.steps)
+    line = {
+        "impl": "reference", "metric": metric, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": name},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                         "sample": sample, "cpu_model": cpu_model()},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = rank_info()
     if rank != 0:
         return 0
     from paper_2204_05520_gb300 import inputs
 
+    if args.workload in ("batch512", "served"):
+        return run_reference_solves(args)
     problem = inputs.workload(args.workload)
     if args.workload in TTR_WORKLOADS:
         return run_reference_ttr(args, problem)
