@@ -63,8 +63,9 @@
  *     (maxVWithObstacle, minVWithObstacle).
  *  R10 ENO2: p- = D-phi + (h/2) c, p+ = D+phi - (h/2) c', c (c') the second
  *     difference of smaller magnitude among those at i-1 and i (i and i+1);
- *     on equal magnitude the centred one (at i).  The comparison is taken in
- *     float32 (see og_one_sided).
+ *     on equal magnitude the centred one (at i).  Magnitudes are equal when
+ *     they differ by at most 2^-40 times the sum of the magnitudes of the
+ *     five window values (the tie margin, OG_ENO_TIE).
  *  R21 time-to-reach Hamiltonian (Section 2.2, Algorithm 2): the control
  *     shortens and the disturbance lengthens the time, so u* = argmin_u and
  *     d* = argmax_d of pbar . f (Algorithm 2's argmin; the equation's printed
@@ -188,41 +189,24 @@ static double og_shifted(const og_grid *g, const double *phi, const int64_t *idx
     return pb + k * sgn * fabs(pb - pin);
 }
 
-/* The same node value as the GPU kernel holds it: float32; a ghost node is
- * formed in float32 arithmetic from the float32 boundary values (R9).  Used
- * only for the float32 stencil decision below. */
-static float og_shifted32(const og_grid *g, const double *phi, const int64_t *idx,
-                          int64_t flat, int d, int off)
-{
-    int64_t n = g->n[d];
-    int64_t j = idx[d] + off;
-    int64_t row = flat - idx[d] * g->stride[d];
-    if (g->periodic[d]) {
-        j = ((j % n) + n) % n;
-        return (float)phi[row + j * g->stride[d]];
-    }
-    if (j >= 0 && j < n) return (float)phi[row + j * g->stride[d]];
-    int64_t b = (j < 0) ? 0 : n - 1;
-    int64_t in = (j < 0) ? 1 : n - 2;
-    float k = (j < 0) ? (float)(-j) : (float)(j - (n - 1));
-    float pb = (float)phi[row + b * g->stride[d]];
-    float pin = (float)phi[row + in * g->stride[d]];
-    float sgn = (pb >= 0.0f) ? 1.0f : -1.0f;
-    return pb + (k * sgn) * fabsf(pb - pin);
-}
+/* Tie margin of the ENO2 stencil choice (reading R10): the two candidate
+ * second differences count as equal in magnitude when their magnitudes differ
+ * by at most OG_ENO_TIE times the sum of the magnitudes of the five window
+ * values.  On data whose candidates are equal in exact arithmetic (mirror
+ * symmetric windows, linear pieces) double rounding leaves differences some
+ * 2^-50 of that sum; 2^-40 is far above that noise and far below any
+ * difference the method resolves. */
+#define OG_ENO_TIE 9.094947017729282e-13   /* 2^-40 */
 
 /* One-sided derivatives p-, p+ along axis d at a node (Section 3.1.4 and
- * Algorithm 1: first-order upwind differences, or second-order ENO R10).
+ * Algorithm 1: first-order upwind differences, or second-order ENO, R10).
  *
- * The ENO2 stencil choice is a discrete decision taken by comparing two
- * floating-point magnitudes.  It is taken in float32, the precision of the
- * GPU kernel, on the five-node window as float32 values (og_shifted32) and
- * with the same order of operations (a = f0 - fm1, b = fp1 - f0, then a - (fm1 - fm2),
- * b - a, (fp2 - fp1) - b), so that both sides decide alike on the same data;
- * the derivative itself is formed from the chosen second difference in
- * float64.  On data that is symmetric in exact arithmetic the two candidates
- * tie exactly, and float64 rounding noise alone would otherwise pick a
- * different stencil than the float32 kernel does. */
+ * ENO2: with the second differences D2_j = (phi_{j+1} - 2 phi_j + phi_{j-1})
+ * / h^2 at j = i-1, i, i+1,
+ *   p- = D-phi + (h/2) c,   c  = D2_{i-1} if |D2_{i-1}| < |D2_i|, else D2_i,
+ *   p+ = D+phi - (h/2) c',  c' = D2_{i+1} if |D2_{i+1}| < |D2_i|, else D2_i,
+ * where "<" means smaller by more than the tie margin above, so that equal
+ * magnitudes (a tie) keep the centred D2_i. */
 static void og_one_sided(const og_grid *g, const double *phi, const int64_t *idx,
                          int64_t flat, int d, int order, double *pm, double *pp)
 {
@@ -239,18 +223,15 @@ static void og_one_sided(const og_grid *g, const double *phi, const int64_t *idx
     }
     double fm2 = og_shifted(g, phi, idx, flat, d, -2);
     double fp2 = og_shifted(g, phi, idx, flat, d, +2);
-    double d2_left = (f0 - 2.0 * fm1 + fm2) / (h * h);     /* at i-1 */
-    double d2_mid = (fp1 - 2.0 * f0 + fm1) / (h * h);      /* at i   */
-    double d2_right = (fp2 - 2.0 * fp1 + f0) / (h * h);    /* at i+1 */
-    float w0 = og_shifted32(g, phi, idx, flat, d, -2), w1 = og_shifted32(g, phi, idx, flat, d, -1);
-    float w2 = (float)f0;
-    float w3 = og_shifted32(g, phi, idx, flat, d, +1), w4 = og_shifted32(g, phi, idx, flat, d, +2);
-    float a32 = w2 - w1, b32 = w3 - w2;
-    float l32 = a32 - (w1 - w0), m32 = b32 - a32, r32 = (w4 - w3) - b32;
-    double c_minus = (fabsf(l32) < fabsf(m32)) ? d2_left : d2_mid;
-    double c_plus = (fabsf(r32) < fabsf(m32)) ? d2_right : d2_mid;
-    *pm = dm + 0.5 * h * c_minus;
-    *pp = dp - 0.5 * h * c_plus;
+    /* second differences in value units (h^2 D2) */
+    double s_left = f0 - 2.0 * fm1 + fm2;     /* at i-1 */
+    double s_mid = fp1 - 2.0 * f0 + fm1;      /* at i   */
+    double s_right = fp2 - 2.0 * fp1 + f0;    /* at i+1 */
+    double margin = OG_ENO_TIE * (fabs(fm2) + fabs(fm1) + fabs(f0) + fabs(fp1) + fabs(fp2));
+    double c_minus = (fabs(s_left) < fabs(s_mid) - margin) ? s_left : s_mid;
+    double c_plus = (fabs(s_right) < fabs(s_mid) - margin) ? s_right : s_mid;
+    *pm = dm + 0.5 * c_minus / h;
+    *pp = dp - 0.5 * c_plus / h;
 }
 
 /* ------------------------------------------------------------------------- */

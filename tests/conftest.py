@@ -19,3 +19,14 @@ def oracle_lib():
 
     oracle.build()
     return oracle
+
+
+def pytest_terminal_summary(terminalreporter):
+    try:
+        import parity_log
+    except ImportError:
+        return
+    if parity_log.NOTES:
+        terminalreporter.section("parity numbers")
+        for test, text in parity_log.NOTES:
+            terminalreporter.write_line("%s: %s" % (test, text))

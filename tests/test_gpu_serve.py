@@ -1,11 +1,15 @@
 """Serving loop (odp_server_*): continuous batching under an HBM budget.
 
 Requests that arrive while others are on the GPU join later launches; each
-result must equal the same request solved alone (odp_solve_hjb), and the
-resident HBM never exceeds the budget."""
+result must equal the same request solved alone (odp_solve_hjb), match the
+FP64 oracle (the 1e-4 bar for upwind solves, twice the oracle's own float32
+sensitivity for ENO2 solves, equal step counts), and the resident HBM never
+exceeds the budget."""
 import numpy as np
 import pytest
 
+import oracle
+import parity
 from paper_2204_05520_gb300 import inputs, odp
 
 pytestmark = pytest.mark.gpu
@@ -21,6 +25,7 @@ def cuda():
 
     _build.build()
     odp.load()
+    oracle.build()
     return torch
 
 
@@ -53,9 +58,18 @@ def mixed_requests(count, seed):
     return out
 
 
+def served_like_requests(count, seed=1):
+    """Requests drawn as the served workload draws them (Poisson mix of
+    upwind Dubins3D and ENO2 + TVD-RK2 DubinsCar4D, horizons U[0.5, 3]) on
+    reduced grids (sides 31-35 and 20-24), so the oracle checks each one."""
+    return [p for _, p in inputs.served_requests(100.0, count=count, seed=seed,
+                                                 side3=(31, 35), side4=(20, 24))]
+
+
 def test_results_are_the_same_alone_and_in_the_mix():
-    problems = mixed_requests(10, seed=5)
-    with odp.Server(hbm_budget_bytes=256 << 20) as srv:
+    problems = mixed_requests(10, seed=5) + served_like_requests(4)
+    assert {p.dynamics for p in problems[10:]} == {"dubins3d", "dubinscar4d"}
+    with odp.Server(hbm_budget_bytes=512 << 20) as srv:
         ids = {}
         # arrivals spread over the first steps: later requests join a batch
         # that is already running
@@ -73,11 +87,10 @@ def test_results_are_the_same_alone_and_in_the_mix():
             st = srv.poll(ids[k])
             assert st["state"] == odp.REQ_DONE and st["steps_done"] == st["steps"]
             v = srv.readback(ids[k], np.empty(p.n, np.float32))
-            ref = solo(p)
-            l = p.target_values()
-            assert np.abs(v - ref).max() <= REL_TOL * float(l.max() - l.min())
             # the same per-node arithmetic as the single solve
-            assert np.array_equal(v, ref)
+            assert np.array_equal(v, solo(p))
+            # and the FP64 oracle's solve of the same request
+            parity.check_whole_solve(p, v, st["steps"], name="served %s" % p.name)
             srv.release(ids[k])
         assert srv.info()["used_bytes"] == 0
 

@@ -91,6 +91,30 @@ def test_eno2_exact_on_quadratics_in_the_interior():
         np.testing.assert_allclose(t["pp"][..., d][inner], grad[d][inner], atol=1e-10)
 
 
+def test_eno2_tie_margin():
+    # Reading R10: ENO2 keeps the centred second difference when the two
+    # candidates have equal magnitude in exact arithmetic.  Window at node 2
+    # of the periodic array (-0.9, -0.8, -0.6, -0.5, 0.4), h = 1:
+    #   second differences at 1, 2, 3: -0.6 + 1.6 - 0.9 = 0.1,
+    #   -0.5 + 1.2 - 0.8 = -0.1, 0.4 + 1.0 - 0.6 = 0.8;
+    #   D- = 0.2, D+ = 0.1.  |0.1| = |-0.1| is a tie, so c = c' = -0.1 and
+    #   p- = 0.2 - 0.05 = 0.15, p+ = 0.1 + 0.05 = 0.15.
+    # Double rounding of these decimals gives |0.0999...98| < |-0.1000...09|,
+    # so a plain floating-point compare would take c = 0.1 (p- = 0.25).
+    p = box_problem((5,), (0.0,), (5.0,), (True,))
+    phi = np.array([-0.9, -0.8, -0.6, -0.5, 0.4])
+    t = oracle.terms(p, phi, order=2)
+    assert t["pm"][2, 0] == pytest.approx(0.15, abs=1e-12)
+    assert t["pp"][2, 0] == pytest.approx(0.15, abs=1e-12)
+    # a real difference of 1e-9 (far above the 2^-40 margin) is resolved:
+    # phi_0 = -0.9 - 1e-9 makes the left difference 0.1 - 1e-9, the smaller,
+    # so c = 0.1 - 1e-9 and p- = 0.2 + 0.05 - 5e-10
+    phi[0] -= 1e-9
+    t = oracle.terms(p, phi, order=2)
+    assert t["pm"][2, 0] == pytest.approx(0.25 - 5e-10, abs=1e-12)
+    assert t["pp"][2, 0] == pytest.approx(0.15, abs=1e-12)
+
+
 def test_periodic_wrap_on_every_axis():
     # sin on a periodic axis: p- and p+ are the wrapped one-sided differences
     n = 12
