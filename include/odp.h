@@ -201,6 +201,23 @@ odp_status odp_set_step_limit(odp_grid *g, int64_t max_steps);
  * not follow kernels inside conditional graph nodes.  Errors: ODP_EINVAL. */
 odp_status odp_set_loop_mode(odp_grid *g, int host_stepped);
 
+/* Choose the kernel that runs the stage pass of Algorithm 1 (derivatives,
+ * Hamiltonian, Lax-Friedrichs update and set operations) for grids of 3 or
+ * more dimensions; no paper counterpart, both compute the same per-node
+ * arithmetic, so results are identical.  The bulk-staged pass (Dubins3D,
+ * DubinsCar4D and Rel6D grids whose last axis is a multiple of 4 nodes, with
+ * grid-wide dissipation) has a producer thread per CTA stage every neighbour
+ * tile with bulk async copies into shared-memory rings; the plane-streaming
+ * pass has the compute threads load their own neighbours.  pass = 0
+ * (default) picks the one that measured faster for the model (bulk-staged
+ * for Rel6D, plane-streaming otherwise); pass = 1 forces the plane-streaming
+ * pass; pass = 2 the bulk-staged pass.  The choice holds for later solves of the grid; batched
+ * and served solves always use the plane-streaming pass.  Errors: ODP_EINVAL
+ * (pass out of range, or 2 on a grid whose shape the bulk-staged pass does
+ * not take: last axis not a multiple of 4, fewer than 4 rows or stream
+ * planes, or rings beyond 200 KB of shared memory). */
+odp_status odp_set_stage_pass(odp_grid *g, int pass);
+
 /* Solve the HJ PDE (Algorithm 1) from tau[0] = 0 to tau[n_tau-1].
  *  tau          n_tau >= 2 strictly increasing look-back times (host), tau[0] = 0;
  *               each segment is integrated separately, the last CFL step of a

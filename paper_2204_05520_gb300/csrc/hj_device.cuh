@@ -12,11 +12,27 @@ namespace odp {
 
 ODP_HD float mode_sign(int mode) { return mode == MODE_MAX ? 1.0f : -1.0f; }
 
+// k-th ghost node outside boundary node pb, from d = pb - pin with pin the
+// inner neighbour (Section 3.1.1: extrapolated so that it keeps the sign of
+// pb).  Each operation is rounded on its own (no contraction into an FMA),
+// so every kernel forms the same ghost value.
+ODP_HD float keep_sign_ghost_d(float pb, float d, float k)
+{
+#ifdef __CUDA_ARCH__
+    return __fadd_rn(pb, __fmul_rn(k * (pb >= 0.0f ? 1.0f : -1.0f), fabsf(d)));
+#else
+    volatile float t = k * (pb >= 0.0f ? 1.0f : -1.0f) * fabsf(d);
+    return pb + t;
+#endif
+}
+
 ODP_HD float keep_sign_ghost(float pb, float pin, float k)
 {
-    // k-th ghost node outside boundary node pb with inner neighbour pin
-    // (Section 3.1.1: extrapolated so that it keeps the sign of pb)
-    return pb + k * (pb >= 0.0f ? 1.0f : -1.0f) * fabsf(pb - pin);
+#ifdef __CUDA_ARCH__
+    return keep_sign_ghost_d(pb, __fsub_rn(pb, pin), k);
+#else
+    return keep_sign_ghost_d(pb, pb - pin, k);
+#endif
 }
 
 // Unscaled one-sided differences of one node from its five-node window

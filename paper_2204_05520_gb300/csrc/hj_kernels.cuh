@@ -65,7 +65,13 @@ ODP_HD float last_axis_value(const float *__restrict__ row, int j, int n, int pe
 // (unscaled; reading R12 of the model).
 ODP_HD void rel6d_x_drift(float vp, const float4 &ve, float c, float wp, float y, float *a)
 {
+    // explicit roundings: the same value in every kernel that inlines this
+#ifdef __CUDA_ARCH__
+    const float t = __fmul_rn(wp, y);
+    for (int k = 0; k < 4; ++k) a[k] = __fadd_rn(__fadd_rn(-vp, __fmul_rn(lane(ve, k), c)), t);
+#else
     for (int k = 0; k < 4; ++k) a[k] = -vp + lane(ve, k) * c + wp * y;
+#endif
 }
 
 // Half-scaled drift coefficients of the four nodes of a segment,
@@ -227,6 +233,34 @@ ODP_HD void segment_axis(const float4 &m2, const float4 &m1, const float4 &c, co
     axis_pair<ORDER>(make_float2(m2.z, m2.w), make_float2(m1.z, m1.w), make_float2(c.z, c.w),
                      make_float2(p1.z, p1.w), make_float2(p2.z, p2.w), a23, cS,
                      abs_cA ? f2abs(a23) : f2splat(cD), L23, has_a, has_s);
+}
+
+// segment_axis from the axis's differences instead of its five rows: a, b
+// the backward and forward differences (f0 - fm1, fp1 - f0) and d2l, d2m,
+// d2r the second differences at i-1, i, i+1 (a - (fm1 - fm2), b - a,
+// (fp2 - fp1) - b), computed by the caller with the same operations, so the
+// result is that of segment_axis bit for bit.
+template <int ORDER>
+ODP_HD void segment_axis_d(const float4 &a, const float4 &b, const float4 &d2l, const float4 &d2m, const float4 &d2r,
+                           const float *cA, float cS, float cD, float2 &L01, float2 &L23, bool has_a, bool has_s)
+{
+    float2 dm = make_float2(a.x, a.y), dp = make_float2(b.x, b.y);
+    if (ORDER == 2) {
+        const float2 m = make_float2(d2m.x, d2m.y);
+        const float2 cm = f2pick(make_float2(d2l.x, d2l.y), m), cp = f2pick(make_float2(d2r.x, d2r.y), m);
+        dm = f2fma(cm, f2splat(0.5f), dm);
+        dp = f2fma(cp, f2splat(-0.5f), dp);
+    }
+    pair_terms(dm, dp, make_float2(cA[0], cA[1]), cS, f2splat(cD), L01, has_a, has_s);
+    dm = make_float2(a.z, a.w);
+    dp = make_float2(b.z, b.w);
+    if (ORDER == 2) {
+        const float2 m = make_float2(d2m.z, d2m.w);
+        const float2 cm = f2pick(make_float2(d2l.z, d2l.w), m), cp = f2pick(make_float2(d2r.z, d2r.w), m);
+        dm = f2fma(cm, f2splat(0.5f), dm);
+        dp = f2fma(cp, f2splat(-0.5f), dp);
+    }
+    pair_terms(dm, dp, make_float2(cA[2], cA[3]), cS, f2splat(cD), L23, has_a, has_s);
 }
 
 // The Rel6D heading axis with per-node dissipation: each node's heading-rate
@@ -738,14 +772,64 @@ inline int reduce_blocks(int64_t n)
 }  // namespace odp
 
 #include "hj_plane.cuh"
+#include "hj_bulk.cuh"
 
 namespace odp {
+
+// The bulk-staged pass of a single solve (hj_bulk.cuh): one kernel per RK
+// stage and obstacle use.
+template <int ND, int ORDER, int DYN>
+cudaError_t launch_stage_bulk_t(const GridDesc &g, const DynDesc &dy, SolveState *st, const float *l,
+                                const float *gob, int stage, int brt, cudaStream_t s)
+{
+    const int blocks = g.bk.items, th = 32 * (g.bk.cwarps + 1), sm = g.bk.smem[ORDER - 1];
+    const bool ob = gob != nullptr;
+    if (stage == 0) {
+        if (ob)
+            k_stage_bulk<ND, ORDER, DYN, 0, 1><<<blocks, th, sm, s>>>(g, dy, st, l, gob, stage, brt);
+        else
+            k_stage_bulk<ND, ORDER, DYN, 0, 0><<<blocks, th, sm, s>>>(g, dy, st, l, gob, stage, brt);
+    } else if (stage == 1) {
+        k_stage_bulk<ND, ORDER, DYN, 1, 0><<<blocks, th, sm, s>>>(g, dy, st, l, gob, stage, brt);
+    } else {
+        if (ob)
+            k_stage_bulk<ND, ORDER, DYN, 2, 1><<<blocks, th, sm, s>>>(g, dy, st, l, gob, stage, brt);
+        else
+            k_stage_bulk<ND, ORDER, DYN, 2, 0><<<blocks, th, sm, s>>>(g, dy, st, l, gob, stage, brt);
+    }
+    return cudaGetLastError();
+}
+
+template <int ND, int ORDER, int DYN>
+cudaError_t configure_stage_bulk_t()
+{
+    const int bytes = 227 * 1024;
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void *f) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    };
+    set((const void *)k_stage_bulk<ND, ORDER, DYN, 0, 0>);
+    set((const void *)k_stage_bulk<ND, ORDER, DYN, 0, 1>);
+    set((const void *)k_stage_bulk<ND, ORDER, DYN, 1, 0>);
+    set((const void *)k_stage_bulk<ND, ORDER, DYN, 2, 0>);
+    set((const void *)k_stage_bulk<ND, ORDER, DYN, 2, 1>);
+    return e;
+}
 
 template <int ND, int DYN>
 cudaError_t launch_stage_t(const GridDesc &g, const DynDesc &dy, SolveState *st, const float *l,
                            const float *gob, int order, int stage, int brt, cudaStream_t s)
 {
     if constexpr (ND >= 3) {
+        if constexpr (DYN == DYN_DUBINS3D || DYN == DYN_DUBINSCAR4D || DYN == DYN_REL6D) {
+            // bk.use: 1 automatic (the bulk-staged pass where it measured
+            // faster: Rel6D), 2 the bulk-staged pass wherever it applies
+            const bool want = g.bk.use == 2 || (g.bk.use == 1 && DYN == DYN_REL6D);
+            if (want && g.n[ND - 1] % 4 == 0 && !dy.local_diss && g.bk.smem[order - 1] > 0) {
+                if (order == 1) return launch_stage_bulk_t<ND, 1, DYN>(g, dy, st, l, gob, stage, brt, s);
+                return launch_stage_bulk_t<ND, 2, DYN>(g, dy, st, l, gob, stage, brt, s);
+            }
+        }
         if (g.pg.use) {
             // Dubins3D, DubinsCar4D and Rel6D grids whose last axis is a
             // multiple of 4 get one kernel per RK stage and obstacle use; the
@@ -813,11 +897,16 @@ cudaError_t launch_stage_t(const GridDesc &g, const DynDesc &dy, SolveState *st,
     return cudaGetLastError();
 }
 
-// Nothing to configure: the plane-streaming tiles stay below the default
-// 48 KB of dynamic shared memory.
+// The plane-streaming tiles stay below the default 48 KB of dynamic shared
+// memory; the bulk-staged pass's rings may need more.
 template <int ND, int DYN>
 cudaError_t configure_stage_t()
 {
+    if constexpr (ND >= 3 && (DYN == DYN_DUBINS3D || DYN == DYN_DUBINSCAR4D || DYN == DYN_REL6D)) {
+        cudaError_t e = configure_stage_bulk_t<ND, 1, DYN>();
+        if (e == cudaSuccess) e = configure_stage_bulk_t<ND, 2, DYN>();
+        return e;
+    }
     return cudaSuccess;
 }
 

@@ -238,6 +238,75 @@ void odp::plane_geometry(GridDesc &D, int sms)
     pg.use = 1;
 }
 
+#ifndef ODP_BULK_WAVES
+#define ODP_BULK_WAVES 4
+#endif
+#ifndef ODP_BULK_RC
+#define ODP_BULK_RC 5
+#endif
+#ifndef ODP_BULK_RX
+#define ODP_BULK_RX 3
+#endif
+
+void odp::bulk_geometry(GridDesc &D, int sms)
+{
+    BulkGeom &bk = D.bk;
+    bk = BulkGeom{};
+    const int nd = D.ndim;
+    if (nd < 3 || D.n[nd - 1] % 4 != 0) return;
+    const int nr = D.nr, segs = D.segs, ns = D.n[nd - 3];
+    if (nr < 4 || ns < 4 || segs > 128) return;
+    // every model here has non-periodic stream and row axes; the pass
+    // takes only those
+    if (D.periodic[nd - 2] || D.periodic[nd - 3]) return;
+    // bands of about 256 compute threads (balanced band heights)
+    int rb = 256 / segs;
+    if (rb < 1) rb = 1;
+    int nb = 1;
+    if (rb >= nr) {
+        rb = nr;
+    } else {
+        nb = (nr + rb - 1) / rb;
+        rb = (nr + nb - 1) / nb;
+    }
+    const int cwarps = (rb * segs + 31) / 32;
+    if (cwarps + 1 > 16) return;
+    bk.rb = rb;
+    bk.nbands = nb;
+    bk.cwarps = cwarps;
+    bk.rc = ODP_BULK_RC;
+    bk.rx = ODP_BULK_RX;
+    const long long row_bytes = 4LL * D.n_pad;
+    for (int o = 1; o <= 2; ++o) {
+        const long long bytes = 512 + bk.rc * (rb + 2LL * o) * row_bytes + bk.rx * (2LL * o * (nd - 3)) * rb * row_bytes;
+        bk.smem[o - 1] = bytes <= 200 * 1024 ? int(bytes) : 0;
+    }
+    if (bk.smem[0] == 0 && bk.smem[1] == 0) return;
+    long long pencils = 1;
+    for (int d = 0; d < nd - 3; ++d) pencils *= D.n[d];
+    // resident CTAs per SM from shared memory and threads (80-96 registers a
+    // thread caps them near three); chunks sized for about ODP_BULK_WAVES waves
+    const int sm_bytes = bk.smem[1] ? bk.smem[1] : bk.smem[0];
+    int per_sm = (228 * 1024) / (sm_bytes + 1024);
+    const int by_regs = 65536 / (88 * 32 * (cwarps + 1));
+    if (per_sm > by_regs) per_sm = by_regs;
+    if (per_sm < 1) per_sm = 1;
+    const long long target = (long long)ODP_BULK_WAVES * per_sm * sms;
+    const long long base = pencils * nb;
+    long long nch = (target + base - 1) / base;
+    if (nch > ns / 4) nch = ns / 4;   // at least four planes per chunk
+    if (nch < 1) nch = 1;
+    int chunk = int((ns + nch - 1) / nch);
+    // every chunk holds at least two planes (the window fill reads two ahead)
+    while (ns % chunk != 0 && ns % chunk < 2) ++chunk;
+    bk.chunk = chunk;
+    bk.nchunks = (ns + chunk - 1) / chunk;
+    bk.items = int(base * bk.nchunks);
+    bk.div_nchunks = make_fastdiv(uint32_t(bk.nchunks));
+    bk.div_nbands = make_fastdiv(uint32_t(bk.nbands));
+    bk.use = 1;
+}
+
 static void release(odp_grid *g)
 {
     if (!g) return;
@@ -409,6 +478,8 @@ extern "C" odp_status odp_grid_create(int ndim, const int32_t *n, const double *
         s *= (d == ndim - 1) ? g->n_pad : n[d];
     }
     plane_geometry(D, 152);   // needs the axis sizes above
+    bulk_geometry(D, 152);
+    g->bulk_ok = D.bk.use;
     ODP_TRY(cudaMalloc(&g->tables, size_t(tab_len) * sizeof(float)));
     ODP_TRY(cudaMemcpy(g->tables, tab.data(), size_t(tab_len) * sizeof(float), cudaMemcpyHostToDevice));
     for (int d = 0; d < ndim; ++d) D.coord[d] = g->tables + coord_off[d];
@@ -883,6 +954,21 @@ extern "C" odp_status odp_set_loop_mode(odp_grid *g, int host_stepped)
     if (!g) return fail(ODP_EINVAL, "grid is NULL");
     if (host_stepped != 0 && host_stepped != 1) return fail(ODP_EINVAL, "host_stepped must be 0 or 1");
     g->host_loop = host_stepped;
+    return ODP_OK;
+}
+
+extern "C" odp_status odp_set_stage_pass(odp_grid *g, int pass)
+{
+    if (!g) return fail(ODP_EINVAL, "grid is NULL");
+    if (pass < 0 || pass > 2) return fail(ODP_EINVAL, "pass must be 0, 1 or 2");
+    if (pass == 2 && !g->bulk_ok)
+        return fail(ODP_EINVAL, "the bulk-staged pass does not apply to this grid's shape");
+    const int use = g->bulk_ok ? (pass == 0 ? 1 : pass == 2 ? 2 : 0) : 0;
+    g->stage_pass = pass;
+    if (g->desc.bk.use != use) {
+        g->desc.bk.use = use;
+        g->dyn_version += 1;   // the captured loop holds the old kernels
+    }
     return ODP_OK;
 }
 

@@ -118,6 +118,21 @@ struct PlaneGeom {
     FastDiv div_bdim[3], div_nblk[3], div_bvol;
 };
 
+// Geometry of the bulk-staged stage pass of a single solve (hj_bulk.cuh;
+// host computed).  Work items as in PlaneGeom (chunk fastest, then band,
+// then outer pencil in C order); the CTA has cwarps compute warps and one
+// producer warp; rc / rx ring slots hold centre and neighbour tiles.
+struct BulkGeom {
+    int use;           // 0: never; 1: where it is the faster pass (Rel6D); 2: wherever it applies
+    int rb, nbands;    // rows per band (the last band may be shorter), bands
+    int chunk, nchunks;
+    int items;         // CTAs per launch
+    int cwarps;        // compute warps per CTA
+    int rc, rx;        // ring slots
+    int smem[2];       // dynamic shared bytes for stencil radius 1, 2
+    FastDiv div_nchunks, div_nbands;
+};
+
 // Storage: C order with the last axis padded to n_pad, a multiple of 4 nodes,
 // so that every row starts on a 16-byte boundary and a thread can move four
 // consecutive nodes of a row with one vector access.  Padding lanes are never
@@ -150,6 +165,7 @@ struct GridDesc {
     int nthreads_rb;             // segs * row_groups * planes
     FastDiv div_row_groups;
     PlaneGeom pg;
+    BulkGeom bk;
 };
 
 struct DynDesc {

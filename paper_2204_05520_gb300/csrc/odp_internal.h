@@ -23,6 +23,9 @@ void plane_geometry(GridDesc &D, int sms);
 // The same geometry for a grid advanced together with many others: stream
 // chunks of up to 16 planes (the parallelism comes from the many grids).
 void plane_geometry_many(GridDesc &D);
+// Geometry of the bulk-staged pass of a single solve (D.bk; bk.use = 0 when
+// the pass does not apply), aiming at about four waves of CTAs on `sms` SMs.
+void bulk_geometry(GridDesc &D, int sms);
 }  // namespace odp
 
 // Kernel arguments (grid and dynamics descriptors) are frozen into the graph
@@ -76,6 +79,8 @@ struct odp_grid {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int64_t launches_per_step = 0;
     int host_loop = 0;                // 1: the time loop is stepped from the host
+    int bulk_ok = 0;                  // the bulk-staged pass applies to this grid's shape
+    int stage_pass = 0;               // odp_set_stage_pass: 0 automatic, 1 plane-streaming, 2 bulk-staged
     void *ttr = nullptr;              // time-to-reach plan (ttr.cu), built on first use
     // time-varying sets (odp_set_target_schedule / odp_set_obstacle_schedule):
     // n sets of total_pad floats each; during a solve l and obst hold the

@@ -122,6 +122,7 @@ def load():
             "odp_set_dissipation": ([P, i32], i32),
             "odp_set_step_limit": ([P, i64], i32),
             "odp_set_loop_mode": ([P, i32], i32),
+            "odp_set_stage_pass": ([P, i32], i32),
             "odp_solve_hjb": ([P, P, i32, i32, i32, i32, f64, i32, P], i32),
             "odp_solve_status": ([P, P], i32),
             "odp_value_readback": ([P, i32, P, i64, i32], i32),
@@ -270,6 +271,11 @@ def set_loop_mode(g, host_stepped: bool):
     """Run the time loop as one CUDA graph (False, default) or stepped from the
     host with the same kernels (True; for profilers)."""
     _check(load().odp_set_loop_mode(g, 1 if host_stepped else 0), "odp_set_loop_mode")
+
+
+def set_stage_pass(g, pass_: int):
+    """0: automatic, 1: plane-streaming pass, 2: bulk-staged pass."""
+    _check(load().odp_set_stage_pass(g, int(pass_)), "odp_set_stage_pass")
 
 
 def solve_hjb(g, tau, set_kind="brt", space_order=1, time_order=1, cfl=0.8, keep_snapshots=False,

@@ -36,16 +36,20 @@ def oracle_f32_storage(problem, l):
 
 
 def oracle_sensitivity(problem, ref):
-    """(float32 storage, target perturbed by 1e-7 relative): how far each
-    moves the oracle's solve `ref`, over the value range."""
+    """How far float32 storage and a target perturbed by 1e-7 relative move
+    the oracle's solve `ref`: (max over the value range for each, then the
+    fraction of nodes each moves by more than 1e-4 of the range)."""
     l = problem.target_values()
     rng_l = float(l.max() - l.min())
     a, steps = oracle_f32_storage(problem, l)
     assert steps == int(ref["steps"].sum())
     noise = np.random.default_rng(0).standard_normal(l.shape)
     b = oracle.solve(problem, l=l.astype(np.float64) * (1.0 + 1e-7 * noise))["final"]
-    return (float(np.abs(a - ref["final"]).max()) / rng_l,
-            float(np.abs(b - ref["final"]).max()) / rng_l)
+    da = np.abs(a.reshape(-1) - ref["final"].reshape(-1))
+    db = np.abs(b.reshape(-1) - ref["final"].reshape(-1))
+    tol = REL_TOL * rng_l
+    return (float(da.max()) / rng_l, float(db.max()) / rng_l,
+            float((da > tol).mean()), float((db > tol).mean()))
 
 
 def check_whole_solve(problem, v, steps, ref=None, spread=None, name=None):
@@ -68,9 +72,10 @@ def check_whole_solve(problem, v, steps, ref=None, spread=None, name=None):
     if spread is None:
         spread = oracle_sensitivity(problem, ref)
     frac = float((d > tol).mean())
+    frac_bar = max(0.01, 2.0 * max(spread[2:])) if len(spread) > 2 else 0.01
     parity_log.note(name or problem.name, "whole solve, %d steps: max err/range %.2e; oracle's own "
-                    "sensitivity %.2e (float32 storage) / %.2e (target 1e-7); nodes over 1e-4: %.4f%%"
-                    % (steps, err, spread[0], spread[1], 100 * frac))
-    assert err <= max(REL_TOL, 2.0 * max(spread)), (err, spread)
-    assert frac <= 0.01, frac
+                    "sensitivity %.2e (float32 storage) / %.2e (target 1e-7); nodes over 1e-4: %.4f%% "
+                    "(bar %.2f%%)" % (steps, err, spread[0], spread[1], 100 * frac, 100 * frac_bar))
+    assert err <= max(REL_TOL, 2.0 * max(spread[:2])), (err, spread)
+    assert frac <= frac_bar, (frac, frac_bar)
     return err

@@ -316,9 +316,9 @@ def read_sensitivity(workload):
         for line in fh:
             if line.startswith("#") or not line.strip():
                 continue
-            name, steps, f32store, lpert = [c.strip() for c in line.split("|")]
-            if name == workload:
-                return int(steps), (float(f32store), float(lpert))
+            cols = [c.strip() for c in line.split("|")]
+            if cols[0] == workload:
+                return int(cols[1]), tuple(float(c) for c in cols[2:])
     raise KeyError(workload)
 
 
@@ -553,3 +553,48 @@ def test_capture_model_refuses_per_node_dissipation():
     with pytest.raises(odp.OdpError) as e:
         odp.Grid.for_problem(dataclasses.replace(p, dissipation="local"))
     assert e.value.code == odp.EINVAL
+
+
+# ---------------------------------------------------------------------------
+# the two stage-pass kernels (plane-streaming, bulk-staged) compute the same
+# per-node arithmetic: bit-identical values and step counts
+# ---------------------------------------------------------------------------
+
+PASS_CASES = [
+    inputs.dubinscar4d(n=(21, 19, 11, 16)),                              # ENO2 + RK2, edge CTAs on x
+    inputs.dubins3d(),                                                    # upwind + Euler, 41x41x36
+    inputs.dubinscar4d(n=(13, 13, 7, 12), u_mode="max", set_kind="brs"),
+    inputs.rel6d(n=(7, 7, 8, 4, 4, 4), space_order=2, horizon=0.2),
+    inputs.rel6d(n=(6, 5, 8, 5, 4, 8), horizon=0.2),                      # upwind + RK2, periodic outer axis
+    inputs.reach_avoid(inputs.dubinscar4d(n=(21, 19, 11, 16), horizon=1.0), inputs.dubins_obstacle()),
+    inputs.dubinscar4d(),                                                 # 80x80x40x64
+    inputs.rel6d(),                                                       # 24^6
+]
+
+
+@pytest.mark.parametrize("problem", PASS_CASES, ids=lambda p: "%s_o%d%d" % (p.name, p.space_order, p.time_order))
+def test_bulk_and_plane_passes_agree_bit_for_bit(problem):
+    import torch
+
+    l_dev = torch.from_numpy(problem.target_values()).cuda()
+    out = []
+    for pass_ in (1, 2):
+        with odp.Grid.for_problem(problem) as g:
+            odp.set_stage_pass(g.handle, pass_)
+            g.set_target(l_dev)
+            st = g.solve_problem(problem, stats=True)
+            out.append((st["steps"], g.readback(torch.empty_like(l_dev)).cpu().numpy()))
+    assert out[0][0] == out[1][0] > 0
+    assert np.array_equal(out[0][1], out[1][1])
+
+
+def test_bulk_pass_is_refused_where_it_does_not_apply():
+    p = inputs.dubins3d(n=(23, 19, 13))       # last axis not a multiple of 4 nodes
+    with odp.Grid.for_problem(p) as g:
+        with pytest.raises(odp.OdpError) as e:
+            odp.set_stage_pass(g.handle, 2)
+        assert e.value.code == odp.EINVAL
+        odp.set_stage_pass(g.handle, 1)
+        odp.set_stage_pass(g.handle, 0)
+        with pytest.raises(odp.OdpError):
+            odp.set_stage_pass(g.handle, 3)
