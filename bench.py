@@ -60,6 +60,8 @@ def parse_args():
                     help="served workload: cap on the grid nodes of resident solves, millions (0: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline workload only (skip the other configurations)")
     ap.add_argument("--dissipation", choices=("global", "local"), default="global",
                     help="Lax-Friedrichs dissipation: grid alpha or each node's own alpha")
     ap.add_argument("--host-loop", action="store_true",
@@ -370,6 +372,77 @@ def run_reference(args):
 # our arm
 # ---------------------------------------------------------------------------
 
+# FP32 lane operations per node of one stage of the ENO2 Lax-Friedrichs
+# update (Algorithm 1), counted from the scheme: per axis 7 differences, 2
+# magnitude comparisons and 2 selects (the ENO choice), 2 fused multiply-adds
+# (p-, p+), 2 additions (their sum and difference) and 2 fused multiply-adds
+# (drift or input-bound term, dissipation) = 17; plus the update (1 fused
+# multiply-add; RK2 stage 2 adds the Heun average, 2, and the BRT min, 1).
+ALU_OPS_PER_AXIS = {1: 8, 2: 17}   # upwind: 2 differences, 2 additions, 2 + 2 fused multiply-adds
+GB300_FP32_LANE_OPS = 152 * 128 * 2.07e9   # SMs x FP32 lanes x maximum SM clock
+
+
+def alu_ops_per_node_step(problem) -> float:
+    per_stage = ALU_OPS_PER_AXIS[problem.space_order] * problem.ndim
+    if problem.time_order == 2:
+        return (per_stage + 1) + (per_stage + 1 + 2 + (1 if problem.set_kind == "brt" else 0))
+    return per_stage + 1 + (1 if problem.set_kind == "brt" else 0)
+
+
+def measure_solve(problem, steps, warmup, stream=None):
+    """Device time of `steps` whole solves (one CUDA graph each) of `problem`
+    with its values resident; returns a dict of figures."""
+    import torch
+
+    from paper_2204_05520_gb300 import odp
+
+    stream = stream or torch.cuda.Stream()
+    N = problem.points
+    l_dev = torch.from_numpy(problem.target_values()).cuda()
+    with odp.Grid.for_problem(problem, stream=stream) as grid:
+        grid.set_target(l_dev)
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                grid.solve_problem(problem)
+        st = odp.solve_status(grid.handle)
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            grid.solve_problem(problem)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        odp.solve_status(grid.handle)
+        ms = ev0.elapsed_time(ev1) / steps
+        stages = (1, 2) if problem.time_order == 2 else (0,)
+        stage_ms = [odp.time_stage(grid.handle, k, reps=10) for k in stages]
+    n_steps = int(st["steps"])
+    return {"workload": problem.name, "nodes": N, "time_steps_per_solve": n_steps, "ms_per_solve": ms,
+            "solves_per_s": 1000.0 / ms, "updates_per_s": N * n_steps / (ms / 1000.0),
+            "alg_bytes_per_solve": float(st["bytes"]),
+            "roofline_frac": float(st["bytes"]) / (ms / 1000.0) / 1e9 / hbm_peak()[0],
+            "alu_frac": alu_ops_per_node_step(problem) * N * n_steps / (ms / 1000.0) / GB300_FP32_LANE_OPS,
+            "stage_ms_isolated": stage_ms, "gpu_launches_per_solve": int(st["launches"])}
+
+
+def extra_workloads(args):
+    """The other configurations beside the headline, on one GPU: the 3D
+    Dubins car (41x41x36), the 6D relative model (24^6), 512 batched
+    Dubins3D solves and the served Poisson stream at three rates."""
+    from paper_2204_05520_gb300 import inputs
+
+    out = {}
+    out["dubins3d_41x41x36"] = measure_solve(inputs.workload("dubins3d"), 50, 5)
+    out["rel6d_24^6"] = measure_solve(inputs.workload("rel6d"), 2, 1)
+    out["batch512_dubins3d"] = measure_batch(3, 2)
+    points, single = measure_served([10.0, 30.0, 100.0], 2.0, args.budget_gb)
+    out["served_poisson"] = {"rates": points, "window_s": 2.0, "budget_gb": args.budget_gb,
+                             "saturation_solves_per_s": max((pt["solves_per_s"] or 0.0) for pt in points),
+                             "one_at_a_time_solves_per_s": single}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -435,7 +508,8 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                 "traffic": dram_traffic(problem.name),
-                "kernel": "k_stage_plane (whole time loop timed)", "peak_source": peak_kind,
+                "kernel": "%s (whole time loop timed)" % (
+                    "k_stage_bulk" if problem.dynamics == "rel6d" else "k_stage_plane"), "peak_source": peak_kind,
                 "alg_bytes_per_launch": bytes_per_solve / stage_launches,
                 "avg_launch_ms": ms_per_step / stage_launches,
                 "stage_ms_isolated": stage_ms}
@@ -478,6 +552,14 @@ def run_ours(args):
             cpu["single_core"] = {"value": ups1, "unit": UNIT, "cores": 1,
                                   "sample": "%d time step(s) of the full grid, %.1f s" % (nst1, secs1)}
 
+    extras = None
+    if world == 1 and args.workload == "dubinscar4d" and not args.no_extras:
+        extras = extra_workloads(args)
+    alu = {"bound": "alu", "achieved": alu_ops_per_node_step(problem) * N * steps_per_solve / (ms_per_step / 1000.0),
+           "peak": GB300_FP32_LANE_OPS, "unit": "FP32 lane ops/s",
+           "frac": alu_ops_per_node_step(problem) * N * steps_per_solve / (ms_per_step / 1000.0) / GB300_FP32_LANE_OPS,
+           "ops_per_node_step": alu_ops_per_node_step(problem)}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -500,6 +582,9 @@ def run_ours(args):
             "clocks": clocks,
             "alg_bytes_per_solve": bytes_per_solve,
             "solves_per_s": world * 1000.0 / ms_per_step,
+            "roofline_alu": alu,
+            "stage_pass": "plane-streaming" if problem.dynamics != "rel6d" else "bulk-staged",
+            "extra_workloads": extras,
         }
         print(json.dumps(line), flush=True)
     grid.close()
@@ -583,6 +668,14 @@ def run_ttr(args):
         ups, secs, threads, nsw = oracle_ttr_sample(problem, want)
         cpu = {"value": ups, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "%d sweeps of the full %s grid (%d nodes), %.1f s" % (nsw, problem.name, N, secs)}
+    extras = None
+    if world == 1 and args.workload == "dubinscar4d" and not args.no_extras:
+        extras = extra_workloads(args)
+    alu = {"bound": "alu", "achieved": alu_ops_per_node_step(problem) * N * steps_per_solve / (ms_per_step / 1000.0),
+           "peak": GB300_FP32_LANE_OPS, "unit": "FP32 lane ops/s",
+           "frac": alu_ops_per_node_step(problem) * N * steps_per_solve / (ms_per_step / 1000.0) / GB300_FP32_LANE_OPS,
+           "ops_per_node_step": alu_ops_per_node_step(problem)}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -610,18 +703,14 @@ def run_ttr(args):
     return 0
 
 
-def run_batch(args):
-    """512 independent Dubins3D BRT solves (seed 0): one batched persistent
-    launch against the same solves issued one at a time."""
+def measure_batch(steps, warmup, dist=None, local=0):
+    """512 independent Dubins3D BRT solves (seed 0): one batched call against
+    the same solves issued one at a time through grids created beforehand
+    (no allocation in either timed region).  Returns a dict of figures."""
     import torch
 
-    from paper_2204_05520_gb300 import _build, inputs, odp
+    from paper_2204_05520_gb300 import inputs, odp
 
-    rank, world, local = rank_info()
-    torch.cuda.set_device(local)
-    dist = dist_setup(world, True)
-    _build.build()
-    odp.load()
     problems = inputs.batch_problems(count=512, seed=0)
     stream = torch.cuda.Stream()
     grids = []
@@ -630,71 +719,88 @@ def run_batch(args):
         g.set_target(torch.from_numpy(p.target_values()).cuda())
         grids.append(g)
     horizons = [p.tau[-1] for p in problems]
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         st = odp.batch_solve(grids, horizons)
     torch.cuda.synchronize()
     barrier(dist)
     t0 = time.perf_counter()
     dev_ms = 0.0
-    for _ in range(args.steps):
+    for _ in range(steps):
         st = odp.batch_solve(grids, horizons)
         dev_ms += st["device_ms"]
-    batched_s = max_over_ranks(dist, (time.perf_counter() - t0) / args.steps, torch.device("cuda", local))
-    # one at a time through the single-solve graph
+    batched_s = max_over_ranks(dist, (time.perf_counter() - t0) / steps, torch.device("cuda", local))
+    # one at a time through the single-solve graph of each (pre-created) grid
     for g, p in zip(grids, problems):
         g.solve_problem(p)
     torch.cuda.synchronize()
+    reps = max(1, steps // 5)
     t0 = time.perf_counter()
-    for _ in range(max(1, args.steps // 5)):
+    for _ in range(reps):
         for g, p in zip(grids, problems):
             g.solve_problem(p)
         torch.cuda.synchronize()
-    single_s = (time.perf_counter() - t0) / max(1, args.steps // 5)
-    single_s = max_over_ranks(dist, single_s, torch.device("cuda", local))
-    if rank == 0:
-        n = len(problems)
-        line = {
-            "metric": "batched solves/s", "value": world * n / batched_s, "unit": "solves/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * batched_s, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batch512_dubins3d", "solves": n, "nodes": sum(p.points for p in problems),
-                       "rounds": st["rounds"], "ctas_per_sm": st["ctas_per_sm"]},
-            "point_updates_per_s": st["point_updates"] / batched_s,
-            "device_ms_per_batch": dev_ms / args.steps,
-            "one_at_a_time": {"solves_per_s": n / single_s, "s_per_batch": single_s},
-            "speedup_vs_one_at_a_time": single_s / batched_s,
-            "roofline": {"bound": "hbm", "achieved": st["bytes"] / (dev_ms / args.steps / 1000.0) / 1e9,
-                         "peak": hbm_peak()[0], "unit": "GB/s",
-                         "frac": st["bytes"] / (dev_ms / args.steps / 1000.0) / 1e9 / hbm_peak()[0]},
-        }
-        print(json.dumps(line), flush=True)
+    single_s = max_over_ranks(dist, (time.perf_counter() - t0) / reps, torch.device("cuda", local))
+    n = len(problems)
+    dev_s = dev_ms / steps / 1000.0
+    out = {"solves": n, "nodes": sum(p.points for p in problems), "rounds": st["rounds"],
+           "batched_s": batched_s, "batched_solves_per_s": n / batched_s,
+           "device_ms_per_batch": 1000.0 * dev_s, "point_updates_per_s": st["point_updates"] / batched_s,
+           "launches_per_batch": st.get("launches"), "tuned": st.get("tuned"),
+           "one_at_a_time_solves_per_s": n / single_s, "one_at_a_time_s": single_s,
+           "speedup_vs_one_at_a_time": single_s / batched_s,
+           "roofline_frac": st["bytes"] / dev_s / 1e9 / hbm_peak()[0]}
     for g in grids:
         g.close()
-    return 0
+    return out
 
 
-def run_served(args):
-    """Poisson request stream (seed 1) of Dubins3D and DubinsCar4D solves
-    served with continuous batching under an HBM budget; p50/p99 latency
-    (arrival -> result ready) and completed solves/s per arrival rate."""
-    import numpy as np
+def run_batch(args):
     import torch
 
-    from paper_2204_05520_gb300 import _build, inputs, odp
+    from paper_2204_05520_gb300 import _build, odp
 
     rank, world, local = rank_info()
     torch.cuda.set_device(local)
+    dist = dist_setup(world, True)
     _build.build()
     odp.load()
+    b = measure_batch(args.steps, args.warmup, dist, local)
+    if rank == 0:
+        line = {
+            "metric": "batched solves/s", "value": world * b["batched_solves_per_s"], "unit": "solves/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * b["batched_s"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch512_dubins3d", "solves": b["solves"], "nodes": b["nodes"],
+                       "rounds": b["rounds"]},
+            "point_updates_per_s": b["point_updates_per_s"],
+            "device_ms_per_batch": b["device_ms_per_batch"],
+            "one_at_a_time": {"solves_per_s": b["one_at_a_time_solves_per_s"], "s_per_batch": b["one_at_a_time_s"]},
+            "speedup_vs_one_at_a_time": b["speedup_vs_one_at_a_time"],
+            "roofline": {"bound": "hbm", "frac": b["roofline_frac"], "peak": hbm_peak()[0], "unit": "GB/s"},
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def measure_served(rates, window, budget_gb, max_resident_mnodes=0.0, single_count=24):
+    """Poisson request streams (seed 1) of Dubins3D and DubinsCar4D solves
+    served with continuous batching under an HBM budget; p50/p99 latency
+    (arrival -> result ready) and completed solves/s per arrival rate, and
+    the same requests solved one at a time through grids created before the
+    timed region.  Returns (points, one_at_a_time_solves_per_s)."""
+    import numpy as np
+    import torch
+
+    from paper_2204_05520_gb300 import inputs, odp
+
     stream = torch.cuda.Stream()
-    rates = [float(r) for r in args.rates.split(",")]
     points = []
-    budget = int(args.budget_gb * (1 << 30))
+    budget = int(budget_gb * (1 << 30))
     with odp.Server(budget, stream=stream) as srv:
-        srv.set_max_resident(int(args.max_resident_mnodes * 1e6))
+        srv.set_max_resident(int(max_resident_mnodes * 1e6))
         for rate in rates:
-            count = int(min(2000, max(10, rate * args.window)))
+            count = int(min(2000, max(10, rate * window)))
             stream_reqs = inputs.served_requests(rate, count=count, seed=1)
             targets = [p.target_values() for _, p in stream_reqs]
             outs = {}
@@ -702,7 +808,7 @@ def run_served(args):
             t0 = time.monotonic()
             nxt = 0
             done = 0
-            deadline = t0 + 20.0 + args.window
+            deadline = t0 + 20.0 + window
             while done < count and time.monotonic() < deadline:
                 now = time.monotonic() - t0
                 while nxt < count and stream_reqs[nxt][0] <= now:
@@ -738,16 +844,39 @@ def run_served(args):
             # drain anything still resident before the next rate
             while srv.info()["resident"] or srv.info()["queued"]:
                 srv.step(rounds=64)
-    # one at a time: requests of the same stream solved sequentially
-    reqs = inputs.served_requests(rates[-1], count=min(40, int(rates[-1] * args.window)), seed=1)
+    # one at a time: requests of the same stream, each solved through its own
+    # grid created (and given its target) before the timed region, result read
+    # back to the host
+    reqs = [p for _, p in inputs.served_requests(rates[-1], count=single_count, seed=1)]
+    grids = []
+    for p in reqs:
+        g = odp.Grid.for_problem(p, stream=stream)
+        g.set_target(p.target_values())
+        grids.append(g)
+    outs = [np.empty(p.n, np.float32) for p in reqs]
+    grids[0].solve_problem(reqs[0])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _, p in reqs:
-        with odp.Grid.for_problem(p, stream=stream) as g:
-            g.set_target(p.target_values())
-            g.solve_problem(p)
-            g.readback(np.empty(p.n, np.float32))
+    for g, p, o in zip(grids, reqs, outs):
+        g.solve_problem(p)
+        g.readback(o)
     single = len(reqs) / (time.perf_counter() - t0)
+    for g in grids:
+        g.close()
+    return points, single
+
+
+def run_served(args):
+    import torch
+
+    from paper_2204_05520_gb300 import _build, odp
+
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    _build.build()
+    odp.load()
+    rates = [float(r) for r in args.rates.split(",")]
+    points, single = measure_served(rates, args.window, args.budget_gb, args.max_resident_mnodes)
     best = max((pt["solves_per_s"] or 0.0) for pt in points)
     if rank == 0:
         line = {"metric": "served solves/s (saturation) with p50/p99 latency", "value": best,

@@ -263,6 +263,13 @@ typedef struct {
     int32_t rows_per_thread;
     double point_updates;  /* sum over grids of nodes x steps                  */
     double bytes;          /* algorithmic HBM bytes                            */
+    int32_t plane_chunk;   /* plane path: stream planes per CTA, chosen by the
+                              autotuner (0: row-blocked path)                 */
+    int32_t graph;         /* plane path: 1 the batch graph was captured by
+                              this call, 2 a cached graph was replayed        */
+    int64_t launches;      /* plane path: kernel launches in the batch graph   */
+    int32_t tuned;         /* 1: this call ran the autotuner                   */
+    int32_t reserved;
 } odp_batch_stats;
 
 /* Solve n independent grids over [0, T[i]] together.  Every grid must have
@@ -272,7 +279,11 @@ typedef struct {
  * float64 step schedule, same per-node kernel arithmetic) and its final value
  * is read back with odp_value_readback(g, -1).  When every grid is a Dubins3D
  * or DubinsCar4D grid that the plane-streaming pass takes, each round (step
- * index) and RK phase is one launch over every grid still running; other
+ * index) and RK phase is one launch over every grid still running, all of
+ * them one CUDA graph captured once per batch signature (model, orders,
+ * grid count, rounds, launch shapes) and replayed by later calls; the
+ * stream-chunk cap of the plane items (8, 16, 32 or 64 planes per CTA) is
+ * autotuned on the first rounds and cached per signature; other
  * batches run one persistent cooperative launch of the row-blocked pass, its
  * shape (CTAs per SM) autotuned on the first rounds and cached per batch
  * signature.  Supported models: Dubins3D, DubinsCar4D, and the 2-3D single
@@ -397,12 +408,17 @@ odp_status odp_server_info(odp_server *s, odp_server_stats *out);
  *  cuda_stream  stream the work runs on (NULL: legacy default stream); the
  *               call synchronises it before returning
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents:
- * each call clears what must start at zero, and calls whose GPU work overlaps
- * (for example on two streams at once) race on it.
- * Errors: ODP_EINVAL (arguments, or a grid needing more than the array holds:
- * about 1.3 million nodes), ODP_ENUMERIC, ODP_ECUDA. */
+ * device, with that device current).  The call copies its small records
+ * from host memory and synchronises its stream before returning, so it
+ * cannot be recorded into a CUDA graph: on a capturing stream it returns
+ * ODP_EINVAL.  All calls share the array and it keeps the last call's
+ * contents: each call clears what must start at zero.  Calls whose GPU work
+ * overlapped would race on the array; the library prevents that within a
+ * process by holding a per-device lock for the whole call (calls on one
+ * device run one after another; calls on different devices do not wait for
+ * each other).  The caller's current device is restored before returning.
+ * Errors: ODP_EINVAL (arguments, a capturing stream, or a grid needing more
+ * than the array holds: about 1.3 million nodes), ODP_ENUMERIC, ODP_ECUDA. */
 odp_status odp_solve_noalloc(int ndim, const int32_t *n, const double *lo, const double *hi,
                              const uint8_t *periodic, odp_dyn kind, const double *params, int n_params,
                              odp_mode u_mode, odp_mode d_mode, const float *l, double T, odp_set set,

@@ -308,36 +308,57 @@ static cudaError_t launch_plane_round(int order, int ctas, int threads, int smem
                                       const int *sorted, const int *item_start, int n, int round, int phase,
                                       cudaStream_t s)
 {
-    if (order == 1) {
-        cudaError_t e = cudaFuncSetAttribute(k_batch_plane<ND, 1, DYN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             smem);
-        if (e != cudaSuccess) return e;
+    if (order == 1)
         k_batch_plane<ND, 1, DYN><<<ctas, threads, smem, s>>>(bg, sorted, item_start, n, round, phase);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(k_batch_plane<ND, 2, DYN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             smem);
-        if (e != cudaSuccess) return e;
+    else
         k_batch_plane<ND, 2, DYN><<<ctas, threads, smem, s>>>(bg, sorted, item_start, n, round, phase);
-    }
     return cudaGetLastError();
+}
+
+// The dynamic shared memory the round launches need (set before capturing
+// them: it is not a stream operation).
+template <int ND, int DYN>
+static cudaError_t set_plane_smem(int order, int smem)
+{
+    if (order == 1)
+        return cudaFuncSetAttribute(k_batch_plane<ND, 1, DYN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return cudaFuncSetAttribute(k_batch_plane<ND, 2, DYN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 
-void plane_geometry_many(GridDesc &D)
+// Stream-axis chunks of up to `cap` planes (the parallelism of a batch comes
+// from its many grids, so the single-solve geometry, which cuts finer, is
+// recut).
+static void plane_geometry_chunk(GridDesc &D, int cap)
 {
-    // the parallelism comes from the many grids: stream-axis chunks of up to
-    // 16 planes (the single-solve geometry cuts finer)
     PlaneGeom &pg = D.pg;
     if (!pg.use) return;
     const int pencils = pg.items / (pg.nbands * pg.nchunks);
-    pg.chunk = pg.ns < 16 ? pg.ns : 16;
+    pg.chunk = pg.ns < cap ? pg.ns : cap;
     pg.nchunks = (pg.ns + pg.chunk - 1) / pg.chunk;
     pg.items = pencils * pg.nbands * pg.nchunks;
     pg.div_nchunks = make_fastdiv(uint32_t(pg.nchunks));
 }
+
+void plane_geometry_many(GridDesc &D) { plane_geometry_chunk(D, 16); }
+
+// The CUDA graph of a plane-path batch's per-round launches, kept for the
+// batch signature it was captured for (the launch shapes and the workspace
+// pointers its kernel arguments hold).
+struct PlaneGraphKey {
+    int kind = -1, order = 0, time_order = 0, n = 0, rounds = 0, chunk = 0, threads = 0, smem = 0;
+    const void *bg = nullptr, *ints = nullptr;
+    std::vector<int> active;   // CTAs of every launch
+    bool operator==(const PlaneGraphKey &o) const
+    {
+        return kind == o.kind && order == o.order && time_order == o.time_order && n == o.n && rounds == o.rounds &&
+               chunk == o.chunk && threads == o.threads && smem == o.smem && bg == o.bg && ints == o.ints &&
+               active == o.active;
+    }
+};
 
 struct BatchWorkspace {
     std::mutex mu;
@@ -347,6 +368,10 @@ struct BatchWorkspace {
     BatchBarrier *bar = nullptr;
     size_t cap_grids = 0, cap_ints = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    PlaneGraphKey graph_key;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t cap_stream = nullptr;   // private stream the batch graph is captured on
+    int cap_device = -1;
 };
 
 static BatchWorkspace &workspace()
@@ -401,6 +426,17 @@ using namespace odp;
     } while (0)
 
 static std::map<TuneKey, int> g_tuned;
+// plane-path batches: the tuned stream-chunk cap per batch signature
+struct PlaneTuneKey {
+    int kind, order, time_order, n, rounds;
+    double nodes;
+    bool operator<(const PlaneTuneKey &o) const
+    {
+        return std::tie(kind, order, time_order, n, rounds, nodes) <
+               std::tie(o.kind, o.order, o.time_order, o.n, o.rounds, o.nodes);
+    }
+};
+static std::map<PlaneTuneKey, int> g_plane_tuned;
 static std::mutex g_tuned_mu;
 static int g_tune_enabled = 1;
 
@@ -534,24 +570,158 @@ extern "C" odp_status odp_batch_solve(odp_grid *const *grids, int n, const doubl
     const int *d_active_rk2 = d_active + rounds;
 
     if (plane) {
-        int threads = 32, smem = 0;
-        for (int i = 0; i < n; ++i) {
-            threads = std::max(threads, hb[size_t(i)].g.pg.threads);
-            smem = std::max(smem, hb[size_t(i)].g.pg.smem[space_order - 1]);
-        }
-        ODP_TRY_CUDA(cudaEventRecord(W.ev0, s));
-        for (int r = 0; r < rounds; ++r) {
-            for (int phase = 0; phase < time_order; ++phase) {
-                const int ctas = phase == 0 ? active[size_t(r)] : active_rk2[size_t(r)];
-                if (ctas == 0) continue;
-                cudaError_t e = kind0 == DYN_DUBINS3D
-                                    ? launch_plane_round<3, DYN_DUBINS3D>(space_order, ctas, threads, smem, W.bg,
-                                                                          d_sorted, d_start, n, r, phase, s)
-                                    : launch_plane_round<4, DYN_DUBINSCAR4D>(space_order, ctas, threads, smem, W.bg,
-                                                                             d_sorted, d_start, n, r, phase, s);
-                ODP_TRY_CUDA(e);
+        // The plane layout of the batch for a stream-chunk cap: every grid's
+        // items, the item list, the active prefix of every launch; uploaded.
+        int threads = 32, smem = 0, chunk = 16;
+        std::vector<int> launch_ctas;
+        auto apply = [&](int cap) -> cudaError_t {
+            chunk = cap;
+            threads = 32;
+            smem = 0;
+            for (int i = 0; i < n; ++i) {
+                BatchGrid &B = hb[size_t(i)];
+                B.g.pg = grids[i]->desc.pg;
+                plane_geometry_chunk(B.g, cap);
+                B.items = B.g.pg.items;
+                threads = std::max(threads, B.g.pg.threads);
+                smem = std::max(smem, B.g.pg.smem[space_order - 1]);
+            }
+            for (int k = 0; k < n; ++k)
+                item_start[size_t(k) + 1] = item_start[size_t(k)] + hb[size_t(sorted[size_t(k)])].items;
+            int k = n;
+            launch_ctas.clear();
+            for (int r = 0; r < rounds; ++r) {
+                while (k > 0 && hb[size_t(sorted[size_t(k) - 1])].n_steps <= r) --k;
+                active[size_t(r)] = item_start[size_t(k)];
+                active_rk2[size_t(r)] = time_order == 2 ? active[size_t(r)] : 0;
+                launch_ctas.push_back(active[size_t(r)]);
+                if (time_order == 2) launch_ctas.push_back(active_rk2[size_t(r)]);
+            }
+            packed.clear();
+            packed.insert(packed.end(), sorted.begin(), sorted.end());
+            packed.insert(packed.end(), item_start.begin(), item_start.end());
+            packed.insert(packed.end(), active.begin(), active.end());
+            packed.insert(packed.end(), active_rk2.begin(), active_rk2.end());
+            cudaError_t e = cudaMemcpyAsync(W.bg, hb.data(), sizeof(BatchGrid) * size_t(n), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(W.ints, packed.data(), sizeof(int) * nints, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = kind0 == DYN_DUBINS3D ? set_plane_smem<3, DYN_DUBINS3D>(space_order, smem)
+                                                            : set_plane_smem<4, DYN_DUBINSCAR4D>(space_order, smem);
+            return e;
+        };
+        auto launch_rounds = [&](int r1) -> cudaError_t {
+            for (int r = 0; r < r1; ++r) {
+                for (int phase = 0; phase < time_order; ++phase) {
+                    const int ctas = phase == 0 ? active[size_t(r)] : active_rk2[size_t(r)];
+                    if (ctas == 0) continue;
+                    cudaError_t e = kind0 == DYN_DUBINS3D
+                                        ? launch_plane_round<3, DYN_DUBINS3D>(space_order, ctas, threads, smem, W.bg,
+                                                                              d_sorted, d_start, n, r, phase, s)
+                                        : launch_plane_round<4, DYN_DUBINSCAR4D>(space_order, ctas, threads, smem,
+                                                                                 W.bg, d_sorted, d_start, n, r, phase, s);
+                    if (e != cudaSuccess) return e;
+                }
+            }
+            return cudaSuccess;
+        };
+
+        // Autotuner: the stream-chunk cap (planes per CTA, which sets the
+        // items per grid and so the CTAs of every launch), timed on the first
+        // rounds of this batch and cached per batch signature.  Every probe
+        // restarts from round 0, which reads the targets, so the probes
+        // leave no trace in the solve.
+        double nodes_all = 0.0;
+        for (int i = 0; i < n; ++i) nodes_all += double(grids[i]->total);
+        const PlaneTuneKey tkey{kind0, space_order, time_order, n, rounds, nodes_all};
+        int best_cap = 16;
+        bool have = false;
+        {
+            std::lock_guard<std::mutex> lk(g_tuned_mu);
+            auto it = g_plane_tuned.find(tkey);
+            if (it != g_plane_tuned.end()) {
+                best_cap = it->second;
+                have = true;
             }
         }
+        bool tuned_now = false;
+        if (!have && g_tune_enabled && rounds >= 2) {
+            const int probe = std::min(rounds, 6);
+            const int caps[4] = {8, 16, 32, 64};
+            float best = 1e30f;
+            for (int c = 0; c < 4; ++c) {
+                ODP_TRY_CUDA(apply(caps[c]));
+                if (c == 0) ODP_TRY_CUDA(launch_rounds(probe));   // warm the caches once
+                for (int rep = 0; rep < 2; ++rep) {
+                    ODP_TRY_CUDA(cudaEventRecord(W.ev0, s));
+                    ODP_TRY_CUDA(launch_rounds(probe));
+                    ODP_TRY_CUDA(cudaEventRecord(W.ev1, s));
+                    ODP_TRY_CUDA(cudaEventSynchronize(W.ev1));
+                    float ms = 0.0f;
+                    cudaEventElapsedTime(&ms, W.ev0, W.ev1);
+                    if (ms < best) {
+                        best = ms;
+                        best_cap = caps[c];
+                    }
+                }
+            }
+            std::lock_guard<std::mutex> lk(g_tuned_mu);
+            g_plane_tuned[tkey] = best_cap;
+            tuned_now = true;
+        }
+        ODP_TRY_CUDA(apply(best_cap));
+
+        // the whole batch as one CUDA graph of its per-round launches,
+        // captured once per signature and replayed
+        PlaneGraphKey gkey;
+        gkey.kind = kind0;
+        gkey.order = space_order;
+        gkey.time_order = time_order;
+        gkey.n = n;
+        gkey.rounds = rounds;
+        gkey.chunk = chunk;
+        gkey.threads = threads;
+        gkey.smem = smem;
+        gkey.bg = W.bg;
+        gkey.ints = W.ints;
+        gkey.active = launch_ctas;
+        bool captured_now = false;
+        if (!W.graph_exec || !(W.graph_key == gkey)) {
+            if (W.graph_exec) cudaGraphExecDestroy(W.graph_exec);
+            W.graph_exec = nullptr;
+            // captured on a private stream (the caller's may be the legacy
+            // default stream, which cannot be captured), launched on the
+            // caller's; the uploads above are ordered before the launch by s
+            if (!W.cap_stream || W.cap_device != device) {
+                if (W.cap_stream) cudaStreamDestroy(W.cap_stream);
+                W.cap_stream = nullptr;
+                ODP_TRY_CUDA(cudaStreamCreateWithFlags(&W.cap_stream, cudaStreamNonBlocking));
+                W.cap_device = device;
+            }
+            cudaStream_t cs = W.cap_stream;
+            std::swap(s, cs);   // launch_rounds issues on s
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) e = launch_rounds(rounds);
+            cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+            std::swap(s, cs);
+            if (e == cudaSuccess && e2 != cudaSuccess) e = e2;
+            if (e != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                cudaGetLastError();
+                return fail(ODP_ECUDA, "capturing the batch's launches: %s", cudaGetErrorString(e));
+            }
+            e = cudaGraphInstantiate(&W.graph_exec, graph, 0);
+
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                W.graph_exec = nullptr;
+                return fail(ODP_ECUDA, "instantiating the batch graph: %s", cudaGetErrorString(e));
+            }
+            W.graph_key = gkey;
+            captured_now = true;
+        }
+        ODP_TRY_CUDA(cudaEventRecord(W.ev0, s));
+        ODP_TRY_CUDA(cudaGraphLaunch(W.graph_exec, s));
         ODP_TRY_CUDA(cudaEventRecord(W.ev1, s));
         k_batch_finish<<<(n + 127) / 128, 128, 0, s>>>(W.bg, n);
         ODP_TRY_CUDA(cudaGetLastError());
@@ -574,6 +744,10 @@ extern "C" odp_status odp_batch_solve(odp_grid *const *grids, int n, const doubl
             stats->rounds = rounds;
             stats->ctas_per_sm = 0;       // one launch per round, occupancy by the hardware
             stats->rows_per_thread = 0;   // plane pass
+            stats->plane_chunk = chunk;
+            stats->launches = int64_t(launch_ctas.size());
+            stats->graph = captured_now ? 1 : 2;
+            stats->tuned = tuned_now ? 1 : 0;
             double updates = 0.0, bytes = 0.0;
             for (int i = 0; i < n; ++i) {
                 const double nodes = double(grids[i]->total) * double(hb[size_t(i)].n_steps);
@@ -741,9 +915,14 @@ __global__ void k_noalloc_out(const BatchGrid *bg, float *out)
     }
 }
 
+constexpr int kNoallocMaxDevices = 64;
+
+// Per device: the array's device address (looked up on the first call) and
+// a lock held for the whole call, so calls on one device run one after
+// another and calls on different devices do not wait for each other.
 struct NoallocDevice {
-    std::mutex mu;
-    unsigned char *base[64] = {nullptr};
+    std::mutex mu[kNoallocMaxDevices];
+    unsigned char *base[kNoallocMaxDevices] = {nullptr};
 };
 
 static NoallocDevice &noalloc_devices()
@@ -794,7 +973,10 @@ extern "C" odp_status odp_solve_noalloc(int ndim, const int32_t *n, const double
         if (n[d] < (periodic[d] ? 1 : 2) || !(hi[d] > lo[d]) || !std::isfinite(lo[d]) || !std::isfinite(hi[d]))
             return fail(ODP_EINVAL, "odp_solve_noalloc: bad axis %d", d);
         total *= n[d];
+        if (total >= (int64_t(1) << 31)) return fail(ODP_EINVAL, "odp_solve_noalloc: grid has 2^31 nodes or more");
     }
+    if (total / n[ndim - 1] * ((n[ndim - 1] + 3) / 4 * 4) >= (int64_t(1) << 31))
+        return fail(ODP_EINVAL, "odp_solve_noalloc: padded grid storage has 2^31 floats or more");
     const int nl = n[ndim - 1], npad = (nl + 3) / 4 * 4;
     const int64_t rows = total / nl, total_pad = rows * npad;
     int64_t tab_len = 0;
@@ -808,14 +990,28 @@ extern "C" odp_status odp_solve_noalloc(int ndim, const int32_t *n, const double
         return fail(ODP_EINVAL, "odp_solve_noalloc: the grid needs %zu bytes of scratch, the fixed limit is %zu "
                                 "(about %lld nodes)", bytes, kNoallocBytes, (long long)(kNoallocBytes / 12));
 
-    int device = 0;
+    int device = 0, caller_device = 0;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // the call copies from host memory and synchronises its stream, so it
+    // cannot be recorded into a CUDA graph: checked before any other CUDA
+    // call, so that a refused call leaves the caller's capture intact
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    ODP_TRY_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(ODP_EINVAL, "odp_solve_noalloc: the stream is capturing; this call cannot be captured");
+    ODP_TRY_CUDA(cudaGetDevice(&caller_device));
     if (s) ODP_TRY_CUDA(cudaStreamGetDevice(s, &device));
-    else ODP_TRY_CUDA(cudaGetDevice(&device));
-    if (device < 0 || device >= 64) return fail(ODP_EINVAL, "odp_solve_noalloc: device %d out of range", device);
+    else device = caller_device;
+    if (device < 0 || device >= kNoallocMaxDevices)
+        return fail(ODP_EINVAL, "odp_solve_noalloc: device %d out of range", device);
+    // the caller's current device is restored on every return
+    struct DeviceRestore {
+        int dev;
+        ~DeviceRestore() { cudaSetDevice(dev); }
+    } restore{caller_device};
     ODP_TRY_CUDA(cudaSetDevice(device));
     NoallocDevice &ND = noalloc_devices();
-    std::lock_guard<std::mutex> lock(ND.mu);
+    std::lock_guard<std::mutex> lock(ND.mu[device]);
     if (!ND.base[device]) {
         // set-up, once per device, with that device current: the array's
         // device address (its host-side name is not a device address)

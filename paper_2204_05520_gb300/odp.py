@@ -56,7 +56,9 @@ class TtrStats(ctypes.Structure):
 class BatchStats(ctypes.Structure):
     _fields_ = [("device_ms", ctypes.c_double), ("rounds", ctypes.c_int64),
                 ("ctas_per_sm", ctypes.c_int32), ("rows_per_thread", ctypes.c_int32),
-                ("point_updates", ctypes.c_double), ("bytes", ctypes.c_double)]
+                ("point_updates", ctypes.c_double), ("bytes", ctypes.c_double),
+                ("plane_chunk", ctypes.c_int32), ("graph", ctypes.c_int32), ("launches", ctypes.c_int64),
+                ("tuned", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -332,7 +334,16 @@ def batch_solve(grids, horizons, set_kind="brt", space_order=1, time_order=1, cf
 def solve_noalloc(problem, l, out, stream=None):
     """Solve ``problem`` over [0, T] without allocating device memory: ``l``
     and ``out`` are the caller's device tensors (float32, problem.n), all
-    other state lives in the library's fixed device array."""
+    other state lives in the library's fixed device array.  The entry point
+    takes a plain solve over tau = {0, T}: a problem with an obstacle,
+    per-node dissipation or intermediate tau points is refused (ValueError),
+    since its answer would differ from the grid object's solve."""
+    if getattr(problem, "obstacle", None) is not None:
+        raise ValueError("solve_noalloc: reach-avoid (an obstacle) is not supported")
+    if getattr(problem, "dissipation", "global") != "global":
+        raise ValueError("solve_noalloc: only grid-wide dissipation is supported")
+    if len(problem.tau) != 2 or float(problem.tau[0]) != 0.0:
+        raise ValueError("solve_noalloc: the schedule must be tau = (0, T)")
     nd = problem.ndim
     n_pts = problem.points
     lp, ldev = _buffer(l, n_pts, writable=False)

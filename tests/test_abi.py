@@ -89,3 +89,21 @@ def test_launch_geometry_covers_the_grid(lib, n):
         assert g["ctas"] == pencils * nb * -(-ns // g["chunk"])
         assert g["cta_threads"] == -(-rb * segs // 32) * 32 and g["cta_threads"] <= 512
         assert 0 < g["smem_r1"] < g["smem_r2"] <= 48 * 1024
+
+
+def test_noalloc_binding_refuses_what_the_entry_point_does_not_solve():
+    # reach-avoid, per-node dissipation and intermediate tau points would give
+    # a different answer than the grid object's solve: refused before any
+    # library call (no GPU needed)
+    import dataclasses
+
+    from paper_2204_05520_gb300 import inputs, odp
+
+    p = inputs.dubins3d(n=(9, 9, 8), horizon=0.5)
+    bad = [inputs.reach_avoid(p, inputs.dubins_obstacle()),
+           dataclasses.replace(p, dissipation="local"),
+           dataclasses.replace(p, tau=(0.0, 0.2, 0.5)),
+           dataclasses.replace(p, tau=(0.1, 0.5))]
+    for q in bad:
+        with pytest.raises(ValueError):
+            odp.solve_noalloc(q, None, None)

@@ -150,3 +150,20 @@ def test_batch_workload_sample_full_sizes():
     order = sorted(range(len(problems)), key=lambda i: problems[i].points)
     for i in sorted({order[0], order[-1], order[len(order) // 3], order[2 * len(order) // 3]}):
         parity.check_whole_solve(problems[i], outs[i], steps[i], name="batched %s" % problems[i].name)
+
+
+def test_batch_graph_is_captured_once_and_replayed():
+    # the plane-path batch runs as one CUDA graph of its per-round launches:
+    # captured by the first call of a batch signature (which also autotunes
+    # the stream-chunk cap), replayed by the next; the values are the same
+    # both times and equal to the solo solves
+    problems = small_dubins_batch(10, seed=11)
+    outs1, st1, steps1 = batched(problems)
+    outs2, st2, steps2 = batched(problems)
+    assert st1["plane_chunk"] in (8, 16, 32, 64) and st2["plane_chunk"] == st1["plane_chunk"]
+    assert st1["graph"] == 1 and st2["graph"] == 2
+    assert st2["tuned"] == 0
+    assert st1["launches"] == st2["launches"] == max(steps1)
+    for p, a, b in zip(problems, outs1, outs2):
+        assert np.array_equal(a, b)
+        assert np.array_equal(a, solo(p)[0])

@@ -256,6 +256,36 @@ def test_alpha_rel6d_closed_form_and_theta_rule():
     assert a[2] == pytest.approx(a_th.max(), abs=1e-15)
 
 
+def test_alpha_rel6d_with_unequal_input_bounds():
+    # bounds (a_p, alpha_p, a_e, w_e) = (0.7, 0.4, 0.3, 1.2), all different, so
+    # each input must drive its own axis (reading R12):
+    #   v_p' = a_p -> alpha = 0.7;  w_p' = alpha_p -> 0.4;  v_e' = a_e -> 0.3;
+    #   th' = w_e - w_p -> with both signs of p_th somewhere, 1.2 + max|w_p| = 2.2;
+    #   x' = -v_p + v_e cos th + w_p y and y' = v_e sin th - w_p x carry no
+    #   input: 1.5 + 1.5 + 4 = 7 and 1.5 + 4 = 5.5 as with unit bounds.
+    # Swapping the evader's two inputs would give 1.2 on v_e and 1.3 on th.
+    p = inputs.rel6d(n=(24, 6, 24, 3, 3, 3), bounds=(0.7, 0.4, 0.3, 1.2))
+    p.lo = (-4.0, -4.0, -math.pi, 0.5, -1.0, 0.5)
+    t = oracle.terms(p, inputs.random_field(p.n, seed=12), order=1)
+    a = t["alpha"]
+    assert a[0] == pytest.approx(7.0, abs=1e-12)
+    assert a[1] == pytest.approx(5.5, abs=1e-12)
+    assert a[2] == pytest.approx(2.2, abs=1e-12)
+    assert a[3] == pytest.approx(0.7, abs=1e-15)
+    assert a[4] == pytest.approx(0.4, abs=1e-15)
+    assert a[5] == pytest.approx(0.3, abs=1e-15)
+    # the dynamics themselves: one state, each input alone
+    z = np.array([[1.0, -2.0, 0.3, 0.8, 0.5, 1.1]])
+    u = np.array([[0.7, 0.0]])
+    d = np.array([[0.0, 1.2]])
+    f = oracle.eval_dynamics_batch("rel6d", p.params, z, u, d)[0]
+    assert f[3] == pytest.approx(0.7) and f[4] == 0.0 and f[5] == 0.0
+    assert f[2] == pytest.approx(1.2 - 0.5)
+    f = oracle.eval_dynamics_batch("rel6d", p.params, z, np.array([[0.0, 0.4]]), np.array([[0.3, 0.0]]))[0]
+    assert f[4] == pytest.approx(0.4) and f[5] == pytest.approx(0.3) and f[3] == 0.0
+    assert f[2] == pytest.approx(-0.5)
+
+
 # ---------------------------------------------------------------------------
 # Lax-Friedrichs sign, upwinding, CFL step and TVD-RK2 (Algorithm 1,
 # Section 3.1.3): exact transports

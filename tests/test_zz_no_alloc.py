@@ -60,6 +60,53 @@ def test_two_calls_in_a_row_match_the_regular_entry_point():
         assert np.abs(got - want).max() <= REL_TOL * float(l.max() - l.min())
 
 
+def test_a_call_allocates_no_device_memory():
+    # after one warm-up call, a second call changes neither the device's free
+    # memory nor the memory torch's caching allocator holds
+    import torch
+
+    p = inputs.dubins3d(n=(31, 31, 24), horizon=0.5)
+    l = torch.from_numpy(p.target_values()).cuda()
+    out = torch.empty_like(l)
+    odp.solve_noalloc(p, l, out)
+    torch.cuda.synchronize()
+    free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+    odp.solve_noalloc(p, l, out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_reserved() == reserved0
+    assert np.isfinite(out.cpu().numpy()).all()
+
+
+def test_the_callers_current_device_is_kept():
+    import torch
+
+    p = inputs.dubins3d(n=(21, 21, 16), horizon=0.3)
+    l = torch.from_numpy(p.target_values()).cuda()
+    before = torch.cuda.current_device()
+    odp.solve_noalloc(p, l, torch.empty_like(l))
+    assert torch.cuda.current_device() == before
+
+
+def test_a_capturing_stream_is_refused():
+    import torch
+
+    p = inputs.dubins3d(n=(21, 21, 16), horizon=0.3)
+    l = torch.from_numpy(p.target_values()).cuda()
+    out = torch.empty_like(l)
+    odp.solve_noalloc(p, l, out)       # first call on this device outside any capture
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    refused = None
+    with torch.cuda.graph(g, stream=s):
+        out.add_(0.0)                  # the captured graph is not empty
+        try:
+            odp.solve_noalloc(p, l, out, stream=s)
+        except odp.OdpError as e:
+            refused = e
+    assert refused is not None and refused.code == odp.EINVAL
+
+
 def test_grids_beyond_the_fixed_array_are_refused():
     import torch
 
