@@ -79,7 +79,8 @@ typedef struct odp_grid odp_grid;
  *                      y' = v sin th - a x, th' = b - a; control a (evader turn,
  *                      |a| <= A), disturbance b (pursuer turn, |b| <= B);
  *                      params (v, A, B); every alpha component is reduced per
- *                      stage; no per-node dissipation
+ *                      stage (interval bounds of the coupled switching
+ *                      function y p_x - x p_y - p_th over each node's box)
  * Angles (th) must lie on a periodic axis. */
 typedef enum {
     ODP_DYN_SINGLE_INT = 0,
@@ -184,8 +185,11 @@ odp_status odp_set_obstacle_schedule(odp_grid *g, const float *g_seq, int n_sets
  * per_node = 0 (default) uses the grid alpha, the largest rate over the grid
  * per component (Section 2.1); per_node = 1 uses each node's own alpha_i, the
  * largest rate over the input extremes its derivative box admits (Algorithm
- * 1's second loop).  Per-node solves run the generic stage kernels; grids
- * with per_node = 1 are refused by odp_batch_solve.  Errors: ODP_EINVAL. */
+ * 1's second loop).  Per-node solves run the generic stage kernels; for the
+ * capture model, whose bounds come from interval arithmetic over the box,
+ * the per-stage alpha pass writes each node's coefficients to a buffer of 12
+ * bytes per node that the solve allocates on first use.  Grids with
+ * per_node = 1 are refused by odp_batch_solve.  Errors: ODP_EINVAL. */
 odp_status odp_set_dissipation(odp_grid *g, int per_node);
 
 /* Limit the number of full time steps of one solve (default 10,000,000).  A

@@ -153,8 +153,9 @@ ODP_HD void axis_pair(float2 fm2, float2 fm1, float2 f0, float2 fp1, float2 fp2,
 // window between the four nodes (the same float32 operations as diffs()).
 template <int ORDER>
 ODP_HD void axis_last(const float *w, const float *cA, float cS, float cD, float *L, bool has_a, bool has_s,
-                      float *Pout = nullptr)
+                      float *Pout = nullptr, const float *cDn = nullptr)
 {
+    // cDn (optional): each node's own dissipation coefficient instead of cD
     float e[7];
 #pragma unroll
     for (int j = 0; j < 7; ++j) e[j] = w[j + 1] - w[j];
@@ -176,7 +177,7 @@ ODP_HD void axis_last(const float *w, const float *cA, float cS, float cD, float
         float acc = L[k];
         if (has_a) acc = fmaf(cA[k], P, acc);
         if (has_s) acc = fmaf(cS, fabsf(P), acc);
-        L[k] = fmaf(cD, M, acc);
+        L[k] = fmaf(cDn ? cDn[k] : cD, M, acc);
     }
 }
 

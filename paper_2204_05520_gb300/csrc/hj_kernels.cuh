@@ -190,15 +190,18 @@ struct StageArgs {
 template <int ORDER>
 ODP_HD void segment_axis_P(const float4 &m2, const float4 &m1, const float4 &c, const float4 &p1, const float4 &p2,
                            const float *cA, float cS, float cD, float2 &L01, float2 &L23, bool has_a, bool has_s,
-                           float2 &P01, float2 &P23)
+                           float2 &P01, float2 &P23, const float4 *cDn = nullptr)
 {
+    // cDn (optional): each node's own dissipation coefficient instead of cD
     float2 dm, dp;
     pair_diffs<ORDER>(make_float2(m2.x, m2.y), make_float2(m1.x, m1.y), make_float2(c.x, c.y),
                       make_float2(p1.x, p1.y), make_float2(p2.x, p2.y), dm, dp);
-    pair_terms(dm, dp, make_float2(cA[0], cA[1]), cS, f2splat(cD), L01, has_a, has_s, &P01);
+    pair_terms(dm, dp, make_float2(cA[0], cA[1]), cS, cDn ? make_float2(cDn->x, cDn->y) : f2splat(cD), L01, has_a,
+               has_s, &P01);
     pair_diffs<ORDER>(make_float2(m2.z, m2.w), make_float2(m1.z, m1.w), make_float2(c.z, c.w),
                       make_float2(p1.z, p1.w), make_float2(p2.z, p2.w), dm, dp);
-    pair_terms(dm, dp, make_float2(cA[2], cA[3]), cS, f2splat(cD), L23, has_a, has_s, &P23);
+    pair_terms(dm, dp, make_float2(cA[2], cA[3]), cS, cDn ? make_float2(cDn->z, cDn->w) : f2splat(cD), L23, has_a,
+               has_s, &P23);
 }
 
 // The capture model's evader term (Section 4.2): the evader turn a enters
@@ -454,6 +457,14 @@ ODP_HD bool stage_tile(const GridDesc &g, const DynDesc &dy, const StageArgs &A,
         float2 L01 = make_float2(0.0f, 0.0f), L23 = make_float2(0.0f, 0.0f);
 
         float2 Pc[2][2];   // capture model: unscaled sums of axes x, y (two node pairs)
+        // capture model with per-node dissipation: each node's own
+        // coefficients, written by the stage's alpha pass
+        float4 cdn4[3] = {};
+        const bool cap_local = DYN == DYN_CAPTURE && dy.local_diss && g.cdn != nullptr;
+        if (cap_local) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) cdn4[d] = ldg4(g.cdn + d * g.cdn_stride + base);
+        }
         // outer axes: neighbour rows one by one
 #pragma unroll
         for (int d = 0; d < ND - 2; ++d) {
@@ -467,7 +478,7 @@ ODP_HD bool stage_tile(const GridDesc &g, const DynDesc &dy, const StageArgs &A,
             }
             if (DYN == DYN_CAPTURE)
                 segment_axis_P<ORDER>(m2, m1, c4, p1, p2, cA[d], cS[d], A.cD[d], L01, L23, has_drift<DYN, ND>(d),
-                                      has_bound<DYN, ND>(d), Pc[0][0], Pc[0][1]);
+                                      has_bound<DYN, ND>(d), Pc[0][0], Pc[0][1], cap_local ? &cdn4[d < 3 ? d : 2] : nullptr);
             else if (DYN == DYN_REL6D && d == 2 && dy.local_diss)
                 segment_axis_rel6d_theta<ORDER>(m2, m1, c4, p1, p2, cA[d], cS[d], dy, ldgf(g.coord[4] + idx[4]),
                                                 0.5f * g.inv_dz[2], L01, L23);
@@ -484,7 +495,7 @@ ODP_HD bool stage_tile(const GridDesc &g, const DynDesc &dy, const StageArgs &A,
             const float4 p1 = col[i + O + 1], p2 = col[i + O + 2 < NC ? i + O + 2 : NC - 1];
             if (DYN == DYN_CAPTURE)
                 segment_axis_P<ORDER>(m2, m1, c4, p1, p2, cA[d], cS[d], A.cD[d], L01, L23, has_drift<DYN, ND>(d),
-                                      has_bound<DYN, ND>(d), Pc[1][0], Pc[1][1]);
+                                      has_bound<DYN, ND>(d), Pc[1][0], Pc[1][1], cap_local ? &cdn4[d < 3 ? d : 2] : nullptr);
             else
                 segment_axis<ORDER>(m2, m1, c4, p1, p2, cA[d], cS[d], A.cD[d], L01, L23, has_drift<DYN, ND>(d),
                                     has_bound<DYN, ND>(d),
@@ -513,8 +524,10 @@ ODP_HD bool stage_tile(const GridDesc &g, const DynDesc &dy, const StageArgs &A,
         }
         float L[4] = {L01.x, L01.y, L23.x, L23.y};
         float Pth[4];
+        constexpr int cl = ND - 1 < 2 ? ND - 1 : 2;
+        const float cdl[4] = {cdn4[cl].x, cdn4[cl].y, cdn4[cl].z, cdn4[cl].w};
         axis_last<ORDER>(w, cA[ND - 1], cS[ND - 1], A.cD[ND - 1], L, has_drift<DYN, ND>(ND - 1), has_bound<DYN, ND>(ND - 1),
-                         DYN == DYN_CAPTURE ? Pth : nullptr);
+                         DYN == DYN_CAPTURE ? Pth : nullptr, cap_local ? cdl : nullptr);
         if (DYN == DYN_CAPTURE) {
             const float Px[4] = {Pc[0][0].x, Pc[0][0].y, Pc[0][1].x, Pc[0][1].y};
             const float Py[4] = {Pc[1][0].x, Pc[1][0].y, Pc[1][1].x, Pc[1][1].y};
@@ -733,10 +746,17 @@ __global__ void __launch_bounds__(256) k_alpha_capture(GridDesc g, DynDesc dy, S
             else if (hi[2] < 0.0f) bs[0] = -b_up;
             else { bs[0] = -B; bs[1] = B; nb = 2; }
             const float cth = ldgf(g.cos_tab + s0 + k), sth = ldgf(g.sin_tab + s0 + k);
+            float aloc[3] = {0.0f, 0.0f, 0.0f};
             for (int ia = 0; ia < na; ++ia) {
-                amax[0] = fmaxf(amax[0], fabsf(-v + v * cth + as[ia] * y));
-                amax[1] = fmaxf(amax[1], fabsf(v * sth - as[ia] * x));
-                for (int ib = 0; ib < nb; ++ib) amax[2] = fmaxf(amax[2], fabsf(bs[ib] - as[ia]));
+                aloc[0] = fmaxf(aloc[0], fabsf(-v + v * cth + as[ia] * y));
+                aloc[1] = fmaxf(aloc[1], fabsf(v * sth - as[ia] * x));
+                for (int ib = 0; ib < nb; ++ib) aloc[2] = fmaxf(aloc[2], fabsf(bs[ib] - as[ia]));
+            }
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                amax[d] = fmaxf(amax[d], aloc[d]);
+                // per-node dissipation (Algorithm 1's second loop): this node's own bound
+                if (g.cdn) g.cdn[d * g.cdn_stride + base + k] = 0.5f * aloc[d] * g.inv_dz[d];
             }
         }
     }

@@ -366,10 +366,18 @@ __device__ __forceinline__ void plane_pass(const GridDesc &g, const DynDesc &dy,
                 }
                 // stream axis from the register window
                 float2 Pc[2][2];   // capture model: unscaled sums of axes x (stream), y (row)
+                // capture model with per-node dissipation: each node's own
+                // coefficients, written by the stage's alpha pass
+                float4 cdn4[3] = {};
+                const bool cap_local = DYN == DYN_CAPTURE && local && g.cdn != nullptr;
+                if (cap_local) {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) cdn4[d] = ldg4(g.cdn + d * g.cdn_stride + gi);
+                }
                 if (DYN == DYN_CAPTURE)
                     segment_axis_P<ORDER>(w[u % Q], w[(u + O - 1) % Q], c4, w[(u + O + 1) % Q], w[(u + Q - 1) % Q],
                                           cA[sa], cS[sa], cD[sa], L01, L23, has_drift<DYN, ND>(sa),
-                                          has_bound<DYN, ND>(sa), Pc[0][0], Pc[0][1]);
+                                          has_bound<DYN, ND>(sa), Pc[0][0], Pc[0][1], cap_local ? &cdn4[0] : nullptr);
                 else
                     segment_axis<ORDER>(w[u % Q], w[(u + O - 1) % Q], c4, w[(u + O + 1) % Q], w[(u + Q - 1) % Q],
                                         cA[sa], cS[sa], cD[sa], L01, L23, has_drift<DYN, ND>(sa),
@@ -398,7 +406,7 @@ __device__ __forceinline__ void plane_pass(const GridDesc &g, const DynDesc &dy,
                     if (DYN == DYN_CAPTURE)
                         segment_axis_P<ORDER>(m2, m1, c4, p1, p2, cA[ND - 2], cS[ND - 2], cD[ND - 2], L01, L23,
                                               has_drift<DYN, ND>(ND - 2), has_bound<DYN, ND>(ND - 2), Pc[1][0],
-                                              Pc[1][1]);
+                                              Pc[1][1], cap_local ? &cdn4[1] : nullptr);
                     else
                         segment_axis<ORDER>(m2, m1, c4, p1, p2, cA[ND - 2], cS[ND - 2], cD[ND - 2], L01, L23,
                                             has_drift<DYN, ND>(ND - 2), has_bound<DYN, ND>(ND - 2),
@@ -422,8 +430,10 @@ __device__ __forceinline__ void plane_pass(const GridDesc &g, const DynDesc &dy,
                             if (s0 + k - 2 >= nl) v[k] = C[k - 2];
                     }
                     float Pth[4];
+                    const float cdl[4] = {cdn4[2].x, cdn4[2].y, cdn4[2].z, cdn4[2].w};
                     axis_last<ORDER>(v, cA[ND - 1], cS[ND - 1], cD[ND - 1], L, has_drift<DYN, ND>(ND - 1),
-                                     has_bound<DYN, ND>(ND - 1), DYN == DYN_CAPTURE ? Pth : nullptr);
+                                     has_bound<DYN, ND>(ND - 1), DYN == DYN_CAPTURE ? Pth : nullptr,
+                                     cap_local ? cdl : nullptr);
                     if (DYN == DYN_CAPTURE) {
                         const float Px[4] = {Pc[0][0].x, Pc[0][0].y, Pc[0][1].x, Pc[0][1].y};
                         const float Py[4] = {Pc[1][0].x, Pc[1][0].y, Pc[1][1].x, Pc[1][1].y};

@@ -322,6 +322,7 @@ static void release(odp_grid *g)
     cudaFree(g->phi_b);
     cudaFree(g->l);
     cudaFree(g->obst);
+    cudaFree(g->cdn);
     cudaFree(g->l_seq);
     cudaFree(g->g_seq);
     cudaFree(g->tables);
@@ -534,8 +535,6 @@ extern "C" odp_status odp_set_dynamics(odp_grid *g, odp_dyn kind, const double *
     }
     if (angle >= 0 && !g->periodic[angle])
         return fail(ODP_EINVAL, "axis %d holds an angle and must be periodic", angle);
-    if (kind == ODP_DYN_DUBINS_CAPTURE && g->local_diss)
-        return fail(ODP_EINVAL, "per-node dissipation is not available for the capture model");
     DynDesc dy{};
     dy.kind = int(kind);
     dy.umode = int(u_mode);
@@ -694,8 +693,6 @@ extern "C" odp_status odp_set_dissipation(odp_grid *g, int per_node)
 {
     if (!g) return fail(ODP_EINVAL, "grid is NULL");
     if (per_node != 0 && per_node != 1) return fail(ODP_EINVAL, "per_node must be 0 or 1");
-    if (per_node && g->has_dyn && g->dyn.kind == DYN_CAPTURE)
-        return fail(ODP_EINVAL, "per-node dissipation is not available for the capture model");
     if (g->local_diss != per_node) {
         g->local_diss = per_node;
         g->dyn.local_diss = per_node;
@@ -1014,6 +1011,26 @@ extern "C" odp_status odp_solve_hjb(odp_grid *g, const double *tau, int n_tau, o
     g->brt = (set == ODP_BRT) ? 1 : 0;
     g->keep = keep_snapshots ? 1 : 0;
     g->n_tau = n_tau;
+    // per-node dissipation of the capture model: the alpha pass writes each
+    // node's coefficients into a buffer the stage pass reads (allocated on
+    // first use, 3 arrays of total_pad floats)
+    float *cdn = nullptr;
+    if (g->dyn.kind == DYN_CAPTURE && g->local_diss) {
+        if (!g->cdn) {
+            const size_t bytes = 3 * size_t(g->total_pad) * sizeof(float);
+            if (cudaMalloc(&g->cdn, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                g->cdn = nullptr;
+                return fail(ODP_ENOMEM, "per-node dissipation buffer of %zu bytes", bytes);
+            }
+        }
+        cdn = g->cdn;
+    }
+    if (g->desc.cdn != cdn) {
+        g->desc.cdn = cdn;
+        g->desc.cdn_stride = int(g->total_pad);
+        g->dyn_version += 1;   // the captured loop holds the old descriptor
+    }
     GraphKey key;
     key.order = space_order;
     key.time_order = time_order;
@@ -1118,6 +1135,9 @@ extern "C" odp_status odp_solve_status(odp_grid *g, odp_solve_stats *stats)
         if (g->brt) b += 4.0;
         if (g->has_obst) b += 4.0;
         if (dynamic_alpha_mask(g)) b += 4.0 * g->time_order;
+        // capture model with per-node dissipation: each stage writes and
+        // reads three coefficients per node
+        if (g->desc.cdn) b += 24.0 * g->time_order;
         stats->bytes = b * double(g->total) * double(h.steps);
         // the once-per-solve alpha reduction (and first k_dt) included
         stats->launches = g->launches_per_step * h.steps + (dynamic_alpha_mask(g) ? 1 : 2);

@@ -154,6 +154,11 @@ struct GridDesc {
     const float *coord[ODP_MAXD];  // node coordinates of each axis (device)
     const float *cos_tab;        // cos / sin of the angle axis nodes (device)
     const float *sin_tab;
+    // per-node dissipation of the capture model: each node's coefficient
+    // alpha_d / (2 h_d) per axis d, written by its alpha pass every stage
+    // (3 arrays of cdn_stride floats at the nodes' storage offsets), or nullptr
+    float *cdn;
+    int cdn_stride;
     // geometry of the row-blocked stage pass: a thread owns one four-node
     // segment of the last axis in each of R consecutive rows of axis ndim-2
     // (a "row group"); threads are numbered segment fastest, then row group,

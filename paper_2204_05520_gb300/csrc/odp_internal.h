@@ -55,6 +55,7 @@ struct odp_grid {
 
     float *phi_a = nullptr, *phi_b = nullptr, *l = nullptr;
     float *obst = nullptr;            // reach-avoid obstacle g (allocated on first use)
+    float *cdn = nullptr;             // per-node dissipation coefficients of the capture model
     bool has_obst = false;
     int local_diss = 0;               // per-node dissipation (odp_set_dissipation)
     float *tables = nullptr;          // all node-coordinate and trig tables

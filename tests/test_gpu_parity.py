@@ -540,19 +540,32 @@ def test_capture_model_matches_oracle(problem):
     check(problem)
 
 
-def test_capture_model_refuses_per_node_dissipation():
+CAPTURE_LOCAL_CASES = [
+    per_node(inputs.dubins_capture()),                                    # 40^3, the paper's grid, T = 1.5
+    per_node(inputs.dubins_capture(n=(21, 23, 18), space_order=2, time_order=2, horizon=0.5)),
+    per_node(inputs.dubins_capture(n=(25, 25, 20), u_mode="min", d_mode="max", set_kind="brs", horizon=0.5)),
+    per_node(inputs.dubins_capture(n=(13, 3, 10), horizon=0.4)),          # 3 rows: the row-blocked pass
+]
+
+
+@pytest.mark.parametrize("problem", CAPTURE_LOCAL_CASES, ids=lambda p: "%s_o%d%d_%s_local" % (
+    p.name, p.space_order, p.time_order, p.u_mode))
+def test_capture_model_per_node_dissipation_matches_oracle(problem):
+    # Algorithm 1's second loop on the coupled-switching model of Section
+    # 4.2: each node's alpha_i from interval bounds of y p_x - x p_y - p_th
+    # over its derivative box (reading R20).  The per-node bound switches
+    # with the signs of those intervals, a discontinuity like ENO2's, so the
+    # run is compared step by step (one-step segments) at the 1e-4 bar.
+    check_parity_resync(problem)
+
+
+def test_capture_model_per_node_dissipation_is_refused_by_the_batch():
     p = inputs.dubins_capture(n=(9, 9, 8))
-    with odp.Grid.for_problem(p) as g:
-        with pytest.raises(odp.OdpError) as e:
-            odp.set_dissipation(g.handle, True)
-        assert e.value.code == odp.EINVAL
+    with odp.Grid.for_problem(per_node(p)) as g:
         g.set_target(p.target_values())
         with pytest.raises(odp.OdpError) as e:
             odp.batch_solve([g], [0.5])
         assert e.value.code == odp.EINVAL
-    with pytest.raises(odp.OdpError) as e:
-        odp.Grid.for_problem(dataclasses.replace(p, dissipation="local"))
-    assert e.value.code == odp.EINVAL
 
 
 # ---------------------------------------------------------------------------
