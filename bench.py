@@ -64,6 +64,8 @@ def parse_args():
                     help="headline workload only (skip the other configurations)")
     ap.add_argument("--dissipation", choices=("global", "local"), default="global",
                     help="Lax-Friedrichs dissipation: grid alpha or each node's own alpha")
+    ap.add_argument("--stage-pass", choices=("auto", "plane", "bulk"), default="auto",
+                    help="stage-pass kernel of the single solve (auto: the faster one for the model)")
     ap.add_argument("--host-loop", action="store_true",
                     help="step the time loop from the host (same kernels; for profilers)")
     return ap.parse_args()
@@ -84,8 +86,8 @@ def hbm_peak():
 
 # sources that define the stage pass and the model instantiations it is
 # profiled on: a DRAM-traffic record holds only while these are unchanged
-STAGE_SOURCES = ("odp_common.cuh", "hj_device.cuh", "hj_kernels.cuh", "hj_plane.cuh", "kern_dubins.cu",
-                 "kern_rel6d.cu")
+STAGE_SOURCES = ("odp_common.cuh", "hj_device.cuh", "hj_kernels.cuh", "hj_plane.cuh", "hj_bulk.cuh",
+                 "kern_dubins.cu", "kern_rel6d.cu")
 
 
 def kernel_sources_sha() -> str:
@@ -465,6 +467,7 @@ def run_ours(args):
     grid = odp.Grid.for_problem(problem, stream=stream)
     if args.host_loop:
         odp.set_loop_mode(grid.handle, True)
+    odp.set_stage_pass(grid.handle, {"auto": 0, "plane": 1, "bulk": 2}[args.stage_pass])
     grid.set_target(l_dev)
 
     with torch.cuda.stream(stream):
@@ -509,7 +512,9 @@ def run_ours(args):
                 "frac": achieved / peak, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                 "traffic": dram_traffic(problem.name),
                 "kernel": "%s (whole time loop timed)" % (
-                    "k_stage_bulk" if problem.dynamics == "rel6d" else "k_stage_plane"), "peak_source": peak_kind,
+                    "k_stage_bulk" if (args.stage_pass == "bulk" or (args.stage_pass == "auto" and
+                                                                       problem.dynamics == "rel6d"))
+                    else "k_stage_plane"), "peak_source": peak_kind,
                 "alg_bytes_per_launch": bytes_per_solve / stage_launches,
                 "avg_launch_ms": ms_per_step / stage_launches,
                 "stage_ms_isolated": stage_ms}
@@ -583,7 +588,8 @@ def run_ours(args):
             "alg_bytes_per_solve": bytes_per_solve,
             "solves_per_s": world * 1000.0 / ms_per_step,
             "roofline_alu": alu,
-            "stage_pass": "plane-streaming" if problem.dynamics != "rel6d" else "bulk-staged",
+            "stage_pass": {"plane": "plane-streaming", "bulk": "bulk-staged"}.get(
+                args.stage_pass, "plane-streaming" if problem.dynamics != "rel6d" else "bulk-staged"),
             "extra_workloads": extras,
         }
         print(json.dumps(line), flush=True)
@@ -615,6 +621,7 @@ def run_ttr(args):
     grid = odp.Grid.for_problem(problem, stream=stream)
     if args.host_loop:
         odp.set_loop_mode(grid.handle, True)
+    odp.set_stage_pass(grid.handle, {"auto": 0, "plane": 1, "bulk": 2}[args.stage_pass])
     grid.set_target(l_dev)
     st = None
     for _ in range(max(1, args.warmup)):

@@ -341,20 +341,29 @@ __global__ void __launch_bounds__(512) __maxnreg__((bulk_max_regs<ND, ORDER, DYN
     float *dst = (stage == 2) ? st->cur : st->nxt;
     const float *prev = st->cur;
 
-    // work item: chunk fastest, then band, then outer pencil (C order)
+    // work item: chunk fastest, then band, then outer pencil.  Outer pencils
+    // are numbered block by block (the plane pass's blocks of up to 8
+    // indices per outer axis), so CTAs that run together stage each other's
+    // pencils as neighbour tiles while they are still in L2.
     const uint32_t item = blockIdx.x;
     const uint32_t q1 = fast_div(item, bk.div_nchunks);
     const int chunk = int(item - q1 * uint32_t(bk.nchunks));
-    uint32_t outer = fast_div(q1, bk.div_nbands);
+    const uint32_t outer = fast_div(q1, bk.div_nbands);
     const int band = int(q1 - outer * uint32_t(bk.nbands));
     int idx[ND];
     int pencil = 0;
+    if (NOUT > 0) {
+        const PlaneGeom &pg = g.pg;
+        const uint32_t blk0 = fast_div(outer, pg.div_bvol);
+        uint32_t wi = outer - blk0 * uint32_t(pg.bvol), blk = blk0;
 #pragma unroll
-    for (int d = NOUT - 1; d >= 0; --d) {
-        const uint32_t qd = fast_div(outer, g.div[d]);
-        idx[d] = int(outer - qd * uint32_t(g.n[d]));
-        outer = qd;
-        pencil += idx[d] * g.stride[d];
+        for (int d = NOUT - 1; d >= 0; --d) {
+            const uint32_t wq = fast_div(wi, pg.div_bdim[d]), bq = fast_div(blk, pg.div_nblk[d]);
+            idx[d] = int(blk - bq * uint32_t(pg.nblk[d])) * pg.bdim[d] + int(wi - wq * uint32_t(pg.bdim[d]));
+            wi = wq;
+            blk = bq;
+            pencil += idx[d] * g.stride[d];
+        }
     }
     const int s_begin = chunk * bk.chunk;
     const int s_end = min(ns, s_begin + bk.chunk);
@@ -526,9 +535,21 @@ __global__ void __launch_bounds__(512) __maxnreg__((bulk_max_regs<ND, ORDER, DYN
         const int gi = base + s * plane;
         float4 lx = make_float4(0.f, 0.f, 0.f, 0.f), px = lx, gx = lx;
         if (active && ok) {
-            if (use_l) lx = ldg4(l + gi);
-            if (use_g) gx = ldg4(gob + gi);
-            if (stage == 2) px = *reinterpret_cast<const float4 *>(prev + gi);
+#ifndef ODP_BULK_STREAMING
+#define ODP_BULK_STREAMING 1
+#endif
+            // l, the obstacle and phi^n are read once and the output written
+            // once: streaming accesses (evict first), so L2 keeps the tiles
+            // that neighbouring CTAs stage again
+            if (ODP_BULK_STREAMING) {
+                if (use_l) lx = __ldcs(reinterpret_cast<const float4 *>(l + gi));
+                if (use_g) gx = __ldcs(reinterpret_cast<const float4 *>(gob + gi));
+                if (stage == 2) px = __ldcs(reinterpret_cast<const float4 *>(prev + gi));
+            } else {
+                if (use_l) lx = ldg4(l + gi);
+                if (use_g) gx = ldg4(gob + gi);
+                if (stage == 2) px = *reinterpret_cast<const float4 *>(prev + gi);
+            }
             const float4 c4 = *reinterpret_cast<const float4 *>(C);
             // stream-axis differences of plane s (ghost planes past a
             // non-periodic end from the carried differences)
@@ -626,7 +647,10 @@ __global__ void __launch_bounds__(512) __maxnreg__((bulk_max_regs<ND, ORDER, DYN
                                  has_bound<DYN, ND>(ND - 1));
             }
             const float4 out = update_nodes(dt, stage, use_l, c4, L, px, lx, use_g, gx, 4, fin);
-            *reinterpret_cast<float4 *>(dst + gi) = out;
+            if (ODP_BULK_STREAMING)
+                __stcs(reinterpret_cast<float4 *>(dst + gi), out);
+            else
+                *reinterpret_cast<float4 *>(dst + gi) = out;
         }
         release(&sm.empty_c[r_slot]);
         advance(r_slot, r_par, rc);

@@ -253,7 +253,8 @@ void odp::bulk_geometry(GridDesc &D, int sms)
     BulkGeom &bk = D.bk;
     bk = BulkGeom{};
     const int nd = D.ndim;
-    if (nd < 3 || D.n[nd - 1] % 4 != 0) return;
+    // the pass numbers its outer pencils with the plane pass's blocks
+    if (nd < 3 || D.n[nd - 1] % 4 != 0 || !D.pg.use) return;
     const int nr = D.nr, segs = D.segs, ns = D.n[nd - 3];
     if (nr < 4 || ns < 4 || segs > 128) return;
     // every model here has non-periodic stream and row axes; the pass
