@@ -513,7 +513,7 @@ def run_ours(args):
                 "traffic": dram_traffic(problem.name),
                 "kernel": "%s (whole time loop timed)" % (
                     "k_stage_bulk" if (args.stage_pass == "bulk" or (args.stage_pass == "auto" and
-                                                                       problem.dynamics == "rel6d"))
+                                                                       problem.ndim >= 4))
                     else "k_stage_plane"), "peak_source": peak_kind,
                 "alg_bytes_per_launch": bytes_per_solve / stage_launches,
                 "avg_launch_ms": ms_per_step / stage_launches,
@@ -589,7 +589,7 @@ def run_ours(args):
             "solves_per_s": world * 1000.0 / ms_per_step,
             "roofline_alu": alu,
             "stage_pass": {"plane": "plane-streaming", "bulk": "bulk-staged"}.get(
-                args.stage_pass, "plane-streaming" if problem.dynamics != "rel6d" else "bulk-staged"),
+                args.stage_pass, "plane-streaming" if problem.ndim < 4 else "bulk-staged"),
             "extra_workloads": extras,
         }
         print(json.dumps(line), flush=True)

@@ -213,9 +213,9 @@ odp_status odp_set_loop_mode(odp_grid *g, int host_stepped);
  * grid-wide dissipation) has a producer thread per CTA stage every neighbour
  * tile with bulk async copies into shared-memory rings; the plane-streaming
  * pass has the compute threads load their own neighbours.  pass = 0
- * (default) picks the one that measured faster for the model (bulk-staged
- * for Rel6D, plane-streaming otherwise); pass = 1 forces the plane-streaming
- * pass; pass = 2 the bulk-staged pass.  The choice holds for later solves of the grid; batched
+ * (default) picks the one that measured faster (bulk-staged on grids of 4 or
+ * more dimensions, plane-streaming on 3-D grids); pass = 1 forces the
+ * plane-streaming pass; pass = 2 the bulk-staged pass.  The choice holds for later solves of the grid; batched
  * and served solves always use the plane-streaming pass.  Errors: ODP_EINVAL
  * (pass out of range, or 2 on a grid whose shape the bulk-staged pass does
  * not take: last axis not a multiple of 4, fewer than 4 rows or stream

@@ -117,8 +117,12 @@ constexpr uint32_t BULK_WAIT_ITERS = 1u << 26;
 static __device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity)
 {
     const uint64_t t0 = global_ns();
+#ifndef ODP_BULK_BACKOFF
+#define ODP_BULK_BACKOFF 0
+#endif
     for (uint32_t it = 0; it < BULK_WAIT_ITERS; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (ODP_BULK_BACKOFF && it >= 4) __nanosleep(ODP_BULK_BACKOFF);   // leave issue slots to working warps
         if ((it & 63u) == 63u && global_ns() - t0 > BULK_WAIT_NS) return false;
     }
     return false;
@@ -144,11 +148,14 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 // ---------------------------------------------------------------------------
 // the pass
 // ---------------------------------------------------------------------------
-constexpr int BULK_RC_MAX = 8, BULK_RX_MAX = 4;
-// barriers (192 bytes), then the CTA's ghost table (count + up to 24 rules of
-// 4 ints), then the rings
-constexpr int BULK_GHOST_MAX = 24;
+constexpr int BULK_RC_MAX = 8, BULK_RX_MAX = 6;
+// barriers (full and empty per centre slot, empty per neighbour slot: at
+// most 176 bytes), the ghost-rule count at byte 192 and up to 16 rules of
+// 16 bytes from byte 208 (a grid has at most 2 r x 3 = 12), then the rings
+constexpr int BULK_GHOST_MAX = 16;
 constexpr int BULK_BAR_AREA = 512;
+static_assert(8 * (2 * BULK_RC_MAX + BULK_RX_MAX) <= 192, "barriers overlap the ghost table");
+static_assert(208 + 16 * BULK_GHOST_MAX <= BULK_BAR_AREA, "the ghost table overlaps the rings");
 
 // One ghost rule of an outer-axis neighbour slot that is not staged: slot
 // dst is formed from slots b and i (-1: the centre tile) k cells outside.
@@ -171,7 +178,7 @@ __device__ __forceinline__ BulkSmem bulk_smem(unsigned char *raw, const BulkGeom
     uint64_t *b = reinterpret_cast<uint64_t *>(raw);
     s.full_c = b;
     s.empty_c = b + BULK_RC_MAX;
-    s.empty_x = b + 2 * BULK_RC_MAX + BULK_RX_MAX;
+    s.empty_x = b + 2 * BULK_RC_MAX;
     s.nghost = reinterpret_cast<int *>(raw + 192);
     s.ghost = reinterpret_cast<BulkGhost *>(raw + 208);
     s.ring_c = reinterpret_cast<float *>(raw + BULK_BAR_AREA);
@@ -226,7 +233,8 @@ __device__ __forceinline__ void bulk_neighbours(const GridDesc &g, int d, int id
 // has one full barrier, that of the centre tile of plane s + r, on which the
 // neighbour tiles of plane s complete too.  Returns false if a wait gave up
 // (after waiting, bounded, for the copies already in flight).  The stream
-// and row axes are non-periodic (the planner takes no other grid).
+// and row axes are non-periodic (the planner takes no other grid).  (One
+// copy per lane of the producer warp measured no faster.)
 template <int ND, int O>
 __device__ bool bulk_produce(const GridDesc &g, const BulkGeom &bk, const BulkSmem &sm, const float *src, int pencil,
                              const int *idx, int band_lo, int band_rows, int s_begin, int s_end)
@@ -253,38 +261,55 @@ __device__ bool bulk_produce(const GridDesc &g, const BulkGeom &bk, const BulkSm
         for (int k = 0; k < 2 * O; ++k)
             if (nbq[d][k].staged) x_bytes += uint32_t(band_rows) * row_bytes;
     }
+    // slots advance one tile at a time and count their wraps (no division in
+    // the loop); the u-th use of a slot (u = wraps so far) first waits for
+    // the release of its previous tile, phase u - 1 of the slot's empty
+    // barrier.  Source and destination pointers advance one tile at a time.
     int ic = 0, ix = 0;
+    int cslot = 0, xslot = 0;
+    uint32_t cwrap = 0, xwrap = 0;
     bool ok = true;
+    const float *csrc = src + pencil + (s_begin - O) * plane + r_lo * npad;
+    const float *xsrc = src + pencil + s_begin * plane + band_lo * npad;
+    float *cdst = sm.ring_c + c_off;
+    float *xdst = sm.ring_x;
+    const uint32_t xrow_bytes = uint32_t(band_rows) * row_bytes;
     for (; ic < nplanes + 2 * O; ++ic) {
-        const int slot = ic % bk.rc, u = ic / bk.rc;
-        if (u > 0 && !mbar_wait(&sm.empty_c[slot], uint32_t(u - 1) & 1u)) {
+        if (cwrap > 0 && !mbar_wait(&sm.empty_c[cslot], (cwrap - 1) & 1u)) {
             ok = false;
             break;
         }
         const bool with_x = NX > 0 && ic >= 2 * O;
-        const int xslot = with_x ? ix % bk.rx : 0;
-        if (with_x && ix >= bk.rx && !mbar_wait(&sm.empty_x[xslot], uint32_t(ix / bk.rx - 1) & 1u)) {
+        if (with_x && xwrap > 0 && !mbar_wait(&sm.empty_x[xslot], (xwrap - 1) & 1u)) {
             ok = false;
             break;
         }
         const int q = s_begin - O + ic;                 // plane of the centre tile
         const bool have = q >= 0 && q < ns;
-        mbar_arrive_expect_tx(&sm.full_c[slot], (have ? c_bytes : 0u) + (with_x ? x_bytes : 0u));
-        if (have)
-            bulk_g2s(sm.ring_c + slot * ctile + c_off, src + pencil + q * plane + r_lo * npad, c_bytes,
-                     &sm.full_c[slot]);
+        mbar_arrive_expect_tx(&sm.full_c[cslot], (have ? c_bytes : 0u) + (with_x ? x_bytes : 0u));
+        if (have) bulk_g2s(cdst, csrc, c_bytes, &sm.full_c[cslot]);
         if (with_x) {
-            const int s = s_begin + ix;
-            const float *base = src + pencil + s * plane + band_lo * npad;
-            float *dst = sm.ring_x + xslot * NX * xtile;
 #pragma unroll
             for (int d = 0; d < NOUT; ++d)
 #pragma unroll
                 for (int k = 0; k < 2 * O; ++k)
                     if (nbq[d][k].staged)
-                        bulk_g2s(dst + (d * 2 * O + k) * xtile, base + nbq[d][k].delta, uint32_t(band_rows) * row_bytes,
-                                 &sm.full_c[slot]);
+                        bulk_g2s(xdst + (d * 2 * O + k) * xtile, xsrc + nbq[d][k].delta, xrow_bytes, &sm.full_c[cslot]);
             ++ix;
+            xsrc += plane;
+            xdst += NX * xtile;
+            if (++xslot == bk.rx) {
+                xslot = 0;
+                xdst = sm.ring_x;
+                ++xwrap;
+            }
+        }
+        csrc += plane;
+        cdst += ctile;
+        if (++cslot == bk.rc) {
+            cslot = 0;
+            cdst = sm.ring_c + c_off;
+            ++cwrap;
         }
     }
     if (ok) return true;
@@ -418,7 +443,9 @@ __global__ void __launch_bounds__(512) __maxnreg__((bulk_max_regs<ND, ORDER, DYN
     // ghost rows this thread forms (non-periodic row axis)
     const int gtop = r < O ? r + 1 : 0;
     const int gbot = r >= nr - O ? nr - r : 0;
-    const bool edge_band = band_lo < O || band_lo + band_rows > nr - O;
+    // only the warps holding one of the grid's first or last r rows form
+    // ghost rows (a warp-uniform flag, so the other warps skip the code)
+    const bool edge_band = __any_sync(0xffffffffu, active && (gtop != 0 || gbot != 0));
     // last-axis halo columns: wrapped columns of the same tile row, or ghosts
     int lh_off = -2, rh_off = 4;
     bool lghost = false, rghost = false;
@@ -640,8 +667,10 @@ __global__ void __launch_bounds__(512) __maxnreg__((bulk_max_regs<ND, ORDER, DYN
             {
                 float2 lh = *reinterpret_cast<const float2 *>(C + lh_off);
                 float2 rh = *reinterpret_cast<const float2 *>(C + rh_off);
-                if (lghost) lh = make_float2(keep_sign_ghost(c4.x, c4.y, 2.0f), keep_sign_ghost(c4.x, c4.y, 1.0f));
-                if (rghost) rh = make_float2(keep_sign_ghost(c4.w, c4.z, 1.0f), keep_sign_ghost(c4.w, c4.z, 2.0f));
+                if (!per_l) {   // ghost columns only on a non-periodic last axis (a grid-wide branch)
+                    if (lghost) lh = make_float2(keep_sign_ghost(c4.x, c4.y, 2.0f), keep_sign_ghost(c4.x, c4.y, 1.0f));
+                    if (rghost) rh = make_float2(keep_sign_ghost(c4.w, c4.z, 1.0f), keep_sign_ghost(c4.w, c4.z, 2.0f));
+                }
                 const float v[8] = {lh.x, lh.y, c4.x, c4.y, c4.z, c4.w, rh.x, rh.y};
                 axis_last<ORDER>(v, cA[ND - 1], cS[ND - 1], cD[ND - 1], L, has_drift<DYN, ND>(ND - 1),
                                  has_bound<DYN, ND>(ND - 1));

@@ -843,8 +843,9 @@ cudaError_t launch_stage_t(const GridDesc &g, const DynDesc &dy, SolveState *st,
     if constexpr (ND >= 3) {
         if constexpr (DYN == DYN_DUBINS3D || DYN == DYN_DUBINSCAR4D || DYN == DYN_REL6D) {
             // bk.use: 1 automatic (the bulk-staged pass where it measured
-            // faster: Rel6D), 2 the bulk-staged pass wherever it applies
-            const bool want = g.bk.use == 2 || (g.bk.use == 1 && DYN == DYN_REL6D);
+            // faster: grids of 4 or more dimensions), 2 the bulk-staged pass
+            // wherever it applies
+            const bool want = g.bk.use == 2 || (g.bk.use == 1 && ND >= 4);
             if (want && g.n[ND - 1] % 4 == 0 && !dy.local_diss && g.bk.smem[order - 1] > 0) {
                 if (order == 1) return launch_stage_bulk_t<ND, 1, DYN>(g, dy, st, l, gob, stage, brt, s);
                 return launch_stage_bulk_t<ND, 2, DYN>(g, dy, st, l, gob, stage, brt, s);

@@ -123,7 +123,7 @@ struct PlaneGeom {
 // then outer pencil in C order); the CTA has cwarps compute warps and one
 // producer warp; rc / rx ring slots hold centre and neighbour tiles.
 struct BulkGeom {
-    int use;           // 0: never; 1: where it is the faster pass (Rel6D); 2: wherever it applies
+    int use;           // 0: never; 1: where it is the faster pass (4 or more dims); 2: wherever it applies
     int rb, nbands;    // rows per band (the last band may be shorter), bands
     int chunk, nchunks;
     int items;         // CTAs per launch
