@@ -149,6 +149,9 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 // the pass
 // ---------------------------------------------------------------------------
 constexpr int BULK_RC_MAX = 8, BULK_RX_MAX = 6;
+// read-once tiles staged beside the neighbour tiles of a plane: l, phi^n,
+// the obstacle (each the band's rows of the plane)
+constexpr int BULK_AUX = 3;
 // barriers (full and empty per centre slot, empty per neighbour slot: at
 // most 176 bytes), the ghost-rule count at byte 192 and up to 16 rules of
 // 16 bytes from byte 208 (a grid has at most 2 r x 3 = 12), then the rings
@@ -237,7 +240,8 @@ __device__ __forceinline__ void bulk_neighbours(const GridDesc &g, int d, int id
 // copy per lane of the producer warp measured no faster.)
 template <int ND, int O>
 __device__ bool bulk_produce(const GridDesc &g, const BulkGeom &bk, const BulkSmem &sm, const float *src, int pencil,
-                             const int *idx, int band_lo, int band_rows, int s_begin, int s_end)
+                             const int *idx, int band_lo, int band_rows, int s_begin, int s_end,
+                             const float *const *aux, int naux_mask)
 {
     constexpr int NOUT = ND - 3, NX = 2 * O * NOUT;
     constexpr int sa = ND - 3;
@@ -261,6 +265,13 @@ __device__ bool bulk_produce(const GridDesc &g, const BulkGeom &bk, const BulkSm
         for (int k = 0; k < 2 * O; ++k)
             if (nbq[d][k].staged) x_bytes += uint32_t(band_rows) * row_bytes;
     }
+    // read-once tiles (aux[a] staged when bit a of naux_mask is set)
+    int naux = 0;
+#pragma unroll
+    for (int a = 0; a < BULK_AUX; ++a) naux += (naux_mask >> a) & 1;
+    x_bytes += uint32_t(naux) * uint32_t(band_rows) * row_bytes;
+    const bool xring = NX > 0 || naux > 0;
+    const int xstride = (NX + BULK_AUX) * xtile;   // floats per neighbour slot
     // slots advance one tile at a time and count their wraps (no division in
     // the loop); the u-th use of a slot (u = wraps so far) first waits for
     // the release of its previous tile, phase u - 1 of the slot's empty
@@ -279,7 +290,7 @@ __device__ bool bulk_produce(const GridDesc &g, const BulkGeom &bk, const BulkSm
             ok = false;
             break;
         }
-        const bool with_x = NX > 0 && ic >= 2 * O;
+        const bool with_x = xring && ic >= 2 * O;
         if (with_x && xwrap > 0 && !mbar_wait(&sm.empty_x[xslot], (xwrap - 1) & 1u)) {
             ok = false;
             break;
@@ -295,9 +306,14 @@ __device__ bool bulk_produce(const GridDesc &g, const BulkGeom &bk, const BulkSm
                 for (int k = 0; k < 2 * O; ++k)
                     if (nbq[d][k].staged)
                         bulk_g2s(xdst + (d * 2 * O + k) * xtile, xsrc + nbq[d][k].delta, xrow_bytes, &sm.full_c[cslot]);
+            const int aoff = (s_begin + ix) * plane + pencil + band_lo * npad;
+#pragma unroll
+            for (int a = 0; a < BULK_AUX; ++a)
+                if ((naux_mask >> a) & 1)
+                    bulk_g2s(xdst + (NX + a) * xtile, aux[a] + aoff, xrow_bytes, &sm.full_c[cslot]);
             ++ix;
             xsrc += plane;
-            xdst += NX * xtile;
+            xdst += xstride;
             if (++xslot == bk.rx) {
                 xslot = 0;
                 xdst = sm.ring_x;
@@ -365,6 +381,12 @@ __global__ void __launch_bounds__(512) __maxnreg__((bulk_max_regs<ND, ORDER, DYN
     const float *__restrict__ src = (stage == 2) ? st->nxt : st->cur;
     float *dst = (stage == 2) ? st->cur : st->nxt;
     const float *prev = st->cur;
+    const bool use_l = brt && stage != 1;
+    const bool use_g = (GOB >= 0 ? GOB == 1 : gob != nullptr) && stage != 1;
+    // read-once tiles the producer stages beside the neighbour tiles: l for
+    // the BRT min, phi^n for the Heun average, the obstacle
+    const int aux_mask = (use_l ? 1 : 0) | (stage == 2 ? 2 : 0) | (use_g ? 4 : 0);
+    const bool xring = NX > 0 || aux_mask != 0;
 
     // work item: chunk fastest, then band, then outer pencil.  Outer pencils
     // are numbered block by block (the plane pass's blocks of up to 8
@@ -399,10 +421,10 @@ __global__ void __launch_bounds__(512) __maxnreg__((bulk_max_regs<ND, ORDER, DYN
     if (tid == 0) {
         for (int i = 0; i < bk.rc; ++i) {
             mbar_init(&sm.full_c[i], 1);
-            mbar_init(&sm.empty_c[i], uint32_t(cwarps));
+            mbar_init(&sm.empty_c[i], uint32_t(32 * cwarps));   // every compute thread arrives
         }
         for (int i = 0; i < bk.rx; ++i) {
-            mbar_init(&sm.empty_x[i], uint32_t(cwarps));
+            mbar_init(&sm.empty_x[i], uint32_t(32 * cwarps));
         }
         mbar_fence_init();
         int ng = 0;
@@ -419,9 +441,11 @@ __global__ void __launch_bounds__(512) __maxnreg__((bulk_max_regs<ND, ORDER, DYN
     __syncthreads();
     const int warp = tid >> 5, lane = tid & 31;
     if (warp >= cwarps) {
-        if (warp == cwarps && lane == 0 &&
-            !bulk_produce<ND, O>(g, bk, sm, src, pencil, idx, band_lo, band_rows, s_begin, s_end))
-            atomicOr(&st->flags, FLAG_COPY);
+        if (warp == cwarps && lane == 0) {
+            const float *aux[BULK_AUX] = {l, prev, gob};
+            if (!bulk_produce<ND, O>(g, bk, sm, src, pencil, idx, band_lo, band_rows, s_begin, s_end, aux, aux_mask))
+                atomicOr(&st->flags, FLAG_COPY);
+        }
         return;
     }
 
@@ -432,8 +456,6 @@ __global__ void __launch_bounds__(512) __maxnreg__((bulk_max_regs<ND, ORDER, DYN
     const int r = band_lo + (active ? j : 0);
     const int jt = active ? j : 0;
     const int per_l = g.periodic[ND - 1];
-    const bool use_l = brt && stage != 1;
-    const bool use_g = (GOB >= 0 ? GOB == 1 : gob != nullptr) && stage != 1;
     const unsigned *ab = st->alpha_bits[stage == 2 ? 1 : 0];
     float cD[ND];
 #pragma unroll
@@ -492,10 +514,10 @@ __global__ void __launch_bounds__(512) __maxnreg__((bulk_max_regs<ND, ORDER, DYN
             par ^= 1u;
         }
     };
-    auto release = [&](uint64_t *bar) {
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bar);
-    };
+    // a slot is free once every compute thread has arrived (one arrive
+    // instruction per warp, no branch); each thread arrives after its own
+    // last read of the slot
+    auto release = [&](uint64_t *bar) { mbar_arrive(bar); };
 
     // stream axis: instead of a window of values the thread carries the
     // differences of its segment from plane to plane: ea = w(s) - w(s-1),
@@ -557,26 +579,20 @@ __global__ void __launch_bounds__(512) __maxnreg__((bulk_max_regs<ND, ORDER, DYN
         const float *Tn = sm.ring_c + n_slot * ctile + so;
         advance(n_slot, n_par, rc);
         // the neighbour tiles of plane s completed on the same barrier
-        const float *X = sm.ring_x + x_slot * NX * xtile + xo;
+        const float *X = sm.ring_x + x_slot * (NX + BULK_AUX) * xtile + xo;
         const float *C = sm.ring_c + r_slot * ctile + so;
         const int gi = base + s * plane;
         float4 lx = make_float4(0.f, 0.f, 0.f, 0.f), px = lx, gx = lx;
-        if (active && ok) {
+        // every thread computes (threads past the band's last row compute a
+        // copy of its first row), only the valid ones store
+        {
 #ifndef ODP_BULK_STREAMING
 #define ODP_BULK_STREAMING 1
 #endif
-            // l, the obstacle and phi^n are read once and the output written
-            // once: streaming accesses (evict first), so L2 keeps the tiles
-            // that neighbouring CTAs stage again
-            if (ODP_BULK_STREAMING) {
-                if (use_l) lx = __ldcs(reinterpret_cast<const float4 *>(l + gi));
-                if (use_g) gx = __ldcs(reinterpret_cast<const float4 *>(gob + gi));
-                if (stage == 2) px = __ldcs(reinterpret_cast<const float4 *>(prev + gi));
-            } else {
-                if (use_l) lx = ldg4(l + gi);
-                if (use_g) gx = ldg4(gob + gi);
-                if (stage == 2) px = *reinterpret_cast<const float4 *>(prev + gi);
-            }
+            // l, phi^n and the obstacle from the tiles the producer staged
+            if (use_l) lx = *reinterpret_cast<const float4 *>(X + (NX + 0) * xtile);
+            if (stage == 2) px = *reinterpret_cast<const float4 *>(X + (NX + 1) * xtile);
+            if (use_g) gx = *reinterpret_cast<const float4 *>(X + (NX + 2) * xtile);
             const float4 c4 = *reinterpret_cast<const float4 *>(C);
             // stream-axis differences of plane s (ghost planes past a
             // non-periodic end from the carried differences)
@@ -675,15 +691,19 @@ __global__ void __launch_bounds__(512) __maxnreg__((bulk_max_regs<ND, ORDER, DYN
                 axis_last<ORDER>(v, cA[ND - 1], cS[ND - 1], cD[ND - 1], L, has_drift<DYN, ND>(ND - 1),
                                  has_bound<DYN, ND>(ND - 1));
             }
-            const float4 out = update_nodes(dt, stage, use_l, c4, L, px, lx, use_g, gx, 4, fin);
-            if (ODP_BULK_STREAMING)
-                __stcs(reinterpret_cast<float4 *>(dst + gi), out);
-            else
-                *reinterpret_cast<float4 *>(dst + gi) = out;
+            float2 fin_step = fin;
+            const float4 out = update_nodes(dt, stage, use_l, c4, L, px, lx, use_g, gx, 4, fin_step);
+            if (active && ok) {
+                fin = fin_step;
+                if (ODP_BULK_STREAMING)
+                    __stcs(reinterpret_cast<float4 *>(dst + gi), out);
+                else
+                    *reinterpret_cast<float4 *>(dst + gi) = out;
+            }
         }
         release(&sm.empty_c[r_slot]);
         advance(r_slot, r_par, rc);
-        if (NX > 0) {
+        if (xring) {
             release(&sm.empty_x[x_slot]);
             if (++x_slot == rx) x_slot = 0;
         }

@@ -279,7 +279,10 @@ void odp::bulk_geometry(GridDesc &D, int sms)
     bk.rx = ODP_BULK_RX;
     const long long row_bytes = 4LL * D.n_pad;
     for (int o = 1; o <= 2; ++o) {
-        const long long bytes = 512 + bk.rc * (rb + 2LL * o) * row_bytes + bk.rx * (2LL * o * (nd - 3)) * rb * row_bytes;
+        // centre ring, then neighbour slots of 2 o (nd - 3) neighbour tiles
+        // and 3 read-once tiles (l, phi^n, obstacle) each
+        const long long bytes =
+            512 + bk.rc * (rb + 2LL * o) * row_bytes + bk.rx * (2LL * o * (nd - 3) + 3) * rb * row_bytes;
         // (ODP_BULK_RC <= 8 and ODP_BULK_RX <= 6: the barrier area holds that many)
         bk.smem[o - 1] = bytes <= 200 * 1024 ? int(bytes) : 0;
     }
