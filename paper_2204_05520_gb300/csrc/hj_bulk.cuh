@@ -350,15 +350,21 @@ __device__ __forceinline__ float4 ghost4v(const float4 &pb, const float4 &pi, fl
 // alpha static or given per stage (the grid-wide dissipation of Section 2.1).
 // STAGE and GOB as in k_stage_plane.
 #ifndef ODP_BULK_REGS
-#define ODP_BULK_REGS 96
+#define ODP_BULK_REGS 112
 #endif
-// Register cap of the bulk-staged pass: the DubinsCar4D ENO2 pass runs
-// without spills at 96 registers (two CTAs of eight warps per SM; at 80 its
-// second RK stage spills); the others keep the plane pass's budget.
+#ifndef ODP_BULK_REGS6
+#define ODP_BULK_REGS6 96
+#endif
+// Register cap of the bulk-staged pass.  Its rings hold the DubinsCar4D ENO2
+// pass to two CTAs of eight warps per SM, which leaves up to 128 registers a
+// thread: 112 measured fastest (96 spills in the second RK stage).  The
+// others keep the plane pass's budget.
 template <int ND, int ORDER, int DYN>
 constexpr int bulk_max_regs()
 {
-    return (DYN == DYN_DUBINSCAR4D && ORDER == 2) ? ODP_BULK_REGS : plane_max_regs<ND, ORDER, DYN>();
+    return (DYN == DYN_DUBINSCAR4D && ORDER == 2) ? ODP_BULK_REGS
+         : (DYN == DYN_REL6D) ? ODP_BULK_REGS6
+                              : plane_max_regs<ND, ORDER, DYN>();
 }
 
 template <int ND, int ORDER, int DYN, int STAGE, int GOB>
