@@ -499,9 +499,10 @@ def run_ours(args):
     value = world * N * steps_per_solve / (ms_per_step / 1000.0)
 
     # Roofline of the time loop, live over the timed region: the algorithmic
-    # bytes of every stage pass (and of the Rel6D alpha pass) divided by the
-    # event-timed region, so the time of the small dt/alpha kernels counts
-    # against the stage pass.  The stage pass alone (events around 20
+    # bytes of every stage pass divided by the event-timed region, so the
+    # time of the small dt/alpha kernels (and the Rel6D heading-rate pass,
+    # which stops reading once its ceiling is reached) counts against the
+    # stage pass.  The stage pass alone (events around 20
     # back-to-back launches on the grid's stream) is reported beside it.
     stages = (1, 2) if problem.time_order == 2 else (0,)
     stage_ms = [odp.time_stage(grid.handle, s, reps=20) for s in stages]

@@ -634,6 +634,15 @@ __global__ void __launch_bounds__(256) k_alpha_rel6d(GridDesc g, DynDesc dy, Sol
 {
     constexpr int O = ORDER, Q = 2 * O + 1;
     __shared__ float red[8];
+    __shared__ int reached;
+    // No node's bound exceeds dy.acap (the straddling case at the largest
+    // |w_p| of the grid), so once some CTA has reached it the grid maximum
+    // is known whatever the other CTAs would find: they skip their reads.
+    // (The component is cleared before each step's alpha passes.)
+    if (threadIdx.x == 0)
+        reached = dy.acap > 0.0f && __ldcg(&st->alpha_bits[slot][2]) >= __float_as_uint(dy.acap);
+    __syncthreads();
+    if (reached) return;
     const float *__restrict__ src = slot ? st->nxt : st->cur;
     const int nh = g.n[2], inner = g.stride[2];    // heading planes; floats per plane of an (x, y) block
     const uint32_t isegs = uint32_t(inner / 4);

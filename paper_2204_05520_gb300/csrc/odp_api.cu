@@ -547,6 +547,19 @@ extern "C" odp_status odp_set_dynamics(odp_grid *g, odp_dyn kind, const double *
     dy.angle_axis = angle;
     dy.local_diss = g->local_diss;
     for (int k = 0; k < n_params; ++k) dy.prm[k] = float(params[k]);
+    if (kind == ODP_DYN_REL6D) {
+        // ceiling of the heading-rate bound over the grid: the straddling
+        // case max(|b - w_p|, |-b - w_p|) at every w_p node, in float as the
+        // kernel evaluates it (the node coordinates are the float table's)
+        const float b = dy.prm[3];
+        const double h = (g->hi[4] - g->lo[4]) / double(g->periodic[4] ? g->n[4] : g->n[4] - 1);
+        float cap = 0.0f;
+        for (int i = 0; i < g->n[4]; ++i) {
+            const float wp = float(g->lo[4] + double(i) * h);
+            cap = std::max(cap, std::max(std::fabs(b - wp), std::fabs(-b - wp)));
+        }
+        dy.acap = cap;
+    }
     g->dyn = dy;
     g->dyn_version += 1;
     if (angle >= 0) {
@@ -1133,13 +1146,15 @@ extern "C" odp_status odp_solve_status(odp_grid *g, odp_solve_stats *stats)
         }
         // algorithmic HBM bytes per node per step: every stage reads phi once
         // and writes its result; stage 2 also reads phi^n; the last stage of a
-        // tube reads l (and the obstacle of a reach-avoid solve); Rel6D adds
-        // one read of phi per stage for its alpha.
+        // tube reads l (and the obstacle of a reach-avoid solve).
         const double per_stage_rw = 8.0;
         double b = (g->time_order == 1) ? per_stage_rw : (2 * per_stage_rw + 4.0);
         if (g->brt) b += 4.0;
         if (g->has_obst) b += 4.0;
-        if (dynamic_alpha_mask(g)) b += 4.0 * g->time_order;
+        // the capture model's alpha pass reads phi once per stage; the Rel6D
+        // heading-rate pass stops once its ceiling is reached, so its reads
+        // are not counted
+        if (dynamic_alpha_mask(g) && g->dyn.kind != DYN_REL6D) b += 4.0 * g->time_order;
         // capture model with per-node dissipation: each stage writes and
         // reads three coefficients per node
         if (g->desc.cdn) b += 24.0 * g->time_order;

@@ -179,6 +179,9 @@ struct DynDesc {
     int angle_axis;              // axis holding the heading angle, -1 if none
     int local_diss;              // 1: per-node dissipation alpha_i (Algorithm 1's second loop)
     float prm[8];
+    // the largest value the phi-dependent alpha component (Rel6D heading
+    // rate) can take on this grid, in the kernels' float arithmetic; 0: none
+    float acap;
 };
 
 // alpha is kept as the bit pattern of a non-negative float so that the
