@@ -87,7 +87,7 @@ def hbm_peak():
 # sources that define the stage pass and the model instantiations it is
 # profiled on: a DRAM-traffic record holds only while these are unchanged
 STAGE_SOURCES = ("odp_common.cuh", "hj_device.cuh", "hj_kernels.cuh", "hj_plane.cuh", "hj_bulk.cuh",
-                 "kern_dubins.cu", "kern_rel6d.cu")
+                 "kern_dubins.cu", "kern_rel6d.cu", "odp_api.cu")   # odp_api.cu: the launch geometry
 
 
 def kernel_sources_sha() -> str:

@@ -271,7 +271,7 @@ __device__ bool bulk_produce(const GridDesc &g, const BulkGeom &bk, const BulkSm
     for (int a = 0; a < BULK_AUX; ++a) naux += (naux_mask >> a) & 1;
     x_bytes += uint32_t(naux) * uint32_t(band_rows) * row_bytes;
     const bool xring = NX > 0 || naux > 0;
-    const int xstride = (NX + BULK_AUX) * xtile;   // floats per neighbour slot
+    const int xstride = (NX + naux) * xtile;   // floats per neighbour slot
     // slots advance one tile at a time and count their wraps (no division in
     // the loop); the u-th use of a slot (u = wraps so far) first waits for
     // the release of its previous tile, phase u - 1 of the slot's empty
@@ -306,11 +306,14 @@ __device__ bool bulk_produce(const GridDesc &g, const BulkGeom &bk, const BulkSm
                 for (int k = 0; k < 2 * O; ++k)
                     if (nbq[d][k].staged)
                         bulk_g2s(xdst + (d * 2 * O + k) * xtile, xsrc + nbq[d][k].delta, xrow_bytes, &sm.full_c[cslot]);
+            // the read-once tiles follow the neighbour tiles in the order
+            // l, phi^n, obstacle, each present only when staged
             const int aoff = (s_begin + ix) * plane + pencil + band_lo * npad;
+            int apos = NX;
 #pragma unroll
             for (int a = 0; a < BULK_AUX; ++a)
                 if ((naux_mask >> a) & 1)
-                    bulk_g2s(xdst + (NX + a) * xtile, aux[a] + aoff, xrow_bytes, &sm.full_c[cslot]);
+                    bulk_g2s(xdst + (apos++) * xtile, aux[a] + aoff, xrow_bytes, &sm.full_c[cslot]);
             ++ix;
             xsrc += plane;
             xdst += xstride;
@@ -350,15 +353,17 @@ __device__ __forceinline__ float4 ghost4v(const float4 &pb, const float4 &pi, fl
 // alpha static or given per stage (the grid-wide dissipation of Section 2.1).
 // STAGE and GOB as in k_stage_plane.
 #ifndef ODP_BULK_REGS
-#define ODP_BULK_REGS 112
+#define ODP_BULK_REGS 96
 #endif
 #ifndef ODP_BULK_REGS6
 #define ODP_BULK_REGS6 96
 #endif
-// Register cap of the bulk-staged pass.  Its rings hold the DubinsCar4D ENO2
-// pass to two CTAs of eight warps per SM, which leaves up to 128 registers a
-// thread: 112 measured fastest (96 spills in the second RK stage).  The
-// others keep the plane pass's budget.
+// Register cap of the bulk-staged pass.  The DubinsCar4D ENO2 pass runs
+// bands of 128 compute threads (four compute warps and the producer warp):
+// 96 registers (and a 40-byte spill a thread) let four CTAs share an SM,
+// measured faster than 104 or 112 (three CTAs) and than bands of 256
+// threads at 112.  Rel6D runs three CTAs
+// of six warps at 96.  The others keep the plane pass's budget.
 template <int ND, int ORDER, int DYN>
 constexpr int bulk_max_regs()
 {
@@ -393,14 +398,17 @@ __global__ void __launch_bounds__(512) __maxnreg__((bulk_max_regs<ND, ORDER, DYN
     // the BRT min, phi^n for the Heun average, the obstacle
     const int aux_mask = (use_l ? 1 : 0) | (stage == 2 ? 2 : 0) | (use_g ? 4 : 0);
     const bool xring = NX > 0 || aux_mask != 0;
+    // their positions in a neighbour slot, after the NX neighbour tiles
+    const int pos_p = NX + (use_l ? 1 : 0), pos_g = pos_p + (stage == 2 ? 1 : 0);
+    const int xslot_floats = (pos_g + (use_g ? 1 : 0)) * bk.rb * npad;
 
     // work item: chunk fastest, then band, then outer pencil.  Outer pencils
     // are numbered block by block (the plane pass's blocks of up to 8
     // indices per outer axis), so CTAs that run together stage each other's
     // pencils as neighbour tiles while they are still in L2.
     const uint32_t item = blockIdx.x;
-    const uint32_t q1 = fast_div(item, bk.div_nchunks);
-    const int chunk = int(item - q1 * uint32_t(bk.nchunks));
+    const uint32_t q1 = fast_div(item, bk.div_nchunks[O - 1]);
+    const int chunk = int(item - q1 * uint32_t(bk.nchunks[O - 1]));
     const uint32_t outer = fast_div(q1, bk.div_nbands);
     const int band = int(q1 - outer * uint32_t(bk.nbands));
     int idx[ND];
@@ -418,8 +426,8 @@ __global__ void __launch_bounds__(512) __maxnreg__((bulk_max_regs<ND, ORDER, DYN
             pencil += idx[d] * g.stride[d];
         }
     }
-    const int s_begin = chunk * bk.chunk;
-    const int s_end = min(ns, s_begin + bk.chunk);
+    const int s_begin = chunk * bk.chunk[O - 1];
+    const int s_end = min(ns, s_begin + bk.chunk[O - 1]);
     const int band_lo = band * bk.rb;
     const int band_rows = min(bk.rb, nr - band_lo);
 
@@ -585,7 +593,7 @@ __global__ void __launch_bounds__(512) __maxnreg__((bulk_max_regs<ND, ORDER, DYN
         const float *Tn = sm.ring_c + n_slot * ctile + so;
         advance(n_slot, n_par, rc);
         // the neighbour tiles of plane s completed on the same barrier
-        const float *X = sm.ring_x + x_slot * (NX + BULK_AUX) * xtile + xo;
+        const float *X = sm.ring_x + x_slot * xslot_floats + xo;
         const float *C = sm.ring_c + r_slot * ctile + so;
         const int gi = base + s * plane;
         float4 lx = make_float4(0.f, 0.f, 0.f, 0.f), px = lx, gx = lx;
@@ -596,9 +604,9 @@ __global__ void __launch_bounds__(512) __maxnreg__((bulk_max_regs<ND, ORDER, DYN
 #define ODP_BULK_STREAMING 1
 #endif
             // l, phi^n and the obstacle from the tiles the producer staged
-            if (use_l) lx = *reinterpret_cast<const float4 *>(X + (NX + 0) * xtile);
-            if (stage == 2) px = *reinterpret_cast<const float4 *>(X + (NX + 1) * xtile);
-            if (use_g) gx = *reinterpret_cast<const float4 *>(X + (NX + 2) * xtile);
+            if (use_l) lx = *reinterpret_cast<const float4 *>(X + NX * xtile);
+            if (stage == 2) px = *reinterpret_cast<const float4 *>(X + pos_p * xtile);
+            if (use_g) gx = *reinterpret_cast<const float4 *>(X + pos_g * xtile);
             const float4 c4 = *reinterpret_cast<const float4 *>(C);
             // stream-axis differences of plane s (ghost planes past a
             // non-periodic end from the carried differences)

@@ -811,8 +811,12 @@ template <int ND, int ORDER, int DYN>
 cudaError_t launch_stage_bulk_t(const GridDesc &g, const DynDesc &dy, SolveState *st, const float *l,
                                 const float *gob, int stage, int brt, cudaStream_t s)
 {
-    const int blocks = g.bk.items, th = 32 * (g.bk.cwarps + 1), sm = g.bk.smem[ORDER - 1];
     const bool ob = gob != nullptr;
+    // shared memory for the read-once tiles this stage stages (l for the
+    // BRT min, phi^n for the Heun average, the obstacle)
+    const int naux = stage == 1 ? 0 : (brt ? 1 : 0) + (stage == 2 ? 1 : 0) + (ob ? 1 : 0);
+    const int blocks = g.bk.items[ORDER - 1], th = 32 * (g.bk.cwarps + 1);
+    const int sm = int(bulk_smem_bytes(g.bk, g.n_pad, ND, ORDER, naux));
     if (stage == 0) {
         if (ob)
             k_stage_bulk<ND, ORDER, DYN, 0, 1><<<blocks, th, sm, s>>>(g, dy, st, l, gob, stage, brt);
@@ -827,6 +831,30 @@ cudaError_t launch_stage_bulk_t(const GridDesc &g, const DynDesc &dy, SolveState
             k_stage_bulk<ND, ORDER, DYN, 2, 0><<<blocks, th, sm, s>>>(g, dy, st, l, gob, stage, brt);
     }
     return cudaGetLastError();
+}
+
+// Resident CTAs per SM of the bulk-staged pass with `threads` threads and
+// `smem` shared bytes a CTA (the fewer of its two RK stages).
+template <int ND, int ORDER, int DYN>
+cudaError_t occupancy_stage_bulk_t(int threads, int smem, int *per_sm)
+{
+    int a = 0, b = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_stage_bulk<ND, ORDER, DYN, 1, 0>, threads, smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_stage_bulk<ND, ORDER, DYN, 2, 0>, threads, smem);
+    *per_sm = a < b ? a : b;
+    return e;
+}
+
+template <int ND, int DYN>
+cudaError_t occupancy_stage_bulk_nd(int order, int threads, int smem, int *per_sm)
+{
+    if constexpr (ND >= 3 && (DYN == DYN_DUBINS3D || DYN == DYN_DUBINSCAR4D || DYN == DYN_REL6D)) {
+        if (order == 1) return occupancy_stage_bulk_t<ND, 1, DYN>(threads, smem, per_sm);
+        return occupancy_stage_bulk_t<ND, 2, DYN>(threads, smem, per_sm);
+    }
+    *per_sm = 0;
+    return cudaSuccess;
 }
 
 template <int ND, int ORDER, int DYN>

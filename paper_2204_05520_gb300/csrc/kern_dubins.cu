@@ -17,6 +17,12 @@ cudaError_t configure_stage_dubins(int nd)
     return configure_stage_t<4, DYN_DUBINSCAR4D>();
 }
 
+cudaError_t occupancy_stage_bulk_dubins(int nd, int order, int threads, int smem, int *per_sm)
+{
+    if (nd == 3) return occupancy_stage_bulk_nd<3, DYN_DUBINS3D>(order, threads, smem, per_sm);
+    return occupancy_stage_bulk_nd<4, DYN_DUBINSCAR4D>(order, threads, smem, per_sm);
+}
+
 cudaError_t launch_alpha_static_dubins(int nd, const GridDesc &g, const DynDesc &dy,
                                        SolveState *st, cudaStream_t s)
 {

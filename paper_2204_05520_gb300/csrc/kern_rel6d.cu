@@ -12,6 +12,11 @@ cudaError_t launch_stage_rel6d(const GridDesc &g, const DynDesc &dy, SolveState 
 
 cudaError_t configure_stage_rel6d() { return configure_stage_t<6, DYN_REL6D>(); }
 
+cudaError_t occupancy_stage_bulk_rel6d(int order, int threads, int smem, int *per_sm)
+{
+    return occupancy_stage_bulk_nd<6, DYN_REL6D>(order, threads, smem, per_sm);
+}
+
 cudaError_t launch_alpha_static_rel6d(const GridDesc &g, const DynDesc &dy, SolveState *st,
                                       cudaStream_t s)
 {

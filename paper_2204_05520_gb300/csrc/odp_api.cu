@@ -218,12 +218,22 @@ void odp::plane_geometry(GridDesc &D, int sms)
     pg.div_nchunks = make_fastdiv(uint32_t(pg.nchunks));
     pg.div_nbands = make_fastdiv(uint32_t(pg.nbands));
     // blocks of outer pencils: per outer axis the largest divisor of its
-    // length up to 8
+    // length up to ODP_PB0, ODP_PB1, ODP_PB2 (8 each)
+#ifndef ODP_PB0
+#define ODP_PB0 8
+#endif
+#ifndef ODP_PB1
+#define ODP_PB1 8
+#endif
+#ifndef ODP_PB2
+#define ODP_PB2 8
+#endif
+    const int bmax[3] = {ODP_PB0, ODP_PB1, ODP_PB2};
     pg.bvol = 1;
     for (int d = 0; d < 3; ++d) {
         int b = 1;
         if (d < D.ndim - 3)
-            for (int c = 8; c >= 1; --c)
+            for (int c = bmax[d]; c >= 1; --c)
                 if (D.n[d] % c == 0) {
                     b = c;
                     break;
@@ -238,8 +248,11 @@ void odp::plane_geometry(GridDesc &D, int sms)
     pg.use = 1;
 }
 
-#ifndef ODP_BULK_WAVES
-#define ODP_BULK_WAVES 4
+#ifndef ODP_BULK_THREADS
+#define ODP_BULK_THREADS 256   // compute threads a band aims at
+#endif
+#ifndef ODP_BULK_THREADS4
+#define ODP_BULK_THREADS4 128  // ... on the DubinsCar4D grids
 #endif
 #ifndef ODP_BULK_RC
 #define ODP_BULK_RC 5
@@ -248,7 +261,53 @@ void odp::plane_geometry(GridDesc &D, int sms)
 #define ODP_BULK_RX 3
 #endif
 
-void odp::bulk_geometry(GridDesc &D, int sms)
+// Stream-axis chunking of the bulk-staged pass for stencil radius o with
+// per_sm resident CTAs per SM: the chunk count that minimises a makespan
+// model.  A launch runs items / (per_sm x sms) waves; in a partial last wave
+// an SM holds c <= per_sm CTAs and takes 0.4 + 0.6 c / per_sm of a full
+// wave's time; each item costs its planes plus about 2o + 1 planes of window
+// fill and setup.  Launches of fewer than 1.5 waves are avoided where the
+// stream axis allows (measured slow: SMs stay part-empty throughout).
+void odp::bulk_chunking(GridDesc &D, int o, int per_sm, int sms)
+{
+    BulkGeom &bk = D.bk;
+    const int nd = D.ndim, ns = D.n[nd - 3];
+    per_sm = std::max(per_sm, 1);
+    sms = std::max(sms, 1);
+    long long pencils = 1;
+    for (int d = 0; d < nd - 3; ++d) pencils *= D.n[d];
+    const long long base = pencils * bk.nbands;
+    const long long res = (long long)per_sm * sms;
+    double best = 0.0;
+    int best_chunk = 0;
+    bool best_deep = false;
+    for (int nch = 1; nch <= std::max(1, ns / 4); ++nch) {   // at least four planes per chunk
+        int chunk = (ns + nch - 1) / nch;
+        // every chunk holds at least two planes (the window fill reads two ahead)
+        while (ns % chunk != 0 && ns % chunk < 2) ++chunk;
+        const long long items = base * ((ns + chunk - 1) / chunk);
+        const long long full = items / res, last = items - full * res;
+        const long long c = (last + sms - 1) / sms;
+        const double waves = double(full) + (last > 0 ? 0.4 + 0.6 * double(c) / double(per_sm) : 0.0);
+        const double cost = waves * double(chunk + 2 * o + 1);
+        const bool deep = 2 * items >= 3 * res;
+        if (best_chunk == 0 || (deep && !best_deep) || (deep == best_deep && cost < best)) {
+            best = cost;
+            best_chunk = chunk;
+            best_deep = deep;
+        }
+    }
+#ifdef ODP_BULK_NCH
+    best_chunk = (ns + ODP_BULK_NCH - 1) / ODP_BULK_NCH;
+    while (ns % best_chunk != 0 && ns % best_chunk < 2) ++best_chunk;
+#endif
+    bk.chunk[o - 1] = best_chunk;
+    bk.nchunks[o - 1] = (ns + best_chunk - 1) / best_chunk;
+    bk.items[o - 1] = int(base * bk.nchunks[o - 1]);
+    bk.div_nchunks[o - 1] = make_fastdiv(uint32_t(bk.nchunks[o - 1]));
+}
+
+void odp::bulk_geometry(GridDesc &D, int sms, int threads)
 {
     BulkGeom &bk = D.bk;
     bk = BulkGeom{};
@@ -260,8 +319,8 @@ void odp::bulk_geometry(GridDesc &D, int sms)
     // every model here has non-periodic stream and row axes; the pass
     // takes only those
     if (D.periodic[nd - 2] || D.periodic[nd - 3]) return;
-    // bands of about 256 compute threads (balanced band heights)
-    int rb = 256 / segs;
+    // bands of about `threads` compute threads (balanced band heights)
+    int rb = std::max(threads, 32) / segs;
     if (rb < 1) rb = 1;
     int nb = 1;
     if (rb >= nr) {
@@ -277,37 +336,21 @@ void odp::bulk_geometry(GridDesc &D, int sms)
     bk.cwarps = cwarps;
     bk.rc = ODP_BULK_RC;
     bk.rx = ODP_BULK_RX;
-    const long long row_bytes = 4LL * D.n_pad;
+    // (ODP_BULK_RC <= 8 and ODP_BULK_RX <= 6: the barrier area holds that many)
     for (int o = 1; o <= 2; ++o) {
-        // centre ring, then neighbour slots of 2 o (nd - 3) neighbour tiles
-        // and 3 read-once tiles (l, phi^n, obstacle) each
-        const long long bytes =
-            512 + bk.rc * (rb + 2LL * o) * row_bytes + bk.rx * (2LL * o * (nd - 3) + 3) * rb * row_bytes;
-        // (ODP_BULK_RC <= 8 and ODP_BULK_RX <= 6: the barrier area holds that many)
+        const long long bytes = bulk_smem_bytes(bk, D.n_pad, nd, o, 3);
         bk.smem[o - 1] = bytes <= 200 * 1024 ? int(bytes) : 0;
     }
     if (bk.smem[0] == 0 && bk.smem[1] == 0) return;
-    long long pencils = 1;
-    for (int d = 0; d < nd - 3; ++d) pencils *= D.n[d];
-    // resident CTAs per SM from shared memory and threads (80-96 registers a
-    // thread caps them near three); chunks sized for about ODP_BULK_WAVES waves
-    const int sm_bytes = bk.smem[1] ? bk.smem[1] : bk.smem[0];
-    int per_sm = (228 * 1024) / (sm_bytes + 1024);
-    const int by_regs = 65536 / (88 * 32 * (cwarps + 1));
-    if (per_sm > by_regs) per_sm = by_regs;
-    if (per_sm < 1) per_sm = 1;
-    const long long target = (long long)ODP_BULK_WAVES * per_sm * sms;
-    const long long base = pencils * nb;
-    long long nch = (target + base - 1) / base;
-    if (nch > ns / 4) nch = ns / 4;   // at least four planes per chunk
-    if (nch < 1) nch = 1;
-    int chunk = int((ns + nch - 1) / nch);
-    // every chunk holds at least two planes (the window fill reads two ahead)
-    while (ns % chunk != 0 && ns % chunk < 2) ++chunk;
-    bk.chunk = chunk;
-    bk.nchunks = (ns + chunk - 1) / chunk;
-    bk.items = int(base * bk.nchunks);
-    bk.div_nchunks = make_fastdiv(uint32_t(bk.nchunks));
+    // resident CTAs per SM estimated from shared memory and threads (about
+    // 96 registers a thread); odp_set_dynamics replaces the estimate with
+    // the kernels' own occupancy
+    for (int o = 1; o <= 2; ++o) {
+        const int sm_bytes = bk.smem[o - 1] ? bk.smem[o - 1] : bk.smem[2 - o];
+        int per_sm = (228 * 1024) / (sm_bytes + 1024);
+        per_sm = std::min(per_sm, 65536 / (96 * 32 * (cwarps + 1)));
+        bulk_chunking(D, o, std::max(per_sm, 1), sms);
+    }
     bk.div_nbands = make_fastdiv(uint32_t(bk.nbands));
     bk.use = 1;
 }
@@ -484,7 +527,7 @@ extern "C" odp_status odp_grid_create(int ndim, const int32_t *n, const double *
         s *= (d == ndim - 1) ? g->n_pad : n[d];
     }
     plane_geometry(D, 152);   // needs the axis sizes above
-    bulk_geometry(D, 152);
+    bulk_geometry(D, 152, ODP_BULK_THREADS);
     g->bulk_ok = D.bk.use;
     ODP_TRY(cudaMalloc(&g->tables, size_t(tab_len) * sizeof(float)));
     ODP_TRY(cudaMemcpy(g->tables, tab.data(), size_t(tab_len) * sizeof(float), cudaMemcpyHostToDevice));
@@ -578,6 +621,29 @@ extern "C" odp_status odp_set_dynamics(odp_grid *g, odp_dyn kind, const double *
     default: ce = configure_stage_rel6d(); break;
     }
     if (ce != cudaSuccess) return fail(ODP_ECUDA, "configuring the stage kernels: %s", cudaGetErrorString(ce));
+    // the bulk-staged pass: bands sized for the model, stream chunks for the
+    // kernels' own occupancy on this device
+    if (g->bulk_ok && (dy.kind == DYN_DUBINS3D || dy.kind == DYN_DUBINSCAR4D || dy.kind == DYN_REL6D)) {
+        GridDesc &D = g->desc;
+        const int use = D.bk.use;
+        int sms = 0;
+        ODP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
+        bulk_geometry(D, sms, dy.kind == DYN_DUBINSCAR4D ? ODP_BULK_THREADS4 : ODP_BULK_THREADS);
+        if (!D.bk.use) bulk_geometry(D, sms, ODP_BULK_THREADS);   // the shape checked at creation
+        D.bk.use = use;
+        for (int o = 1; o <= 2 && D.bk.rb > 0; ++o) {
+            if (!D.bk.smem[o - 1]) continue;
+            // the occupancy of a BRT stage 2 (l and phi^n staged beside the neighbours)
+            const int threads = 32 * (D.bk.cwarps + 1);
+            const int bytes = int(bulk_smem_bytes(D.bk, D.n_pad, g->ndim, o, 2));
+            int per_sm = 0;
+            ce = dy.kind == DYN_REL6D ? occupancy_stage_bulk_rel6d(o, threads, bytes, &per_sm)
+                                      : occupancy_stage_bulk_dubins(g->ndim, o, threads, bytes, &per_sm);
+            if (ce != cudaSuccess)
+                return fail(ODP_ECUDA, "occupancy of the bulk-staged pass: %s", cudaGetErrorString(ce));
+            if (per_sm > 0) bulk_chunking(D, o, per_sm, sms);
+        }
+    }
     g->has_dyn = true;
     return ODP_OK;
 }

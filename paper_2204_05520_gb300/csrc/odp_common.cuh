@@ -125,13 +125,22 @@ struct PlaneGeom {
 struct BulkGeom {
     int use;           // 0: never; 1: where it is the faster pass (4 or more dims); 2: wherever it applies
     int rb, nbands;    // rows per band (the last band may be shorter), bands
-    int chunk, nchunks;
-    int items;         // CTAs per launch
+    int chunk[2], nchunks[2];   // stream-axis chunking per stencil radius 1, 2
+    int items[2];      // CTAs per launch, per stencil radius
     int cwarps;        // compute warps per CTA
     int rc, rx;        // ring slots
-    int smem[2];       // dynamic shared bytes for stencil radius 1, 2
-    FastDiv div_nchunks, div_nbands;
+    int smem[2];       // dynamic shared bytes per stencil radius with all three read-once tiles (0: too large)
+    FastDiv div_nchunks[2], div_nbands;
 };
+
+// Dynamic shared bytes of the bulk-staged pass: the barrier area, rc centre
+// slots of rb + 2o rows, and rx neighbour slots of 2o (nd - 3) neighbour
+// tiles and naux read-once tiles of rb rows each.
+ODP_HD long long bulk_smem_bytes(const BulkGeom &bk, int n_pad, int nd, int o, int naux)
+{
+    const long long row = 4LL * n_pad;
+    return 512 + bk.rc * (bk.rb + 2LL * o) * row + bk.rx * (2LL * o * (nd - 3) + naux) * bk.rb * row;
+}
 
 // Storage: C order with the last axis padded to n_pad, a multiple of 4 nodes,
 // so that every row starts on a 16-byte boundary and a thread can move four

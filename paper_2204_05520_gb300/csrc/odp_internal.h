@@ -24,8 +24,12 @@ void plane_geometry(GridDesc &D, int sms);
 // chunks of up to 16 planes (the parallelism comes from the many grids).
 void plane_geometry_many(GridDesc &D);
 // Geometry of the bulk-staged pass of a single solve (D.bk; bk.use = 0 when
-// the pass does not apply), aiming at about four waves of CTAs on `sms` SMs.
-void bulk_geometry(GridDesc &D, int sms);
+// the pass does not apply): bands of about `threads` compute threads, and
+// stream-axis chunks for an estimated occupancy on `sms` SMs.
+void bulk_geometry(GridDesc &D, int sms, int threads);
+// Stream-axis chunking of the bulk-staged pass for stencil radius o, with
+// per_sm CTAs resident per SM on `sms` SMs (bk.chunk, nchunks, items).
+void bulk_chunking(GridDesc &D, int o, int per_sm, int sms);
 }  // namespace odp
 
 // Kernel arguments (grid and dynamics descriptors) are frozen into the graph

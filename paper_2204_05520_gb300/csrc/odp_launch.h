@@ -22,6 +22,11 @@ cudaError_t configure_stage_si(int nd, int kind);
 cudaError_t configure_stage_dubins(int nd);
 cudaError_t configure_stage_rel6d();
 
+// Resident CTAs per SM of the bulk-staged pass (radius `order`, `threads`
+// threads and `smem` shared bytes a CTA), after configure_stage_*.
+cudaError_t occupancy_stage_bulk_dubins(int nd, int order, int threads, int smem, int *per_sm);
+cudaError_t occupancy_stage_bulk_rel6d(int order, int threads, int smem, int *per_sm);
+
 // Grid-wide max of the phi-independent alpha components (K1, once per solve).
 cudaError_t launch_alpha_static_si(int nd, const GridDesc &g, const DynDesc &dy, SolveState *st,
                                    cudaStream_t s);
