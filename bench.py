@@ -676,13 +676,6 @@ def run_ttr(args):
         ups, secs, threads, nsw = oracle_ttr_sample(problem, want)
         cpu = {"value": ups, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "%d sweeps of the full %s grid (%d nodes), %.1f s" % (nsw, problem.name, N, secs)}
-    extras = None
-    if world == 1 and args.workload == "dubinscar4d" and not args.no_extras:
-        extras = extra_workloads(args)
-    alu = {"bound": "alu", "achieved": alu_ops_per_node_step(problem) * N * steps_per_solve / (ms_per_step / 1000.0),
-           "peak": GB300_FP32_LANE_OPS, "unit": "FP32 lane ops/s",
-           "frac": alu_ops_per_node_step(problem) * N * steps_per_solve / (ms_per_step / 1000.0) / GB300_FP32_LANE_OPS,
-           "ops_per_node_step": alu_ops_per_node_step(problem)}
 
     if rank == 0:
         line = {
