@@ -30,6 +30,8 @@
 
 #include <type_traits>
 
+#include <type_traits>
+
 #include "hj_kernels.cuh"
 #include "hj_plane.cuh"
 
@@ -587,7 +589,10 @@ __global__ void __launch_bounds__(512) __maxnreg__((bulk_max_regs<ND, ORDER, DYN
     float2 fin = make_float2(0.f, 0.f);
 
     // One plane s.
-    auto step = [&](int s) {
+    // EDGE: the plane may need stream-axis ghost planes ahead (s + O >= ns);
+    // planes further in skip those tests
+    auto step = [&](int s, auto edge) {
+        constexpr bool EDGE = decltype(edge)::value;
         // the centre tile of plane s + O (with the neighbour tiles of plane s)
         if (!mbar_wait(&sm.full_c[n_slot], n_par)) ok = false;
         const float *Tn = sm.ring_c + n_slot * ctile + so;
@@ -615,10 +620,10 @@ __global__ void __launch_bounds__(512) __maxnreg__((bulk_max_regs<ND, ORDER, DYN
                 const int s1 = r_slot + 1 == rc ? 0 : r_slot + 1;
                 float4 w1 = *reinterpret_cast<const float4 *>(sm.ring_c + s1 * ctile + so);
                 float4 w2 = *reinterpret_cast<const float4 *>(Tn);
-                if (s + 1 >= ns) {          // planes ns, ns + 1 from planes ns - 1 (c4), ns - 2
+                if (EDGE && s + 1 >= ns) {          // planes ns, ns + 1 from planes ns - 1 (c4), ns - 2
                     w1 = ghost_d(c4, ea, 1.0f);
                     w2 = ghost_d(c4, ea, 2.0f);
-                } else if (s + 2 >= ns) {   // plane ns from planes ns - 1 (w1), ns - 2 (c4)
+                } else if (EDGE && s + 2 >= ns) {   // plane ns from planes ns - 1 (w1), ns - 2 (c4)
                     w2 = ghost_d(w1, eb, 1.0f);
                 }
                 const float4 en = sub4(w2, w1);
@@ -631,7 +636,7 @@ __global__ void __launch_bounds__(512) __maxnreg__((bulk_max_regs<ND, ORDER, DYN
                 db = sa_r;
             } else {
                 float4 w1 = *reinterpret_cast<const float4 *>(Tn);
-                if (s + 1 >= ns) w1 = ghost_d(c4, ea, 1.0f);
+                if (EDGE && s + 1 >= ns) w1 = ghost_d(c4, ea, 1.0f);
                 sa_b = sub4(w1, c4);
                 if (s == 0) ea = sub4(c4, ghost_d(c4, sa_b, 1.0f));   // plane -1
                 sa_a = ea;
@@ -726,17 +731,21 @@ __global__ void __launch_bounds__(512) __maxnreg__((bulk_max_regs<ND, ORDER, DYN
 #define ODP_BULK_UNROLL2 1
 #endif
     // two planes per iteration: the carried differences then need no
-    // register moves (a small body still, for the instruction cache)
+    // register moves (a small body still, for the instruction cache); the
+    // last O planes of the grid take the tests for ghost planes ahead
+    using interior = std::false_type;
+    using edge = std::true_type;
+    const int s_hi = min(s_end, ns - O);
     int s = s_begin;
     if (ODP_BULK_UNROLL2) {
 #pragma unroll 1
-        for (; s + 1 < s_end && ok; s += 2) {
-            step(s);
-            step(s + 1);
+        for (; s + 1 < s_hi && ok; s += 2) {
+            step(s, interior{});
+            step(s + 1, interior{});
         }
     }
 #pragma unroll 1
-    for (; s < s_end && ok; ++s) step(s);
+    for (; s < s_end && ok; ++s) step(s, edge{});
     if (!ok) atomicOr(&st->flags, FLAG_COPY);
     if (!(fin.x == 0.0f && fin.y == 0.0f)) atomicOr(&st->flags, FLAG_NONFINITE);
 }
