@@ -151,6 +151,9 @@ ODP_HD void axis_pair(float2 fm2, float2 fm1, float2 f0, float2 fp1, float2 fp2,
 // The last axis of four consecutive nodes from their eight-node window
 // w[j] = phi(first - 2 + j), sharing the first and second differences of the
 // window between the four nodes (the same float32 operations as diffs()).
+// The per-node operations run on node pairs (0, 1) and (2, 3) in paired
+// float32 instructions; each lane is the scalar operation, so the results
+// are those of the scalar form.
 template <int ORDER>
 ODP_HD void axis_last(const float *w, const float *cA, float cS, float cD, float *L, bool has_a, bool has_s,
                       float *Pout = nullptr, const float *cDn = nullptr)
@@ -159,25 +162,34 @@ ODP_HD void axis_last(const float *w, const float *cA, float cS, float cD, float
     float e[7];
 #pragma unroll
     for (int j = 0; j < 7; ++j) e[j] = w[j + 1] - w[j];
+    float d2[6];
+    if (ORDER == 2) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float a = e[k + 1], b = e[k + 2];
-        float dm = a, dp = b;
+        for (int j = 0; j < 6; ++j) d2[j] = e[j + 1] - e[j];   // the second difference at node j - 1
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int k = 2 * h;   // nodes k, k + 1
+        const float2 a = make_float2(e[k + 1], e[k + 2]), b = make_float2(e[k + 2], e[k + 3]);
+        float2 dm = a, dp = b;
         if (ORDER == 2) {
-            const float d2l = a - e[k];
-            const float d2m = b - a;
-            const float d2r = e[k + 3] - b;
-            const float cm = (fabsf(d2l) < fabsf(d2m)) ? d2l : d2m;
-            const float cp = (fabsf(d2r) < fabsf(d2m)) ? d2r : d2m;
-            dm = fmaf(cm, 0.5f, a);
-            dp = fmaf(cp, -0.5f, b);
+            // node i: left choice between D2(i - 1), D2(i); right between D2(i + 1), D2(i)
+            const float2 cm = f2pick(make_float2(d2[k], d2[k + 1]), make_float2(d2[k + 1], d2[k + 2]));
+            const float2 cp = f2pick(make_float2(d2[k + 2], d2[k + 3]), make_float2(d2[k + 1], d2[k + 2]));
+            dm = f2fma(cm, f2splat(0.5f), a);
+            dp = f2fma(cp, f2splat(-0.5f), b);
         }
-        const float P = dp + dm, M = dp - dm;
-        if (Pout) Pout[k] = P;
-        float acc = L[k];
-        if (has_a) acc = fmaf(cA[k], P, acc);
-        if (has_s) acc = fmaf(cS, fabsf(P), acc);
-        L[k] = fmaf(cDn ? cDn[k] : cD, M, acc);
+        const float2 P = f2add(dp, dm), M = f2sub(dp, dm);
+        if (Pout) {
+            Pout[k] = P.x;
+            Pout[k + 1] = P.y;
+        }
+        float2 acc = make_float2(L[k], L[k + 1]);
+        if (has_a) acc = f2fma(make_float2(cA[k], cA[k + 1]), P, acc);
+        if (has_s) acc = f2fma(f2splat(cS), f2abs(P), acc);
+        acc = f2fma(cDn ? make_float2(cDn[k], cDn[k + 1]) : f2splat(cD), M, acc);
+        L[k] = acc.x;
+        L[k + 1] = acc.y;
     }
 }
 
