@@ -143,9 +143,11 @@ int64_t odp_grid_points(const odp_grid *g);
 
 /* Choose the dynamics (Section 4.2 plug-ins, Appendix models; see odp_dyn).
  * params: n_params doubles (host), copied.  u_mode / d_mode: roles of the
- * control and the disturbance.  Errors: ODP_EINVAL (unknown model, wrong
- * dimension count, missing parameters, negative bound, angle axis not
- * periodic). */
+ * control and the disturbance.  On the grid's device the call also sizes the
+ * launches of the stage kernels for this model (it queries their occupancy;
+ * no allocation).  Errors: ODP_EINVAL (unknown model, wrong dimension count,
+ * missing parameters, negative bound, angle axis not periodic), ODP_ECUDA (a
+ * failed CUDA query). */
 odp_status odp_set_dynamics(odp_grid *g, odp_dyn kind, const double *params, int n_params,
                             odp_mode u_mode, odp_mode d_mode);
 
