@@ -1,15 +1,17 @@
 // Host check of the stage kernels' shared-window derivative helpers: the
 // last-axis routine (axis_last, four nodes from one eight-node window, node
-// pairs in paired arithmetic) and the paired routine (pair_diffs) must give,
-// bit for bit, what the one-node definition (diffs) gives at every node,
-// followed by the Lax-Friedrichs terms of the axis.  Runs on the CPU: the
+// pairs in paired arithmetic), the paired routine (pair_diffs) and the
+// four-node routine fed with precomputed differences (segment_axis_d, the
+// bulk-staged pass's stream axis) must give, bit for bit, what the one-node
+// definition (diffs) and the five-row routine (segment_axis) give, followed
+// by the Lax-Friedrichs terms of the axis.  Runs on the CPU: the
 // helpers are __host__ __device__ and every paired operation is, lane by
 // lane, the scalar IEEE operation.  Exit status 0 when all cases agree.
 #include <cstdio>
 #include <cstring>
 #include <random>
 
-#include "hj_device.cuh"
+#include "hj_kernels.cuh"
 
 using namespace odp;
 
@@ -59,6 +61,21 @@ static long check(std::mt19937 &rng, int cases)
         if (memcmp(&dma, &dm2.x, 4) || memcmp(&dpa, &dp2.x, 4) || memcmp(&dmb, &dm2.y, 4) ||
             memcmp(&dpb, &dp2.y, 4))
             ++bad;
+        // four nodes from five rows, and from the differences of those rows
+        // taken with the operations the callers of segment_axis_d use
+        float4 r[5];
+        for (int q = 0; q < 5; ++q)
+            r[q] = make_float4(w[q], w[(q + 1) & 7], w[(q + 2) & 7], w[(q + 3) & 7]);
+        auto sub = [](const float4 &x, const float4 &y) {
+            return make_float4(x.x - y.x, x.y - y.y, x.z - y.z, x.w - y.w);
+        };
+        const float4 a4 = sub(r[2], r[1]), b4 = sub(r[3], r[2]);
+        const float4 d2l = sub(a4, sub(r[1], r[0])), d2m = sub(b4, a4), d2r = sub(sub(r[4], r[3]), b4);
+        float2 A01 = make_float2(Lref[0], Lref[1]), A23 = make_float2(Lref[2], Lref[3]);
+        float2 B01 = A01, B23 = A23;
+        segment_axis<O>(r[0], r[1], r[2], r[3], r[4], cA, cS, cD, A01, A23, has_a, has_s);
+        segment_axis_d<O>(a4, b4, d2l, d2m, d2r, cA, cS, cD, B01, B23, has_a, has_s);
+        if (memcmp(&A01, &B01, 8) || memcmp(&A23, &B23, 8)) ++bad;
     }
     return bad;
 }

@@ -4,7 +4,9 @@ nvcc as a host program that includes the kernels' own device header and
 checks, bit for bit, that the last-axis routine (four nodes from one
 eight-node window, node pairs in paired arithmetic) and the two-window
 paired routine give what diffs() gives node by node (Section 3.1.4's ENO2
-choice and the upwind differences), followed by the Lax-Friedrichs terms."""
+choice and the upwind differences), followed by the Lax-Friedrichs terms,
+and that the four-node routine fed with precomputed differences (the
+bulk-staged pass's stream axis) equals the five-row routine."""
 import os
 import shutil
 import subprocess
