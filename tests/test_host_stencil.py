@@ -34,3 +34,26 @@ def test_shared_window_helpers_match_the_one_node_definition(tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "upwind 0, ENO2 0" in r.stdout
+
+
+def test_stage_launch_geometry_covers_every_grid_exactly_once(tmp_path):
+    """tests/host/geometry_check.cu, linked against the library, runs the
+    library's own host geometry functions (plane-streaming and bulk-staged
+    passes) on 4,000 seeded 3-6-D shapes and checks that bands, stream
+    chunks and pencil blocks cover each grid exactly once and that the
+    fast-division tables divide like '/'."""
+    nvcc = _build.nvcc()
+    if not (os.path.isabs(nvcc) and os.path.exists(nvcc)) and shutil.which(nvcc) is None:
+        pytest.skip("nvcc not available")
+    lib = _build.build()
+    exe = str(tmp_path / "geometry_check")
+    src = os.path.join(ROOT, "tests", "host", "geometry_check.cu")
+    csrc = os.path.join(ROOT, "paper_2204_05520_gb300", "csrc")
+    libdir = os.path.dirname(lib)
+    cmd = [nvcc, *_build.ARCH, "-std=c++17", "-O2", "-I", csrc, "-I", os.path.join(ROOT, "include"),
+           src, "-o", exe, "-L", libdir, "-lodp", "-Xlinker", "-rpath=" + libdir]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "failures: 0" in r.stdout
