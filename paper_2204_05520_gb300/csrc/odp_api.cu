@@ -307,6 +307,20 @@ void odp::bulk_chunking(GridDesc &D, int o, int per_sm, int sms)
     bk.div_nchunks[o - 1] = make_fastdiv(uint32_t(bk.nchunks[o - 1]));
 }
 
+float odp::rel6d_heading_ceiling(float b, double lo, double hi, int n, int periodic)
+{
+    // the straddling case max(|b - w_p|, |-b - w_p|) at every w_p node, in
+    // float as the kernel evaluates it, at the float node coordinates of the
+    // grid's table (the same spacing and rounding as odp_grid_create's)
+    const double h = periodic ? (hi - lo) / double(n) : (hi - lo) / double(n - 1);
+    float cap = 0.0f;
+    for (int i = 0; i < n; ++i) {
+        const float wp = float(lo + double(i) * h);
+        cap = std::max(cap, std::max(std::fabs(b - wp), std::fabs(-b - wp)));
+    }
+    return cap;
+}
+
 void odp::bulk_geometry(GridDesc &D, int sms, int threads)
 {
     BulkGeom &bk = D.bk;
@@ -590,19 +604,7 @@ extern "C" odp_status odp_set_dynamics(odp_grid *g, odp_dyn kind, const double *
     dy.angle_axis = angle;
     dy.local_diss = g->local_diss;
     for (int k = 0; k < n_params; ++k) dy.prm[k] = float(params[k]);
-    if (kind == ODP_DYN_REL6D) {
-        // ceiling of the heading-rate bound over the grid: the straddling
-        // case max(|b - w_p|, |-b - w_p|) at every w_p node, in float as the
-        // kernel evaluates it (the node coordinates are the float table's)
-        const float b = dy.prm[3];
-        const double h = (g->hi[4] - g->lo[4]) / double(g->periodic[4] ? g->n[4] : g->n[4] - 1);
-        float cap = 0.0f;
-        for (int i = 0; i < g->n[4]; ++i) {
-            const float wp = float(g->lo[4] + double(i) * h);
-            cap = std::max(cap, std::max(std::fabs(b - wp), std::fabs(-b - wp)));
-        }
-        dy.acap = cap;
-    }
+    if (kind == ODP_DYN_REL6D) dy.acap = rel6d_heading_ceiling(dy.prm[3], g->lo[4], g->hi[4], g->n[4], g->periodic[4]);
     g->dyn = dy;
     g->dyn_version += 1;
     if (angle >= 0) {

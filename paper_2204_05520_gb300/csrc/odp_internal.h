@@ -27,6 +27,11 @@ void plane_geometry_many(GridDesc &D);
 // the pass does not apply): bands of about `threads` compute threads, and
 // stream-axis chunks for an estimated occupancy on `sms` SMs.
 void bulk_geometry(GridDesc &D, int sms, int threads);
+// Ceiling of the Rel6D heading-rate dissipation bound over a grid whose w_p
+// axis has n nodes on [lo, hi] (periodic or not), b the evader's turn bound:
+// no node's bound exceeds it, and a node whose one-sided differences
+// straddle zero at the largest |w_p| reaches it (the alpha pass stops there).
+float rel6d_heading_ceiling(float b, double lo, double hi, int n, int periodic);
 // Stream-axis chunking of the bulk-staged pass for stencil radius o, with
 // per_sm CTAs resident per SM on `sms` SMs (bk.chunk, nchunks, items).
 void bulk_chunking(GridDesc &D, int o, int per_sm, int sms);

@@ -57,3 +57,26 @@ def test_stage_launch_geometry_covers_every_grid_exactly_once(tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "failures: 0" in r.stdout
+
+
+def test_rel6d_heading_alpha_never_exceeds_its_precomputed_ceiling(tmp_path):
+    """tests/host/alpha_ceiling_check.cu, linked against the library: on
+    3,000 seeded w_p axes the kernels' per-node heading-rate bound never
+    exceeds rel6d_heading_ceiling, and a straddling node reaches it bit for
+    bit -- the premise that lets the alpha pass stop reading at the ceiling
+    with an unchanged result."""
+    nvcc = _build.nvcc()
+    if not (os.path.isabs(nvcc) and os.path.exists(nvcc)) and shutil.which(nvcc) is None:
+        pytest.skip("nvcc not available")
+    lib = _build.build()
+    exe = str(tmp_path / "alpha_ceiling_check")
+    src = os.path.join(ROOT, "tests", "host", "alpha_ceiling_check.cu")
+    csrc = os.path.join(ROOT, "paper_2204_05520_gb300", "csrc")
+    libdir = os.path.dirname(lib)
+    cmd = [nvcc, *_build.ARCH, "-std=c++17", "-O2", "-I", csrc, "-I", os.path.join(ROOT, "include"),
+           src, "-o", exe, "-L", libdir, "-lodp", "-Xlinker", "-rpath=" + libdir]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "failures 0" in r.stdout
