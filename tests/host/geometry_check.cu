@@ -9,7 +9,8 @@
 // fill reads two ahead), at least four planes a chunk where the axis allows,
 // CTA counts equal bands x chunks x pencils, the compute threads of a bulk
 // CTA cover its band, pencil blocks tile every outer axis, and each fast
-// division table divides like '/'.  Exit status 0 when every shape passes.
+// division table divides like '/'; and the chunk counts the makespan model
+// picks on the measured workloads.  Exit status 0 when every shape passes.
 #include <cstdio>
 #include <random>
 
@@ -106,6 +107,41 @@ int main()
                 }
             }
         }
+    }
+    // the chunk counts the makespan model picks on the measured workloads:
+    // DubinsCar4D 80x80x40x64 (ENO2) with bands of 256 threads and two CTAs
+    // per SM -> 5 chunks, with bands of 128 threads and four CTAs -> 3;
+    // Rel6D 24^6 (upwind) with three CTAs per SM -> 1
+    {
+        const char *shape = "measured workloads";
+        GridDesc D{};
+        D.ndim = 4;
+        const int n4[4] = {80, 80, 40, 64};
+        for (int d = 0; d < 4; ++d) D.n[d] = n4[d];
+        D.n_pad = 64;
+        D.segs = 16;
+        D.nr = 40;
+        plane_geometry(D, 152);
+        bulk_geometry(D, 152, 256);
+        CHECK(D.bk.use && D.bk.nbands == 3);
+        bulk_chunking(D, 2, 2, 152);
+        CHECK(D.bk.nchunks[1] == 5);
+        bulk_geometry(D, 152, 128);
+        CHECK(D.bk.use && D.bk.nbands == 5 && D.bk.cwarps == 4);
+        bulk_chunking(D, 2, 4, 152);
+        CHECK(D.bk.nchunks[1] == 3);
+        GridDesc R{};
+        R.ndim = 6;
+        for (int d = 0; d < 6; ++d) R.n[d] = 24;
+        R.periodic[2] = 1;
+        R.n_pad = 24;
+        R.segs = 6;
+        R.nr = 24;
+        plane_geometry(R, 152);
+        bulk_geometry(R, 152, 256);
+        CHECK(R.bk.use && R.bk.nbands == 1 && R.bk.cwarps == 5);
+        bulk_chunking(R, 1, 3, 152);
+        CHECK(R.bk.nchunks[0] == 1);
     }
     printf("shapes with a plane geometry: %d, with a bulk geometry: %d, failures: %ld\n", shapes, bulk_shapes,
            fails);
